@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""RgCSR SpMV benchmark on GB300.
+
+One step = one RgCSR SpMV (group size 32, default kernel) of each of the
+three large synthetic matrices in FP32 and in FP64 (six SpMVs):
+  (a) 3D 7-point Laplacian 128^3        n = 2,097,152  nnz = 14,581,760
+  (b) power-law rows, n = 10^6          nnz ~ 15.6M, longest row 10,000
+  (c) 27-point stencil 96^3, U[-1,1]    n = 884,736    nnz = 23,393,656
+value = algorithmic bytes of the six SpMVs (values + columns of the
+non-zeros, row lengths, group pointers, x once, y once; padding excluded)
+per second, whole job.  Inputs stay resident in HBM; each step streams
+~1.3 GB of algorithmic data (more with padding), far more than the 129 MB
+L2, so no SpMV finds its matrix in L2.
+
+Also reported: per-case GB/s and GFLOP/s (2 nnz / t), the HYB comparator
+on the same cases, the roofline of the dominant kernel against the
+measured HBM copy bandwidth, an end-to-end figure through the host entry
+point (x copied in, y copied out each step), and the CPU oracle as a
+baseline on a bounded sample.
+
+--impl reference runs the CPU oracle (plain FP64 CSR SpMV, one thread) on
+a bounded row sample of the same six cases per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1012_2270_gb300 import synth  # noqa: E402
+from paper_1012_2270_gb300 import roofline  # noqa: E402
+
+METRIC = "RgCSR SpMV GB/s (% of 8 TB/s HBM), GFLOP/s; batched/BF16/bwd vs plain"
+UNIT = "GB/s"
+GROUP = 32
+CASES = [("a", synth.workload_a), ("b", synth.workload_b), ("c", synth.workload_c)]
+DTYPES = ["f32", "f64"]
+VB = {"f32": 4, "f64": 8}
+NP = {"f32": np.float32, "f64": np.float64}
+WORKLOAD = ("RgCSR SpMV, G=32, FP32 and FP64, of (a) 3D 7-point Laplacian 128^3, "
+            "(b) power-law rows n=1e6 (Zipf(2) lengths, max 10,000, natural row order), "
+            "(c) 27-point stencil 96^3")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--cpu-seconds", type=float, default=10.0,
+                   help="CPU work of the oracle baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip HYB and the other forms")
+    return p.parse_args()
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def load_cases():
+    mats = []
+    for name, fn in CASES:
+        A = fn()
+        x = synth.uniform_vector(A.n_cols, seed=0)
+        mats.append((name, A, x))
+    return mats
+
+
+def case_bytes(A, n_groups, dtype):
+    return roofline.rgcsr_spmv_bytes(A.n_rows, A.n_cols, A.nnz, n_groups, VB[dtype])
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_case_inputs(mats):
+    out = []
+    for name, A, x in mats:
+        for dt in DTYPES:
+            val = A.val.astype(NP[dt]).astype(np.float64)
+            xv = x.astype(NP[dt]).astype(np.float64)
+            ng = (A.n_rows + GROUP - 1) // GROUP
+            out.append((f"{name}_{dt}", A, val, xv, case_bytes(A, ng, dt)))
+    return out
+
+
+def row_slice(A, val, lo, hi):
+    p0, p1 = A.rowptr[lo], A.rowptr[hi]
+    return A.rowptr[lo:hi + 1] - p0, A.col[p0:p1], val[p0:p1]
+
+
+def cpu_baseline(mats, seconds):
+    """The oracle as it stands, one thread, repeated over the six cases until
+    `seconds` of CPU work; returns GB/s of algorithmic bytes."""
+    import oracle
+    cases = oracle_case_inputs(mats)
+    t = 0.0
+    nbytes = 0
+    passes = 0
+    while t < seconds or passes == 0:
+        for _, A, val, xv, b in cases:
+            t0 = time.perf_counter()
+            oracle.csr_spmv(A.rowptr, A.col, val, xv)
+            t += time.perf_counter() - t0
+            nbytes += b
+        passes += 1
+    return {"value": nbytes / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{passes} full pass(es) of the six SpMVs (FP64 CSR loop on the FP32/FP64 values), "
+                      f"{t:.1f} s of one host core"}
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return 0
+    import oracle
+    mats = load_cases()
+    cases = oracle_case_inputs(mats)
+    frac = 16     # each step: 1/16 of the rows of every case, rotating slices
+    slices = []   # per case: frac (rowptr, col, val, x, bytes) row slices
+    for key, A, val, xv, b in cases:
+        h = A.n_rows // frac
+        per = []
+        for s in range(frac):
+            rp, col, v = row_slice(A, val, s * h, (s + 1) * h)
+            per.append((rp, col, v, xv, b * (rp[-1] / A.nnz)))
+        slices.append(per)
+
+    def step(k):
+        nb = 0.0
+        for per in slices:
+            rp, col, v, xv, b = per[k % frac]
+            oracle.csr_spmv(rp, col, v, xv)
+            nb += b
+        return nb
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    nb = 0.0
+    for k in range(args.steps):
+        nb += step(args.warmup + k)
+    t = time.perf_counter() - t0
+    value = nb / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD + "; CPU oracle on a rotating 1/16 row slice of each case per step",
+                   "group_size": GROUP},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "per step: FP64 CSR SpMV of a rotating 1/16 row slice of each of the six cases"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        ident = vis.split(",")[local_rank] if vis else str(local_rank)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", ident, "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [s.strip() for s in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1012_2270_gb300 import _lib as L
+    from paper_1012_2270_gb300.rgcsr import HybMatrix, RgCSRMatrix
+
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    mats = load_cases()
+
+    # ---- convert (one-off) ----
+    cases = []
+    for name, A, x in mats:
+        for dt in DTYPES:
+            M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dt]), A.n_cols,
+                                     group_size=GROUP, dtype=getattr(torch, "float32" if dt == "f32" else "float64"))
+            xd = torch.from_numpy(x.astype(NP[dt])).to(dev)
+            yd = torch.empty(A.n_rows, dtype=xd.dtype, device=dev)
+            nb = case_bytes(A, M.s.n_groups, dt)
+            cases.append(dict(key=f"{name}_{dt}", name=name, dt=dt, A=A, M=M, x=xd, y=yd, bytes=nb,
+                              nnz=A.nnz, kernel=f"rgcsr_spmv_split<{'float' if dt == 'f32' else 'double'}>",
+                              pad_pct=M.artificial_zero_percent()))
+    torch.cuda.synchronize()
+    step_bytes = sum(c["bytes"] for c in cases)
+
+    def launch(c):
+        c["M"].spmv(c["x"], out=c["y"])
+
+    # ---- warm-up ----
+    for _ in range(args.warmup):
+        for c in cases:
+            launch(c)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-launch events on the launching stream ----
+    K = args.steps
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in cases] for _ in range(K)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local) if rank == 0 else None
+    time.sleep(0.3 if clocks else 0)
+    t_start.record(stream)
+    for k in range(K):
+        for i, c in enumerate(cases):
+            ev[k][i][0].record(stream)
+            launch(c)
+            ev[k][i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop() if clocks else None
+    ms_total = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    per_case_ms = [statistics.fmean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(K))
+                   for i in range(len(cases))]
+    value = world * K * step_bytes / (ms_total * 1e-3) / 1e9
+
+    detail = {}
+    for c, ms in zip(cases, per_case_ms):
+        detail[c["key"]] = {"gbs": c["bytes"] / (ms * 1e-3) / 1e9, "gflops": 2 * c["nnz"] / (ms * 1e-3) / 1e9,
+                            "us": ms * 1e3, "pct_of_8tbs": 100 * c["bytes"] / (ms * 1e-3) / 1e9 / roofline.NOMINAL_HBM_GBS,
+                            "artificial_zero_pct": c["pad_pct"]}
+
+    # ---- roofline of the dominant kernel ----
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peak_hbm = json.load(open(peaks_path))["hbm_gbs"]
+        peak_src = "measured"
+    else:
+        peak_hbm, peak_src = 6800.0, "fallback"
+    by_kernel = {}
+    for c, ms in zip(cases, per_case_ms):
+        d = by_kernel.setdefault(c["kernel"], {"ms": 0.0, "bytes": 0, "launches": 0})
+        d["ms"] += ms
+        d["bytes"] += c["bytes"]
+        d["launches"] += 1
+    dom = max(by_kernel, key=lambda k: by_kernel[k]["ms"])
+    d = by_kernel[dom]
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+            "frac": achieved / peak_hbm, "traffic": None, "kernel": dom, "peak_source": peak_src,
+            "bytes_per_launch": d["bytes"] / d["launches"], "avg_launch_us": 1e3 * d["ms"] / d["launches"]}
+
+    # ---- end to end: host x in, host y out, through rgcsr_spmv_host ----
+    host = []
+    for c in cases:
+        xh = c["x"].cpu().pin_memory()
+        yh = torch.empty(c["y"].numel(), dtype=c["y"].dtype).pin_memory()
+        host.append((xh, yh, torch.empty_like(c["x"]), torch.empty_like(c["y"])))
+    h2d = sum(h[0].numel() * h[0].element_size() for h in host)
+    d2h = sum(h[1].numel() * h[1].element_size() for h in host)
+    Ke = max(3, K // 4)
+    for c, h in zip(cases, host):
+        c["M"].spmv_host(*h)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(Ke):
+        for c, h in zip(cases, host):
+            c["M"].spmv_host(*h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e = {"value": world * Ke * step_bytes / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "note": "per step and case: x host->device, SpMV, y device->host (pinned), matrix resident"}
+
+    # ---- forms beside plain: HYB comparator ----
+    forms = {}
+    if not args.no_forms:
+        hyb = {}
+        for name, A, x in mats:
+            for dt in DTYPES:
+                H = HybMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dt]), A.n_cols,
+                                       dtype=getattr(torch, "float32" if dt == "f32" else "float64"))
+                xd = torch.from_numpy(x.astype(NP[dt])).to(dev)
+                yd = torch.empty(A.n_rows, dtype=xd.dtype, device=dev)
+                for _ in range(3):
+                    H.spmv(xd, out=yd)
+                reps = max(5, K // 10)
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                for _ in range(reps):
+                    H.spmv(xd, out=yd)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                ms = a0.elapsed_time(a1) / reps
+                nb = roofline.hyb_spmv_bytes(A.n_rows, A.n_cols, A.nnz, H.nnz_coo, VB[dt])
+                key = f"{name}_{dt}"
+                hyb[key] = {"gbs": nb / (ms * 1e-3) / 1e9, "gflops": 2 * A.nnz / (ms * 1e-3) / 1e9,
+                            "us": ms * 1e3, "ell_width": H.ell_width, "nnz_coo": H.nnz_coo,
+                            "rgcsr_over_hyb": (ms * 1e-3) / (detail[key]["us"] * 1e-6)}
+                del H
+        forms["hyb"] = hyb
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(mats, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms_total / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32,f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "group_size": GROUP, "kernel": "split (default)",
+                       "l2": "inputs larger than L2: each step streams the six matrices (~1.3 GB algorithmic)",
+                       "parallelism": f"replicas x{world}"},
+            "gflops": world * K * sum(2 * c["nnz"] for c in cases) / (ms_total * 1e-3) / 1e9,
+            "pct_of_8tbs": 100 * value / world / roofline.NOMINAL_HBM_GBS,
+            "gpu_launches": K * len(cases),
+            "clocks": clk,
+            "roofline": roof,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "detail": detail,
+            "forms": forms,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,183 @@
+/*
+ * rgcsr.h -- C ABI of librgcsr: Row-grouped CSR (RgCSR) sparse
+ * matrix-vector multiplication on NVIDIA GB300 (sm_103a), after Oberhuber,
+ * Suzuki and Vacata, "New Row-grouped CSR format for storing the sparse
+ * matrices on GPU with implementation in CUDA".
+ *
+ * General rules for every entry point
+ * -----------------------------------
+ *  - Pointers are DEVICE pointers unless the name ends in `_host`.
+ *  - The library never allocates device memory.  The caller allocates every
+ *    array (sizes come from the *_plan calls or are stated below) and owns
+ *    it; scratch space is passed in as `workspace` / `workspace_bytes`.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  Calls return after enqueueing unless stated otherwise; the
+ *    *_plan calls synchronise `stream` once to return sizes to the host.
+ *  - Return value: RGCSR_OK (0) or a negative RGCSR_ERR_* code.  Nothing
+ *    traps or asserts on the device.  rgcsr_status_string() names a code.
+ *  - Index types: columns and row lengths int32, group offsets int64; CSR
+ *    row pointers may be int32 or int64.  Rows and columns < 2^31.
+ *  - Value types: RGCSR_F64 and RGCSR_F32 (x and y have the same type), and
+ *    the reduced-storage RGCSR_BF16 / RGCSR_F16 (x and y are float).
+ *  - Every SpMV overwrites y (y = A x, not y += A x), as the paper's
+ *    kernels do.  Empty rows give +0.  n_rows == 0 is a no-op.
+ */
+#ifndef RGCSR_H
+#define RGCSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *rgcsr_stream_t;   /* identical to cudaStream_t */
+
+/* status codes */
+#define RGCSR_OK                     0
+#define RGCSR_ERR_INVALID_ARG       -1   /* NULL pointer, bad size or option   */
+#define RGCSR_ERR_BAD_ROWPTR        -2   /* row_ptr[0] != 0, decreasing, or row_ptr[n] != nnz */
+#define RGCSR_ERR_COL_OOB           -3   /* a column index outside [0, n_cols) */
+#define RGCSR_ERR_INDEX_OVERFLOW    -4   /* a size exceeds its index type      */
+#define RGCSR_ERR_UNSUPPORTED_DTYPE -5   /* value type not valid for this call */
+#define RGCSR_ERR_CUDA              -6   /* a CUDA runtime call failed         */
+#define RGCSR_ERR_WORKSPACE         -7   /* workspace missing or too small     */
+
+/* element types */
+#define RGCSR_F64  0
+#define RGCSR_F32  1
+#define RGCSR_BF16 2
+#define RGCSR_F16  3
+#define RGCSR_I32  4
+#define RGCSR_I64  5
+
+/* A CSR matrix (Sec. 3.1): row r holds entries row_ptr[r] .. row_ptr[r+1]-1
+ * of col_idx/values.  Column order inside a row is kept as given (the paper
+ * assumes ascending columns); duplicates and explicit zeros are entries. */
+typedef struct {
+    int64_t n_rows, n_cols, nnz;
+    const void *row_ptr;        /* n_rows+1 entries of row_ptr_type          */
+    int32_t row_ptr_type;       /* RGCSR_I32 or RGCSR_I64                    */
+    int32_t value_type;         /* RGCSR_F64 or RGCSR_F32                    */
+    const int32_t *col_idx;     /* nnz                                       */
+    const void *values;         /* nnz of value_type                         */
+} rgcsr_csr;
+
+/* An RgCSR matrix (Sec. 3.4).  Rows are cut into groups of G consecutive
+ * rows; group g has R_g = min(G, n_rows - g*G) rows and K_g = the longest
+ * row length in it.  Slot j of row r = g*G + t is stored at
+ *     group_ptr[g] + j*R_g + t        (0 <= j < K_g),
+ * so the j-th entries of a group's rows are contiguous.  Slots past a row's
+ * length are padding ("artificial zeros"): value bits 0, column 0; kernels
+ * never multiply them because row_lengths bounds every row's loop. */
+typedef struct {
+    int64_t n_rows, n_cols, nnz;
+    int32_t group_size;         /* G >= 1 (set by the caller before plan)    */
+    int32_t value_type;         /* storage type of `values`                  */
+    int64_t n_groups;           /* ceil(n_rows / G)                  (plan) */
+    int64_t n_stored;           /* group_ptr[n_groups] = nnz + padding (plan) */
+    int64_t max_row_len;        /*                                   (plan) */
+    void *values;               /* n_stored elements of value_type           */
+    int32_t *columns;           /* n_stored                                  */
+    int64_t *group_ptr;         /* n_groups + 1 ("groupPointers")            */
+    int32_t *row_lengths;       /* n_rows       ("rowLengths")               */
+    float *row_scale;           /* n_rows; BF16/F16 storage only, else NULL  */
+    int64_t *slot_to_csr;       /* optional n_stored: CSR position per slot, -1 = padding */
+} rgcsr_matrix;
+
+/* Kernel selection for rgcsr_spmv_ex (autotuning and ablations). */
+#define RGCSR_KERNEL_AUTO   0    /* default: warp-split kernel                     */
+#define RGCSR_KERNEL_PAPER  1    /* one block per group, one thread per row (Sec. 3.4 listing) */
+#define RGCSR_KERNEL_SPLIT  2    /* one thread per row; long rows of a warp finished
+                                    by the whole warp with a shuffle reduction      */
+#define RGCSR_XLOAD_NC      0    /* x through the read-only (non-coherent) path    */
+#define RGCSR_XLOAD_PLAIN   1    /* x with ordinary global loads                   */
+typedef struct {
+    int32_t kernel;             /* RGCSR_KERNEL_*                                  */
+    int32_t block_threads;      /* 0 = default (256); multiple of 32, <= 256       */
+    int32_t x_load;             /* RGCSR_XLOAD_*                                   */
+    int32_t split_weight;       /* 0 = default; cost of one warp-cooperative step
+                                   relative to one thread-per-row step, x 4        */
+} rgcsr_launch;
+
+/* ----------------------------------------------------------------------- */
+/* Conversion CSR -> RgCSR (Sec. 3.4: groups, padding, groupPointers,       */
+/* rowLengths).  Two phases so that the caller can allocate:                */
+/*   1. rgcsr_plan   -- validates the CSR, writes row_lengths and group_ptr */
+/*                      (both caller-allocated: n_rows and ceil(n/G)+1),    */
+/*                      sets n_groups, n_stored, max_row_len, nnz, sizes.   */
+/*                      Synchronises `stream`.                              */
+/*   2. rgcsr_convert -- scatters values/columns (and slot_to_csr if non-   */
+/*                      NULL) into caller-allocated n_stored arrays.        */
+/*                      M->value_type must equal A->value_type.  Async.     */
+/* ----------------------------------------------------------------------- */
+size_t rgcsr_plan_workspace_bytes(int64_t n_rows, int32_t group_size);
+int rgcsr_plan(const rgcsr_csr *A, rgcsr_matrix *M, void *workspace,
+               size_t workspace_bytes, rgcsr_stream_t stream);
+int rgcsr_convert(const rgcsr_csr *A, const rgcsr_matrix *M, rgcsr_stream_t stream);
+
+/* ----------------------------------------------------------------------- */
+/* SpMV y = A x on an RgCSR matrix (Sec. 3.4 kernel; peak model of the     */
+/* same section).  x: n_cols elements, y: n_rows elements; F64 storage     */
+/* takes double x/y, every other storage float x/y.  x and y must not      */
+/* overlap.  Async.                                                        */
+/* ----------------------------------------------------------------------- */
+int rgcsr_spmv(const rgcsr_matrix *M, const void *x, void *y, rgcsr_stream_t stream);
+int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
+                  const rgcsr_launch *launch, rgcsr_stream_t stream);
+
+/* The same SpMV from and to HOST memory: copies x_host (n_cols elements) to
+ * the caller's device buffer x_dev, runs rgcsr_spmv into y_dev, copies y_dev
+ * to y_host (n_rows elements), all on `stream`.  Pinned host buffers make
+ * the copies asynchronous; the caller synchronises before reading y_host. */
+int rgcsr_spmv_host(const rgcsr_matrix *M, const void *x_host, void *y_host,
+                    void *x_dev, void *y_dev, rgcsr_stream_t stream);
+
+/* ----------------------------------------------------------------------- */
+/* Hybrid ELLPACK + COO (Sec. 3.3), the paper's comparison format.  The ELL */
+/* part is column-major, n_rows x ell_width (slot j of row r at j*n_rows+r, */
+/* padding: value 0, column -1); entries past a row's first ell_width go to */
+/* COO (row, column, value), ordered by row and then by stored order.       */
+/* ell_width < 0 in hyb_plan selects it by the byte-cost rule              */
+/*   minimise n*K*(sv+si) + 2*nnz_coo(K)*(sv+2*si),  ties -> smaller K.     */
+/* ----------------------------------------------------------------------- */
+typedef struct {
+    int64_t n_rows, n_cols, nnz;
+    int32_t value_type;         /* RGCSR_F64 or RGCSR_F32                    */
+    int32_t ell_width;          /* K1                                (plan) */
+    int64_t nnz_coo;            /*                                   (plan) */
+    int64_t max_row_len;        /*                                   (plan) */
+    void *ell_val;              /* ell_width * n_rows                        */
+    int32_t *ell_col;           /* ell_width * n_rows                        */
+    int32_t *coo_row;           /* nnz_coo                                   */
+    int32_t *coo_col;           /* nnz_coo                                   */
+    void *coo_val;              /* nnz_coo                                   */
+} hyb_matrix;
+
+/* Workspace for hyb_plan and hyb_convert (one buffer serves both). */
+size_t hyb_workspace_bytes(int64_t n_rows, int64_t n_cols);
+/* Validates the CSR, picks ell_width (if < 0) and counts nnz_coo.  Sets the
+ * size fields of H; synchronises `stream`.  Rows longer than n_cols + 1
+ * (only possible with duplicate columns) give RGCSR_ERR_INVALID_ARG. */
+int hyb_plan(const rgcsr_csr *A, int32_t ell_width, hyb_matrix *H, void *workspace,
+             size_t workspace_bytes, rgcsr_stream_t stream);
+/* Fills the caller-allocated ELL and COO arrays.  Async. */
+int hyb_convert(const rgcsr_csr *A, const hyb_matrix *H, void *workspace,
+                size_t workspace_bytes, rgcsr_stream_t stream);
+/* y = A x: the ELL step writes y, the COO step adds the overflow.  Rows whose
+ * COO entries span several warps' tiles are combined with atomic adds, so
+ * their last bits may differ between runs.  Async. */
+int hyb_spmv(const hyb_matrix *H, const void *x, void *y, rgcsr_stream_t stream);
+
+/* ----------------------------------------------------------------------- */
+/* Misc                                                                     */
+/* ----------------------------------------------------------------------- */
+const char *rgcsr_status_string(int status);
+/* Library version as major*10000 + minor*100 + patch. */
+int rgcsr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RGCSR_H */

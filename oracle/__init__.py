@@ -152,6 +152,17 @@ class RgCSRLayout:
         return int(self.group_ptr[-1])
 
 
+def rgcsr_sizes(rowptr, group_size: int):
+    """rowLengths and groupPointers only (Sec. 3.4), without the slabs."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    n = rowptr.size - 1
+    G = int(group_size)
+    rl = np.empty(n, np.int32)
+    gp = np.empty((n + G - 1) // G + 1, np.int64)
+    _load().orc_rgcsr_sizes(n, _p(rowptr), G, _p(rl), _p(gp))
+    return rl, gp
+
+
 def rgcsr_layout(rowptr, col, val, group_size: int) -> RgCSRLayout:
     """CSR -> RgCSR (Sec. 3.4).  ``val`` keeps its dtype; values are copied
     bit for bit, padding is all-zero bits with column 0."""

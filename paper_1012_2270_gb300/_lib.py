@@ -1,0 +1,105 @@
+"""ctypes binding of librgcsr.so: the C structs of include/rgcsr.h and the
+exported functions under the same names.  Argument marshalling only; every
+computation runs in the library's CUDA kernels.  Loading fails loudly when
+the library has not been built -- there is no fallback path."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+I32, I64, P, SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t
+
+RGCSR_OK = 0
+RGCSR_ERR_INVALID_ARG = -1
+RGCSR_ERR_BAD_ROWPTR = -2
+RGCSR_ERR_COL_OOB = -3
+RGCSR_ERR_INDEX_OVERFLOW = -4
+RGCSR_ERR_UNSUPPORTED_DTYPE = -5
+RGCSR_ERR_CUDA = -6
+RGCSR_ERR_WORKSPACE = -7
+
+F64, F32, BF16, F16, I32T, I64T = 0, 1, 2, 3, 4, 5
+
+KERNEL_AUTO, KERNEL_PAPER, KERNEL_SPLIT = 0, 1, 2
+XLOAD_NC, XLOAD_PLAIN = 0, 1
+
+
+class CSR(ctypes.Structure):
+    _fields_ = [("n_rows", I64), ("n_cols", I64), ("nnz", I64),
+                ("row_ptr", P), ("row_ptr_type", I32), ("value_type", I32),
+                ("col_idx", P), ("values", P)]
+
+
+class Matrix(ctypes.Structure):
+    _fields_ = [("n_rows", I64), ("n_cols", I64), ("nnz", I64),
+                ("group_size", I32), ("value_type", I32),
+                ("n_groups", I64), ("n_stored", I64), ("max_row_len", I64),
+                ("values", P), ("columns", P), ("group_ptr", P), ("row_lengths", P),
+                ("row_scale", P), ("slot_to_csr", P)]
+
+
+class Launch(ctypes.Structure):
+    _fields_ = [("kernel", I32), ("block_threads", I32), ("x_load", I32), ("split_weight", I32)]
+
+
+class Hyb(ctypes.Structure):
+    _fields_ = [("n_rows", I64), ("n_cols", I64), ("nnz", I64),
+                ("value_type", I32), ("ell_width", I32), ("nnz_coo", I64), ("max_row_len", I64),
+                ("ell_val", P), ("ell_col", P), ("coo_row", P), ("coo_col", P), ("coo_val", P)]
+
+
+_PCSR, _PM, _PL, _PH = (ctypes.POINTER(CSR), ctypes.POINTER(Matrix),
+                        ctypes.POINTER(Launch), ctypes.POINTER(Hyb))
+
+# name -> (restype, argtypes); mirrors include/rgcsr.h
+SIGNATURES = {
+    "rgcsr_plan_workspace_bytes": (SZ, [I64, I32]),
+    "rgcsr_plan": (ctypes.c_int, [_PCSR, _PM, P, SZ, P]),
+    "rgcsr_convert": (ctypes.c_int, [_PCSR, _PM, P]),
+    "rgcsr_spmv": (ctypes.c_int, [_PM, P, P, P]),
+    "rgcsr_spmv_ex": (ctypes.c_int, [_PM, P, P, _PL, P]),
+    "rgcsr_spmv_host": (ctypes.c_int, [_PM, P, P, P, P, P]),
+    "hyb_workspace_bytes": (SZ, [I64, I64]),
+    "hyb_plan": (ctypes.c_int, [_PCSR, I32, _PH, P, SZ, P]),
+    "hyb_convert": (ctypes.c_int, [_PCSR, _PH, P, SZ, P]),
+    "hyb_spmv": (ctypes.c_int, [_PH, P, P, P]),
+    "rgcsr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "rgcsr_version": (ctypes.c_int, []),
+}
+
+_lib = None
+
+
+class RgCSRError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        msg = lib().rgcsr_status_string(status).decode()
+        super().__init__(f"{fn} failed: {msg} ({status})")
+
+
+def lib():
+    """The loaded library.  Raises if librgcsr.so was not built."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"librgcsr.so not found at {path}; build it first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def call(name: str, *args) -> int:
+    """Call an exported function; raise RgCSRError on a negative status."""
+    st = getattr(lib(), name)(*args)
+    if st != RGCSR_OK:
+        raise RgCSRError(name, st)
+    return st

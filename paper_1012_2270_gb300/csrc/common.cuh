@@ -1,0 +1,118 @@
+// common.cuh -- shared device/host helpers of librgcsr (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "rgcsr.h"
+
+#define RGCSR_API extern "C" __attribute__((visibility("default")))
+
+namespace rgcsr {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+#define RGCSR_CUDA_TRY(expr)                                  \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) return RGCSR_ERR_CUDA;         \
+    } while (0)
+
+// A launch error is read back without synchronising.
+inline int launch_status() {
+    return cudaGetLastError() == cudaSuccess ? RGCSR_OK : RGCSR_ERR_CUDA;
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------
+// warp collectives
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_max_i(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+__device__ __forceinline__ int warp_min_i(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+__device__ __forceinline__ int64_t shfl_i64(int64_t v, int src) {
+    int lo = __shfl_sync(kFull, (int)(v & 0xffffffff), src);
+    int hi = __shfl_sync(kFull, (int)(v >> 32), src);
+    return (int64_t)(((uint64_t)(uint32_t)hi << 32) | (uint32_t)lo);
+}
+
+// ---------------------------------------------------------------------------
+// loads: matrix slabs are read once (streaming, evict-first), x through the
+// read-only path so that it stays resident in L1/L2 for reuse.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
+
+template <typename T>
+__device__ __forceinline__ T ld_x(const T *p) { return __ldg(p); }
+
+// ---------------------------------------------------------------------------
+// Row pointer access for int32 or int64 CSR row pointers.
+// ---------------------------------------------------------------------------
+struct RowPtr {
+    const void *p;
+    int wide;   // 1 = int64
+    __device__ __forceinline__ int64_t operator[](int64_t i) const {
+        return wide ? static_cast<const int64_t *>(p)[i]
+                    : (int64_t) static_cast<const int32_t *>(p)[i];
+    }
+};
+
+inline bool valid_value_type(int t) { return t == RGCSR_F64 || t == RGCSR_F32; }
+inline size_t value_bytes(int t) {
+    return t == RGCSR_F64 ? 8 : t == RGCSR_F32 ? 4 : (t == RGCSR_BF16 || t == RGCSR_F16) ? 2 : 0;
+}
+
+// Shared checks on a CSR descriptor (host side, no device access).
+inline int check_csr(const rgcsr_csr *A) {
+    if (!A) return RGCSR_ERR_INVALID_ARG;
+    if (A->n_rows < 0 || A->n_cols < 0 || A->nnz < 0) return RGCSR_ERR_INVALID_ARG;
+    if (A->n_rows >= INT32_MAX || A->n_cols >= INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
+    if (A->row_ptr_type != RGCSR_I32 && A->row_ptr_type != RGCSR_I64) return RGCSR_ERR_INVALID_ARG;
+    if (A->row_ptr_type == RGCSR_I32 && A->nnz >= INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
+    if (!valid_value_type(A->value_type)) return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    if (A->n_rows > 0 && !A->row_ptr) return RGCSR_ERR_INVALID_ARG;
+    if (A->nnz > 0 && (!A->col_idx || !A->values)) return RGCSR_ERR_INVALID_ARG;
+    return RGCSR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device-wide exclusive scan of int64 counts, in place (scan.cu).
+// data[0..count) are replaced by their exclusive prefix sums and
+// data[count] receives the total.  Scratch: scan_partials_bytes(count).
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+inline size_t scan_partials_bytes(int64_t count) {
+    return align_up((size_t)(ceil_div(count + 1, kScanTile) + 1) * sizeof(int64_t), 256);
+}
+int exclusive_scan_i64(int64_t *data, int64_t count, int64_t *partials, cudaStream_t s);
+
+// CSR validation (validate.cu): sets bits of *flags (device int) for a bad
+// row pointer (1) or a column outside [0, n_cols) (2); also writes the
+// longest row length to *max_len (device int64, must start at 0).
+int launch_validate_csr(const rgcsr_csr *A, int *flags, int64_t *max_len, cudaStream_t s);
+int launch_row_lengths(const rgcsr_csr *A, int32_t *row_lengths, cudaStream_t s);
+
+}  // namespace rgcsr

@@ -1,0 +1,227 @@
+// spmv.cu -- y = A x for a matrix in Row-grouped CSR (Sec. 3.4 of the paper).
+//
+// Two kernels:
+//  * rgcsr_spmv_paper: the paper's mapping -- one block per group, one thread
+//    per row, the row's slots visited with stride R_g (currentGroupSize).
+//  * rgcsr_spmv_split (default): one thread per row as well, but a warp
+//    first agrees on a split slot j0.  Every row runs its slots [0, j0) on
+//    its own thread (coalesced: the j-th slots of a group's rows are
+//    adjacent), and the slots [j0, len) of the few rows longer than j0 are
+//    then finished by the whole warp, one row at a time, with a shuffle
+//    reduction.  A warp whose rows have similar lengths (the usual case)
+//    skips the split logic: j0 = its longest row.  This removes the
+//    paper's weak point, where one very long row in a group serialises its
+//    warp (Sec. 4.4.2, Table 6: trans4 and Raj1).
+//
+// Loads: value and column slabs are streamed once (evict-first); x is read
+// through the read-only path so it stays cached for reuse (the paper's
+// texture binding of x, Sec. 3.4 and Sec. 4.3).
+#include "common.cuh"
+#include <climits>
+
+namespace rgcsr {
+namespace {
+
+constexpr int kDefaultThreads = 256;
+constexpr int kUnroll = 8;          // slots in flight per thread
+
+template <typename T, bool NC>
+__device__ __forceinline__ T gather(const T *x, int c) {
+    if constexpr (NC) return __ldg(x + c);
+    else return x[c];
+}
+
+template <typename T, bool NC>
+__global__ void rgcsr_spmv_paper(int64_t n, int32_t G, const T *__restrict__ val,
+                                 const int32_t *__restrict__ col, const int64_t *__restrict__ gp,
+                                 const int32_t *__restrict__ rl, const T *__restrict__ x,
+                                 T *__restrict__ y) {
+    const int64_t g = blockIdx.x;
+    const int64_t row = g * G + threadIdx.x;
+    if (row >= n) return;
+    const int R = (int)min((int64_t)G, n - g * G);     // the last group may be smaller
+    int64_t ptr = gp[g] + threadIdx.x;
+    const int len = rl[row];
+    T acc = 0;
+    for (int j = 0; j < len; ++j) {
+        acc += val[ptr] * gather<T, NC>(x, col[ptr]);
+        ptr += R;
+    }
+    y[row] = acc;
+}
+
+// Split slot j0 for an irregular warp: every lane proposes its own row
+// length as j0 and prices it as
+//   4*j0 + w4 * sum_s ceil(max(0, len_s - j0) / 32)
+// (thread-per-row steps plus weighted warp-cooperative steps); the warp
+// takes the cheapest proposal, ties to the smaller j0.
+__device__ __forceinline__ int choose_split(int len, int w4) {
+    int cand = len;
+    long long cost = 4LL * cand;
+#pragma unroll 8
+    for (int s = 0; s < 32; ++s) {
+        int d = __shfl_sync(kFull, len, s) - cand;
+        if (d > 0) cost += (long long)w4 * ((d + 31) >> 5);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        long long oc = __shfl_xor_sync(kFull, cost, o);
+        int ocand = __shfl_xor_sync(kFull, cand, o);
+        if (oc < cost || (oc == cost && ocand < cand)) { cost = oc; cand = ocand; }
+    }
+    return cand;
+}
+
+template <typename T, bool NC>
+__global__ void __launch_bounds__(kDefaultThreads)
+rgcsr_spmv_split(int64_t n, int32_t G, const T *__restrict__ val, const int32_t *__restrict__ col,
+                 const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
+                 const T *__restrict__ x, T *__restrict__ y, int w4) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = row < n;
+    int len = 0, stride = 0;
+    int64_t ptr = 0;
+    if (valid) {
+        const int64_t g = row / G;
+        const int64_t first = g * G;
+        stride = (int)min((int64_t)G, n - first);
+        ptr = __ldg(gp + g) + (row - first);
+        len = __ldg(rl + row);
+    }
+    const int lmax = warp_max_i(len);
+    const int lmin = warp_min_i(valid ? len : INT_MAX);
+    int j0 = lmax;
+    if (lmax - lmin > 32) j0 = choose_split(len, w4);
+
+    // Phase 1: thread per row over slots [0, min(len, j0)).
+    T acc = 0;
+    const int jend = min(len, j0);
+    for (int j = 0; j < jend; j += kUnroll) {
+        T v[kUnroll];
+        int c[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (j + u < jend) {
+                const int64_t p = ptr + (int64_t)(j + u) * stride;
+                v[u] = ld_stream(val + p);
+                c[u] = ld_stream(col + p);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (j + u < jend) acc = fma(v[u], gather<T, NC>(x, c[u]), acc);
+    }
+
+    // Phase 2: the whole warp finishes each row longer than j0.
+    unsigned long_rows = __ballot_sync(kFull, len > j0);
+    while (long_rows) {
+        const int r = __ffs(long_rows) - 1;
+        long_rows &= long_rows - 1;
+        const int Lr = __shfl_sync(kFull, len, r);
+        const int sr = __shfl_sync(kFull, stride, r);
+        const int64_t pr = shfl_i64(ptr, r);
+        T part = 0;
+        for (int j = j0 + lane; j < Lr; j += 32 * kUnroll) {
+            T v[kUnroll];
+            int c[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int jj = j + 32 * u;
+                if (jj < Lr) {
+                    const int64_t p = pr + (int64_t)jj * sr;
+                    v[u] = ld_stream(val + p);
+                    c[u] = ld_stream(col + p);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                if (j + 32 * u < Lr) part = fma(v[u], gather<T, NC>(x, c[u]), part);
+        }
+        part = warp_sum(part);
+        if (lane == r) acc += part;
+    }
+    if (valid) y[row] = acc;
+}
+
+template <typename T>
+int launch_spmv(const rgcsr_matrix *M, const T *x, T *y, const rgcsr_launch *L, cudaStream_t s) {
+    const int kernel = L ? L->kernel : RGCSR_KERNEL_AUTO;
+    const bool nc = !L || L->x_load == RGCSR_XLOAD_NC;
+    const T *val = static_cast<const T *>(M->values);
+    const int64_t n = M->n_rows;
+    const int32_t G = M->group_size;
+    if (kernel == RGCSR_KERNEL_PAPER) {
+        if (G > 1024) return RGCSR_ERR_INVALID_ARG;
+        if (nc)
+            rgcsr_spmv_paper<T, true><<<(unsigned)M->n_groups, G, 0, s>>>(
+                n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y);
+        else
+            rgcsr_spmv_paper<T, false><<<(unsigned)M->n_groups, G, 0, s>>>(
+                n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y);
+        return launch_status();
+    }
+    if (kernel != RGCSR_KERNEL_AUTO && kernel != RGCSR_KERNEL_SPLIT) return RGCSR_ERR_INVALID_ARG;
+    int threads = (L && L->block_threads) ? L->block_threads : kDefaultThreads;
+    if (threads % 32 || threads < 32 || threads > kDefaultThreads) return RGCSR_ERR_INVALID_ARG;
+    const int w4 = (L && L->split_weight > 0) ? L->split_weight : 8;
+    const int64_t blocks = ceil_div(n, threads);
+    if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
+    if (nc)
+        rgcsr_spmv_split<T, true><<<(unsigned)blocks, threads, 0, s>>>(
+            n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y, w4);
+    else
+        rgcsr_spmv_split<T, false><<<(unsigned)blocks, threads, 0, s>>>(
+            n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y, w4);
+    return launch_status();
+}
+
+int check_matrix(const rgcsr_matrix *M) {
+    if (!M || M->n_rows < 0 || M->n_cols < 0 || M->group_size < 1) return RGCSR_ERR_INVALID_ARG;
+    if (M->n_rows == 0) return RGCSR_OK;
+    if (!M->group_ptr || !M->row_lengths) return RGCSR_ERR_INVALID_ARG;
+    if (M->n_stored > 0 && (!M->values || !M->columns)) return RGCSR_ERR_INVALID_ARG;
+    if (M->n_groups != ceil_div(M->n_rows, M->group_size)) return RGCSR_ERR_INVALID_ARG;
+    return RGCSR_OK;
+}
+
+}  // namespace
+}  // namespace rgcsr
+
+using namespace rgcsr;
+
+RGCSR_API int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
+                            const rgcsr_launch *launch, rgcsr_stream_t stream) {
+    int st = check_matrix(M);
+    if (st != RGCSR_OK) return st;
+    if (M->n_rows == 0) return RGCSR_OK;
+    if (!y || (M->n_cols > 0 && !x)) return RGCSR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (M->value_type) {
+        case RGCSR_F64:
+            return launch_spmv<double>(M, static_cast<const double *>(x), static_cast<double *>(y), launch, s);
+        case RGCSR_F32:
+            return launch_spmv<float>(M, static_cast<const float *>(x), static_cast<float *>(y), launch, s);
+        default:
+            return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    }
+}
+
+RGCSR_API int rgcsr_spmv(const rgcsr_matrix *M, const void *x, void *y, rgcsr_stream_t stream) {
+    return rgcsr_spmv_ex(M, x, y, nullptr, stream);
+}
+
+RGCSR_API int rgcsr_spmv_host(const rgcsr_matrix *M, const void *x_host, void *y_host,
+                              void *x_dev, void *y_dev, rgcsr_stream_t stream) {
+    int st = check_matrix(M);
+    if (st != RGCSR_OK) return st;
+    if (M->n_rows == 0) return RGCSR_OK;
+    if (!x_host || !y_host || !x_dev || !y_dev) return RGCSR_ERR_INVALID_ARG;
+    const size_t xb = M->value_type == RGCSR_F64 ? 8 : 4;
+    cudaStream_t s = (cudaStream_t)stream;
+    RGCSR_CUDA_TRY(cudaMemcpyAsync(x_dev, x_host, (size_t)M->n_cols * xb, cudaMemcpyHostToDevice, s));
+    st = rgcsr_spmv(M, x_dev, y_dev, stream);
+    if (st != RGCSR_OK) return st;
+    RGCSR_CUDA_TRY(cudaMemcpyAsync(y_host, y_dev, (size_t)M->n_rows * xb, cudaMemcpyDeviceToHost, s));
+    return RGCSR_OK;
+}

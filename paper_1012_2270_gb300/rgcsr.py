@@ -1,0 +1,226 @@
+"""Row-grouped CSR (RgCSR) and Hybrid ELL+COO matrices on the GPU.
+
+PyTorch provides device memory and streams only: every array is a torch
+tensor that this module allocates from the sizes the library's ``*_plan``
+calls return, and every computation (validation, conversion, SpMV) is a
+call into librgcsr's CUDA kernels on the current torch stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_VT = {torch.float64: L.F64, torch.float32: L.F32}
+
+
+def _stream_ptr(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr() if t is not None and t.numel() > 0 else 0)
+
+
+def _dev(a, dtype=None, device="cuda") -> torch.Tensor:
+    t = torch.as_tensor(np.ascontiguousarray(a)) if isinstance(a, np.ndarray) else a
+    if dtype is not None and t.dtype != dtype:
+        t = t.to(dtype)
+    return t.to(device).contiguous()
+
+
+def csr_struct(rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, n_cols: int) -> L.CSR:
+    if rowptr.dtype not in (torch.int32, torch.int64):
+        raise TypeError("row pointer must be int32 or int64")
+    if col.dtype != torch.int32:
+        raise TypeError("column indices must be int32")
+    if val.dtype not in _VT:
+        raise TypeError("values must be float32 or float64")
+    c = L.CSR()
+    c.n_rows = rowptr.numel() - 1
+    c.n_cols = int(n_cols)
+    c.nnz = col.numel()
+    c.row_ptr = _ptr(rowptr)
+    c.row_ptr_type = L.I64T if rowptr.dtype == torch.int64 else L.I32T
+    c.value_type = _VT[val.dtype]
+    c.col_idx = _ptr(col)
+    c.values = _ptr(val)
+    return c
+
+
+class RgCSRMatrix:
+    """A matrix in Row-grouped CSR (Sec. 3.4 of the paper) on one GPU.
+
+    Attributes are torch tensors: ``values`` [n_stored], ``columns`` int32
+    [n_stored], ``group_ptr`` int64 [n_groups+1], ``row_lengths`` int32
+    [n_rows] and optionally ``slot_to_csr`` int64 [n_stored].
+    """
+
+    def __init__(self):
+        self.s = L.Matrix()
+        self.values = self.columns = self.group_ptr = self.row_lengths = None
+        self.row_scale = None
+        self.slot_to_csr = None
+
+    # -- construction ------------------------------------------------------
+    @classmethod
+    def from_csr(cls, rowptr, col, val, n_cols: int, group_size: int = 32,
+                 dtype: torch.dtype | None = None, keep_slot_map: bool = False,
+                 device="cuda", stream=None) -> "RgCSRMatrix":
+        """Converts a CSR matrix (host numpy or device tensors) to RgCSR.
+
+        ``dtype`` (float32/float64) is the storage type of the values; the
+        CSR values are cast to it before conversion.  Synchronises once."""
+        rowptr = _dev(rowptr, None, device)
+        col = _dev(col, torch.int32, device)
+        val = _dev(val, dtype, device)
+        A = csr_struct(rowptr, col, val, n_cols)
+        self = cls()
+        n = A.n_rows
+        G = int(group_size)
+        if G < 1:
+            raise ValueError("group_size must be >= 1")
+        n_groups = (n + G - 1) // G
+        self.row_lengths = torch.empty(n, dtype=torch.int32, device=device)
+        self.group_ptr = torch.empty(n_groups + 1, dtype=torch.int64, device=device)
+        M = self.s
+        M.group_size = G
+        M.value_type = A.value_type
+        M.row_lengths = _ptr(self.row_lengths)
+        M.group_ptr = _ptr(self.group_ptr)
+        ws_bytes = L.lib().rgcsr_plan_workspace_bytes(n, G)
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=device)
+        st = _stream_ptr(stream)
+        L.call("rgcsr_plan", ctypes.byref(A), ctypes.byref(M), _ptr(ws), ws_bytes, st)
+        self.values = torch.empty(M.n_stored, dtype=val.dtype, device=device)
+        self.columns = torch.empty(M.n_stored, dtype=torch.int32, device=device)
+        M.values = _ptr(self.values)
+        M.columns = _ptr(self.columns)
+        if keep_slot_map:
+            self.slot_to_csr = torch.empty(M.n_stored, dtype=torch.int64, device=device)
+            M.slot_to_csr = _ptr(self.slot_to_csr)
+        L.call("rgcsr_convert", ctypes.byref(A), ctypes.byref(M), st)
+        return self
+
+    # -- properties ----------------------------------------------------------
+    @property
+    def shape(self):
+        return (self.s.n_rows, self.s.n_cols)
+
+    @property
+    def nnz(self) -> int:
+        return self.s.nnz
+
+    @property
+    def n_stored(self) -> int:
+        return self.s.n_stored
+
+    @property
+    def group_size(self) -> int:
+        return self.s.group_size
+
+    @property
+    def max_row_len(self) -> int:
+        return self.s.max_row_len
+
+    @property
+    def dtype(self) -> torch.dtype:
+        return self.values.dtype
+
+    @property
+    def x_dtype(self) -> torch.dtype:
+        return torch.float64 if self.s.value_type == L.F64 else torch.float32
+
+    def artificial_zero_percent(self) -> float:
+        return 100.0 * (self.n_stored - self.nnz) / self.nnz if self.nnz else 0.0
+
+    # -- products --------------------------------------------------------------
+    def spmv(self, x: torch.Tensor, out: torch.Tensor | None = None,
+             kernel: int = L.KERNEL_AUTO, x_load: int = L.XLOAD_NC, block_threads: int = 0,
+             split_weight: int = 0, stream=None) -> torch.Tensor:
+        """y = A x (overwrites ``out`` if given)."""
+        if x.dtype != self.x_dtype or x.numel() != self.s.n_cols or not x.is_contiguous():
+            raise ValueError(f"x must be a contiguous {self.x_dtype} vector of length {self.s.n_cols}")
+        y = out if out is not None else torch.empty(self.s.n_rows, dtype=self.x_dtype, device=x.device)
+        if kernel == L.KERNEL_AUTO and x_load == L.XLOAD_NC and not block_threads and not split_weight:
+            L.call("rgcsr_spmv", ctypes.byref(self.s), _ptr(x), _ptr(y), _stream_ptr(stream))
+        else:
+            ln = L.Launch(kernel, block_threads, x_load, split_weight)
+            L.call("rgcsr_spmv_ex", ctypes.byref(self.s), _ptr(x), _ptr(y), ctypes.byref(ln),
+                   _stream_ptr(stream))
+        return y
+
+    def spmv_host(self, x_host: torch.Tensor, y_host: torch.Tensor, x_dev: torch.Tensor,
+                  y_dev: torch.Tensor, stream=None) -> None:
+        """Host-to-host SpMV through caller-provided device staging buffers."""
+        L.call("rgcsr_spmv_host", ctypes.byref(self.s), _ptr(x_host), _ptr(y_host),
+               _ptr(x_dev), _ptr(y_dev), _stream_ptr(stream))
+
+    def __matmul__(self, x):
+        return self.spmv(x)
+
+
+class HybMatrix:
+    """Hybrid ELLPACK + COO (Sec. 3.3 of the paper) on one GPU."""
+
+    def __init__(self):
+        self.s = L.Hyb()
+        self.ell_val = self.ell_col = self.coo_row = self.coo_col = self.coo_val = None
+
+    @classmethod
+    def from_csr(cls, rowptr, col, val, n_cols: int, ell_width: int = -1,
+                 dtype: torch.dtype | None = None, device="cuda", stream=None) -> "HybMatrix":
+        rowptr = _dev(rowptr, None, device)
+        col = _dev(col, torch.int32, device)
+        val = _dev(val, dtype, device)
+        A = csr_struct(rowptr, col, val, n_cols)
+        self = cls()
+        H = self.s
+        ws_bytes = L.lib().hyb_workspace_bytes(A.n_rows, A.n_cols)
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=device)
+        st = _stream_ptr(stream)
+        L.call("hyb_plan", ctypes.byref(A), int(ell_width), ctypes.byref(H), _ptr(ws), ws_bytes, st)
+        n, K1, nc = H.n_rows, H.ell_width, H.nnz_coo
+        self.ell_val = torch.empty(n * K1, dtype=val.dtype, device=device)
+        self.ell_col = torch.empty(n * K1, dtype=torch.int32, device=device)
+        self.coo_row = torch.empty(nc, dtype=torch.int32, device=device)
+        self.coo_col = torch.empty(nc, dtype=torch.int32, device=device)
+        self.coo_val = torch.empty(nc, dtype=val.dtype, device=device)
+        H.ell_val, H.ell_col = _ptr(self.ell_val), _ptr(self.ell_col)
+        H.coo_row, H.coo_col, H.coo_val = _ptr(self.coo_row), _ptr(self.coo_col), _ptr(self.coo_val)
+        L.call("hyb_convert", ctypes.byref(A), ctypes.byref(H), _ptr(ws), ws_bytes, st)
+        return self
+
+    @property
+    def shape(self):
+        return (self.s.n_rows, self.s.n_cols)
+
+    @property
+    def nnz(self) -> int:
+        return self.s.nnz
+
+    @property
+    def ell_width(self) -> int:
+        return self.s.ell_width
+
+    @property
+    def nnz_coo(self) -> int:
+        return self.s.nnz_coo
+
+    @property
+    def x_dtype(self) -> torch.dtype:
+        return torch.float64 if self.s.value_type == L.F64 else torch.float32
+
+    def spmv(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if x.dtype != self.x_dtype or x.numel() != self.s.n_cols or not x.is_contiguous():
+            raise ValueError(f"x must be a contiguous {self.x_dtype} vector of length {self.s.n_cols}")
+        y = out if out is not None else torch.empty(self.s.n_rows, dtype=self.x_dtype, device=x.device)
+        L.call("hyb_spmv", ctypes.byref(self.s), _ptr(x), _ptr(y), _stream_ptr(stream))
+        return y
+
+    def __matmul__(self, x):
+        return self.spmv(x)

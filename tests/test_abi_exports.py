@@ -1,0 +1,90 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function
+that include/rgcsr.h declares; host-only argument checks answer without a
+GPU (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1012_2270_gb300 import build as B
+from paper_1012_2270_gb300 import _lib as L
+
+HEADER = os.path.join(B.INCLUDE, "rgcsr.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w \*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if not n.startswith("__")))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("rgcsr_plan", "rgcsr_convert", "rgcsr_spmv", "hyb_plan", "hyb_convert", "hyb_spmv"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in L.SIGNATURES, f"binding lacks {name}"
+
+
+def test_only_declared_symbols_are_exported(lib):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    ours = {s for s in exported if s.startswith(("rgcsr_", "hyb_"))}
+    assert ours == set(declared_functions())
+
+
+def test_status_strings_and_version(lib):
+    assert lib.rgcsr_version() >= 100
+    for code in range(-7, 1):
+        assert lib.rgcsr_status_string(code)
+    assert lib.rgcsr_status_string(L.RGCSR_ERR_COL_OOB).decode().startswith("column")
+
+
+def test_workspace_sizes_host_only(lib):
+    assert lib.rgcsr_plan_workspace_bytes(0, 32) > 0
+    a = lib.rgcsr_plan_workspace_bytes(1_000_000, 32)
+    b = lib.rgcsr_plan_workspace_bytes(1_000_000, 1)
+    assert b > a > 0
+    assert lib.rgcsr_plan_workspace_bytes(10, 0) == 0
+    assert lib.hyb_workspace_bytes(1000, 1000) >= 8 * 1001
+
+
+def test_argument_errors_without_gpu(lib):
+    assert lib.rgcsr_plan(None, None, None, 0, None) == L.RGCSR_ERR_INVALID_ARG
+    A = L.CSR(n_rows=-1)
+    M = L.Matrix(group_size=32)
+    assert lib.rgcsr_plan(ctypes.byref(A), ctypes.byref(M), None, 0, None) == L.RGCSR_ERR_INVALID_ARG
+    A = L.CSR(n_rows=4, n_cols=4, nnz=0, row_ptr_type=L.I64T, value_type=L.BF16)
+    assert lib.rgcsr_plan(ctypes.byref(A), ctypes.byref(M), None, 0, None) == L.RGCSR_ERR_UNSUPPORTED_DTYPE
+    A = L.CSR(n_rows=2**31, n_cols=4, nnz=0, row_ptr_type=L.I64T, value_type=L.F32)
+    assert lib.rgcsr_plan(ctypes.byref(A), ctypes.byref(M), None, 0, None) == L.RGCSR_ERR_INDEX_OVERFLOW
+    A = L.CSR(n_rows=4, n_cols=4, nnz=0, row_ptr_type=L.I64T, value_type=L.F32, row_ptr=1)
+    M = L.Matrix(group_size=32, group_ptr=1, row_lengths=1)
+    assert lib.rgcsr_plan(ctypes.byref(A), ctypes.byref(M), None, 0, None) == L.RGCSR_ERR_WORKSPACE
+    # an empty matrix is a no-op
+    M0 = L.Matrix(n_rows=0, n_cols=0, group_size=32, value_type=L.F32)
+    assert lib.rgcsr_spmv(ctypes.byref(M0), None, None, None) == L.RGCSR_OK
+    M1 = L.Matrix(n_rows=4, n_cols=4, group_size=0, value_type=L.F32)
+    assert lib.rgcsr_spmv(ctypes.byref(M1), None, None, None) == L.RGCSR_ERR_INVALID_ARG
+    H = L.Hyb(n_rows=3, n_cols=3, value_type=L.BF16)
+    assert lib.hyb_spmv(ctypes.byref(H), None, None, None) == L.RGCSR_ERR_UNSUPPORTED_DTYPE
+
+
+def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(B, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(L, "_lib", None)
+    with pytest.raises(RuntimeError, match="not found"):
+        L.lib()

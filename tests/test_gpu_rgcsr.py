@@ -1,0 +1,225 @@
+"""GPU parity of the RgCSR path against the CPU oracle, through the C ABI:
+conversion bit-exact (row lengths, group pointers, value bits, columns,
+slot map), SpMV within tau*|A||x| for every kernel variant, edge cases and
+error codes, and the full-size workloads in the benchmark's configuration."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import TAU, assert_within_bound, rounded_values
+from paper_1012_2270_gb300 import synth
+from paper_1012_2270_gb300 import _lib as L
+from paper_1012_2270_gb300.rgcsr import RgCSRMatrix
+
+pytestmark = pytest.mark.gpu
+
+NP = {"f32": np.float32, "f64": np.float64}
+TT = {"f32": torch.float32, "f64": torch.float64}
+VARIANTS = [dict(), dict(kernel=L.KERNEL_PAPER), dict(kernel=L.KERNEL_SPLIT, x_load=L.XLOAD_PLAIN),
+            dict(kernel=L.KERNEL_SPLIT, block_threads=64, split_weight=4)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1012_2270_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def to_gpu_matrix(A, dtype, G, rowptr_i32=False, slot_map=True):
+    rp = A.rowptr.astype(np.int32) if rowptr_i32 else A.rowptr
+    return RgCSRMatrix.from_csr(rp, A.col, A.val.astype(NP[dtype]), A.n_cols, group_size=G,
+                                dtype=TT[dtype], keep_slot_map=slot_map)
+
+
+def check_layout(M, A, dtype, G):
+    lay = oracle.rgcsr_layout(A.rowptr, A.col, A.val.astype(NP[dtype]), G)
+    assert M.n_stored == lay.n_stored
+    assert M.max_row_len == (int(A.row_lengths().max()) if A.n_rows else 0)
+    assert np.array_equal(M.row_lengths.cpu().numpy(), lay.row_lengths)
+    assert np.array_equal(M.group_ptr.cpu().numpy(), lay.group_ptr)
+    assert np.array_equal(M.columns.cpu().numpy(), lay.columns)
+    ui = np.uint64 if dtype == "f64" else np.uint32
+    assert np.array_equal(M.values.cpu().numpy().view(ui), lay.values.view(ui))
+    if M.slot_to_csr is not None:
+        assert np.array_equal(M.slot_to_csr.cpu().numpy(), lay.slot_to_csr)
+
+
+def check_spmv(M, A, dtype, x, **kw):
+    xd = torch.from_numpy(x.astype(NP[dtype])).cuda()
+    y = M.spmv(xd, **kw).cpu().numpy()
+    y_ref, absy = oracle.csr_spmv(A.rowptr, A.col, rounded_values(A.val, dtype),
+                                  rounded_values(x, dtype))
+    assert_within_bound(y, y_ref, absy, TAU[dtype], f"{A.name} {dtype} {kw}")
+
+
+def ragged(n, m, seed, maxlen=40, long_rows=()):
+    rng = np.random.default_rng(seed)
+    L_ = rng.integers(0, maxlen, n)
+    for r, l in long_rows:
+        L_[r] = l
+    return synth.random_csr(n, m, L_, seed=seed)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("G", [1, 3, 8, 32, 33, 64, 128, 256])
+def test_layout_bit_exact_and_spmv_ragged(dtype, G):
+    A = ragged(1000, 700, seed=G, long_rows=[(5, 650), (517, 300)])  # tail group partial
+    M = to_gpu_matrix(A, dtype, G)
+    check_layout(M, A, dtype, G)
+    x = synth.uniform_vector(A.n_cols, seed=1)
+    for kw in VARIANTS:
+        if kw.get("kernel") == L.KERNEL_PAPER and G > 1024:
+            continue
+        check_spmv(M, A, dtype, x, **kw)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_small_laplacian_int32_rowptr(dtype):
+    A = synth.workload_small_laplacian()
+    M = to_gpu_matrix(A, dtype, 32, rowptr_i32=True)
+    check_layout(M, A, dtype, 32)
+    x = synth.uniform_vector(A.n_cols, seed=0)
+    for kw in VARIANTS:
+        check_spmv(M, A, dtype, x, **kw)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_long_rows_and_rectangular(dtype):
+    # one row of 10,000 in a group of short rows, several long rows in one
+    # warp, a completely empty warp, and n_cols != n_rows
+    rng = np.random.default_rng(7)
+    n, m = 5000, 12000
+    L_ = rng.integers(0, 6, n)
+    L_[100] = 10000
+    L_[200:204] = [3000, 2500, 40, 9000]
+    L_[4000:4032] = 0
+    A = synth.random_csr(n, m, L_, seed=7)
+    M = to_gpu_matrix(A, dtype, 32)
+    check_layout(M, A, dtype, 32)
+    x = synth.uniform_vector(m, seed=3)
+    for kw in VARIANTS:
+        check_spmv(M, A, dtype, x, **kw)
+
+
+def test_padding_never_multiplied_nan_canary():
+    # padding carries column 0; x[0] = NaN must not reach rows that do not
+    # reference column 0
+    rng = np.random.default_rng(11)
+    A = synth.random_csr(300, 50, rng.integers(0, 20, 300), seed=11)
+    keep = A.col != 0
+    rows = np.repeat(np.arange(300), A.row_lengths())[keep]
+    rowptr = np.zeros(301, np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    B = synth.CSRMatrix(300, 50, rowptr, A.col[keep], A.val[keep], "no_col0")
+    x = synth.uniform_vector(50, seed=2)
+    x[0] = np.nan
+    for dtype in ("f32", "f64"):
+        M = to_gpu_matrix(B, dtype, 32)
+        assert M.n_stored > M.nnz                  # there is padding
+        xd = torch.from_numpy(x.astype(NP[dtype])).cuda()
+        for kw in VARIANTS:
+            assert torch.isfinite(M.spmv(xd, **kw)).all(), kw
+
+
+def test_empty_cases():
+    for n, m in [(0, 0), (0, 5), (7, 0), (64, 64)]:
+        A = synth.random_csr(n, m, np.zeros(n, np.int64))
+        M = to_gpu_matrix(A, "f32", 32)
+        assert M.n_stored == 0 and M.nnz == 0
+        y = M.spmv(torch.zeros(m, dtype=torch.float32, device="cuda"))
+        assert y.shape == (n,) and (y == 0).all()
+
+
+def test_error_codes_from_validation():
+    A = ragged(100, 50, seed=1)
+    col = A.col.copy()
+    col[17] = 50                                    # out of range
+    with pytest.raises(L.RgCSRError) as e:
+        RgCSRMatrix.from_csr(A.rowptr, col, A.val, 50, dtype=torch.float32)
+    assert e.value.status == L.RGCSR_ERR_COL_OOB
+    rp = A.rowptr.copy()
+    rp[10], rp[11] = rp[11], rp[10] - 1             # decreasing
+    with pytest.raises(L.RgCSRError) as e:
+        RgCSRMatrix.from_csr(rp, A.col, A.val, 50, dtype=torch.float32)
+    assert e.value.status == L.RGCSR_ERR_BAD_ROWPTR
+    rp = A.rowptr.copy()
+    rp[-1] -= 1                                     # row_ptr[n] != nnz
+    with pytest.raises(L.RgCSRError) as e:
+        RgCSRMatrix.from_csr(rp, A.col, A.val, 50, dtype=torch.float32)
+    assert e.value.status == L.RGCSR_ERR_BAD_ROWPTR
+
+
+def test_identity_diagonal_permutation_exact():
+    n = 4099
+    rng = np.random.default_rng(0)
+    x = rng.uniform(-1, 1, n)
+    d = rng.uniform(-2, 2, n)
+    perm = rng.permutation(n).astype(np.int32)
+    rp = np.arange(n + 1)
+    for dtype in ("f32", "f64"):
+        xd = torch.from_numpy(x.astype(NP[dtype])).cuda()
+        M = RgCSRMatrix.from_csr(rp, perm, np.ones(n), n, dtype=TT[dtype])
+        assert np.array_equal(M.spmv(xd).cpu().numpy(), x.astype(NP[dtype])[perm])
+        M = RgCSRMatrix.from_csr(rp, np.arange(n, dtype=np.int32), d, n, dtype=TT[dtype])
+        assert np.array_equal(M.spmv(xd).cpu().numpy(), d.astype(NP[dtype]) * x.astype(NP[dtype]))
+
+
+def test_host_entry_point_matches_device():
+    A = ragged(3000, 3000, seed=5)
+    M = to_gpu_matrix(A, "f32", 32)
+    x = synth.uniform_vector(3000, seed=4).astype(np.float32)
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.empty(3000, dtype=torch.float32).pin_memory()
+    xd = torch.empty(3000, dtype=torch.float32, device="cuda")
+    yd = torch.empty(3000, dtype=torch.float32, device="cuda")
+    M.spmv_host(xh, yh, xd, yd)
+    torch.cuda.synchronize()
+    assert torch.equal(yh, M.spmv(torch.from_numpy(x).cuda()).cpu())
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads, group size 32 and the default kernel (as benchmarked)
+# ---------------------------------------------------------------------------
+FULL = {"a": synth.workload_a, "b": synth.workload_b, "c": synth.workload_c}
+
+
+@pytest.mark.parametrize("name", ["a", "b", "c"])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_full_size_spmv(name, dtype):
+    A = FULL[name]()
+    M = to_gpu_matrix(A, dtype, 32, slot_map=False)
+    rl, gp = oracle_sizes(A, 32)
+    assert np.array_equal(M.group_ptr.cpu().numpy(), gp)
+    assert np.array_equal(M.row_lengths.cpu().numpy(), rl)
+    sample_groups_bit_exact(M, A, dtype, 32, seed=0)
+    x = synth.uniform_vector(A.n_cols, seed=0)
+    check_spmv(M, A, dtype, x)
+
+
+def oracle_sizes(A, G):
+    return oracle.rgcsr_sizes(A.rowptr, G)
+
+
+def sample_groups_bit_exact(M, A, dtype, G, seed, count=300):
+    """Oracle layout of sampled groups (each rebuilt from its own rows)."""
+    rng = np.random.default_rng(seed)
+    n_groups = (A.n_rows + G - 1) // G
+    rl = A.row_lengths()
+    picks = set(rng.integers(0, n_groups, count).tolist())
+    picks.add(n_groups - 1)
+    picks.add(int(np.argmax(rl)) // G)
+    gp = M.group_ptr.cpu().numpy()
+    vals = M.values.cpu().numpy()
+    cols = M.columns.cpu().numpy()
+    ui = np.uint64 if dtype == "f64" else np.uint32
+    for g in sorted(picks):
+        r0, r1 = g * G, min(A.n_rows, (g + 1) * G)
+        p0, p1 = A.rowptr[r0], A.rowptr[r1]
+        sub_rp = A.rowptr[r0:r1 + 1] - p0
+        lay = oracle.rgcsr_layout(sub_rp, A.col[p0:p1], A.val[p0:p1].astype(NP[dtype]), G)
+        assert lay.n_stored == gp[g + 1] - gp[g]
+        assert np.array_equal(cols[gp[g]:gp[g + 1]], lay.columns)
+        assert np.array_equal(vals[gp[g]:gp[g + 1]].view(ui), lay.values.view(ui))
