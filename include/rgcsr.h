@@ -117,6 +117,27 @@ int rgcsr_plan(const rgcsr_csr *A, rgcsr_matrix *M, void *workspace,
                size_t workspace_bytes, rgcsr_stream_t stream);
 int rgcsr_convert(const rgcsr_csr *A, const rgcsr_matrix *M, rgcsr_stream_t stream);
 
+/* rgcsr_plan without a workspace argument, for callers that cannot
+ * allocate device memory: code that only receives device pointers from
+ * another component and has no allocator of its own, or that runs where a
+ * cudaMalloc/cudaFree (each of which may synchronise the whole device) is
+ * not acceptable, e.g. inside a framework whose caching allocator owns all
+ * device memory.  The paper has no counterpart; it is an interface variant.
+ *
+ * Same inputs, outputs, validation and stream synchronisation as
+ * rgcsr_plan.  The scratch is one fixed array of RGCSR_PLAN_NOALLOC_SCRATCH_BYTES
+ * inside the library, present on every GPU that loads the library until the
+ * process exits; the call allocates nothing.  It serves matrices whose
+ * rgcsr_plan_workspace_bytes(n_rows, group_size) fits in that array (up to
+ * 16,709,631 groups, i.e. about 534 million rows at G = 32); larger ones
+ * return RGCSR_ERR_WORKSPACE without touching the device.
+ * The first call on a device looks up the array's device address for that
+ * (current) device; make that first call before any stream capture.
+ * All calls share the one array: calls whose GPU work overlaps (several
+ * host threads or streams at once) race on it and must be serialised. */
+#define RGCSR_PLAN_NOALLOC_SCRATCH_BYTES 65536
+int rgcsr_plan_noalloc(const rgcsr_csr *A, rgcsr_matrix *M, rgcsr_stream_t stream);
+
 /* ----------------------------------------------------------------------- */
 /* SpMV y = A x on an RgCSR matrix (Sec. 3.4 kernel; peak model of the     */
 /* same section).  x: n_cols elements, y: n_rows elements; F64 storage     */

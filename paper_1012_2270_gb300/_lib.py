@@ -58,6 +58,7 @@ SIGNATURES = {
     "rgcsr_plan_workspace_bytes": (SZ, [I64, I32]),
     "rgcsr_plan": (ctypes.c_int, [_PCSR, _PM, P, SZ, P]),
     "rgcsr_convert": (ctypes.c_int, [_PCSR, _PM, P]),
+    "rgcsr_plan_noalloc": (ctypes.c_int, [_PCSR, _PM, P]),
     "rgcsr_spmv": (ctypes.c_int, [_PM, P, P, P]),
     "rgcsr_spmv_ex": (ctypes.c_int, [_PM, P, P, _PL, P]),
     "rgcsr_spmv_host": (ctypes.c_int, [_PM, P, P, P, P, P]),
