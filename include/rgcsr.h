@@ -87,10 +87,20 @@ typedef struct {
 } rgcsr_matrix;
 
 /* Kernel selection for rgcsr_spmv_ex (autotuning and ablations). */
-#define RGCSR_KERNEL_AUTO   0    /* default: warp-split kernel                     */
+#define RGCSR_KERNEL_AUTO   0    /* default: when the groups are dense (padding <=
+                                    25% of the stored slots) the TMA kernel (FP32,
+                                    or FP64 with <= 8 entries per row on average)
+                                    or else the LEAN kernel; otherwise the warp-split
+                                    kernel                                          */
 #define RGCSR_KERNEL_PAPER  1    /* one block per group, one thread per row (Sec. 3.4 listing) */
 #define RGCSR_KERNEL_SPLIT  2    /* one thread per row; long rows of a warp finished
                                     by the whole warp with a shuffle reduction      */
+#define RGCSR_KERNEL_TMA    3    /* G == 32 only: group slabs staged in shared memory by
+                                    bulk copies (cp.async.bulk), one warp per group,
+                                    persistent grid; needs 16-byte aligned values,
+                                    columns and row_lengths and n_rows >= 32       */
+#define RGCSR_KERNEL_LEAN   4    /* one thread per row, no long-row split, sized for
+                                    full occupancy (rows of similar lengths)        */
 #define RGCSR_XLOAD_NC      0    /* x through the read-only (non-coherent) path    */
 #define RGCSR_XLOAD_PLAIN   1    /* x with ordinary global loads                   */
 typedef struct {
@@ -99,6 +109,10 @@ typedef struct {
     int32_t x_load;             /* RGCSR_XLOAD_*                                   */
     int32_t split_weight;       /* 0 = default; cost of one warp-cooperative step
                                    relative to one thread-per-row step, x 4        */
+    int32_t variant;            /* configuration of the chosen kernel, 0 = default:
+                                   TMA: 0..3 = (slot-rows per chunk, ring stages)
+                                   (8,2), (8,4), (16,2), (4,4); LEAN: 0..1 = 4 or 8
+                                   slots in flight per thread                     */
 } rgcsr_launch;
 
 /* ----------------------------------------------------------------------- */
@@ -194,6 +208,12 @@ int hyb_spmv(const hyb_matrix *H, const void *x, void *y, rgcsr_stream_t stream)
 /* ----------------------------------------------------------------------- */
 /* Misc                                                                     */
 /* ----------------------------------------------------------------------- */
+/* Device-side error bits, sticky until read: RGCSR_STATUS_TIMEOUT means a
+ * kernel gave up waiting for a bulk copy (after ~1 s) and left some rows of
+ * its output unwritten.  rgcsr_get_status copies the bits of the current
+ * device to *status_out and clears them; synchronises `stream`. */
+#define RGCSR_STATUS_TIMEOUT 1
+int rgcsr_get_status(int *status_out, rgcsr_stream_t stream);
 const char *rgcsr_status_string(int status);
 /* Library version as major*10000 + minor*100 + patch. */
 int rgcsr_version(void);

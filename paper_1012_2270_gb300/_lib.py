@@ -22,7 +22,8 @@ RGCSR_ERR_WORKSPACE = -7
 
 F64, F32, BF16, F16, I32T, I64T = 0, 1, 2, 3, 4, 5
 
-KERNEL_AUTO, KERNEL_PAPER, KERNEL_SPLIT = 0, 1, 2
+KERNEL_AUTO, KERNEL_PAPER, KERNEL_SPLIT, KERNEL_TMA, KERNEL_LEAN = 0, 1, 2, 3, 4
+STATUS_TIMEOUT = 1
 XLOAD_NC, XLOAD_PLAIN = 0, 1
 
 
@@ -41,7 +42,8 @@ class Matrix(ctypes.Structure):
 
 
 class Launch(ctypes.Structure):
-    _fields_ = [("kernel", I32), ("block_threads", I32), ("x_load", I32), ("split_weight", I32)]
+    _fields_ = [("kernel", I32), ("block_threads", I32), ("x_load", I32), ("split_weight", I32),
+                ("variant", I32)]
 
 
 class Hyb(ctypes.Structure):
@@ -66,6 +68,7 @@ SIGNATURES = {
     "hyb_plan": (ctypes.c_int, [_PCSR, I32, _PH, P, SZ, P]),
     "hyb_convert": (ctypes.c_int, [_PCSR, _PH, P, SZ, P]),
     "hyb_spmv": (ctypes.c_int, [_PH, P, P, P]),
+    "rgcsr_get_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), P]),
     "rgcsr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rgcsr_version": (ctypes.c_int, []),
 }

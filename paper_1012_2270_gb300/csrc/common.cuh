@@ -115,4 +115,8 @@ int exclusive_scan_i64(int64_t *data, int64_t count, int64_t *partials, cudaStre
 int launch_validate_csr(const rgcsr_csr *A, int *flags, int64_t *max_len, cudaStream_t s);
 int launch_row_lengths(const rgcsr_csr *A, int32_t *row_lengths, cudaStream_t s);
 
+// TMA-staged SpMV for G = 32 (spmv_tma.cu).
+bool tma_eligible(const rgcsr_matrix *M);
+int launch_spmv_tma(const rgcsr_matrix *M, const void *x, void *y, int variant, cudaStream_t s);
+
 }  // namespace rgcsr

@@ -1,6 +1,6 @@
 // spmv.cu -- y = A x for a matrix in Row-grouped CSR (Sec. 3.4 of the paper).
 //
-// Two kernels:
+// Two kernels here (the TMA-staged kernel for G = 32 is in spmv_tma.cu):
 //  * rgcsr_spmv_paper: the paper's mapping -- one block per group, one thread
 //    per row, the row's slots visited with stride R_g (currentGroupSize).
 //  * rgcsr_spmv_split (default): one thread per row as well, but a warp
@@ -144,6 +144,44 @@ rgcsr_spmv_split(int64_t n, int32_t G, const T *__restrict__ val, const int32_t 
     if (valid) y[row] = acc;
 }
 
+// One thread per row and no long-row split, sized for full occupancy
+// (FP32: <= 32 registers, 64 warps per SM; FP64: 48 warps per SM) so that
+// enough loads stay in flight.  For
+// matrices whose rows within a warp have similar lengths.
+template <typename T, int U, int MIN_BLOCKS>
+__global__ void __launch_bounds__(kDefaultThreads, MIN_BLOCKS)
+rgcsr_spmv_lean(int64_t n, int32_t G, const T *__restrict__ val, const int32_t *__restrict__ col,
+                const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
+                const T *__restrict__ x, T *__restrict__ y) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    const int64_t g = row / G;
+    const int64_t first = g * G;
+    const int stride = (int)min((int64_t)G, n - first);
+    const int64_t off = __ldg(gp + g) + (row - first);
+    const T *vp = val + off;
+    const int32_t *cp = col + off;
+    const int len = __ldg(rl + row);
+    T acc = 0;
+    for (int j = 0; j < len; j += U) {
+        T v[U];
+        int c[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (j + u < len) {
+                v[u] = ld_stream(vp + (int64_t)u * stride);
+                c[u] = ld_stream(cp + (int64_t)u * stride);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (j + u < len) acc = fma(v[u], __ldg(x + c[u]), acc);
+        vp += (int64_t)U * stride;
+        cp += (int64_t)U * stride;
+    }
+    y[row] = acc;
+}
+
 template <typename T>
 int launch_spmv(const rgcsr_matrix *M, const T *x, T *y, const rgcsr_launch *L, cudaStream_t s) {
     const int kernel = L ? L->kernel : RGCSR_KERNEL_AUTO;
@@ -151,6 +189,20 @@ int launch_spmv(const rgcsr_matrix *M, const T *x, T *y, const rgcsr_launch *L, 
     const T *val = static_cast<const T *>(M->values);
     const int64_t n = M->n_rows;
     const int32_t G = M->group_size;
+    if (kernel == RGCSR_KERNEL_LEAN) {
+        const int64_t blocks = ceil_div(n, kDefaultThreads);
+        if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
+        const int variant = L ? L->variant : 0;
+        if (variant == 0)
+            rgcsr_spmv_lean<T, 4, (sizeof(T) == 4 ? 8 : 6)><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
+                n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y);
+        else if (variant == 1)
+            rgcsr_spmv_lean<T, 8, (sizeof(T) == 4 ? 6 : 4)><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
+                n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y);
+        else
+            return RGCSR_ERR_INVALID_ARG;
+        return launch_status();
+    }
     if (kernel == RGCSR_KERNEL_PAPER) {
         if (G > 1024) return RGCSR_ERR_INVALID_ARG;
         if (nc)
@@ -197,6 +249,28 @@ RGCSR_API int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
     if (M->n_rows == 0) return RGCSR_OK;
     if (!y || (M->n_cols > 0 && !x)) return RGCSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    int kernel = launch ? launch->kernel : RGCSR_KERNEL_AUTO;
+    if (kernel == RGCSR_KERNEL_AUTO) {
+        // Dense groups (padding <= 25% of the stored slots): the TMA-staged
+        // kernel for FP32 and for short FP64 rows, the full-occupancy
+        // thread-per-row kernel for long FP64 rows; anything else (uneven
+        // rows, long rows) takes the warp-split kernel.
+        const bool dense = M->n_stored * 4 <= M->nnz * 5;
+        const bool short_rows = M->nnz <= 8 * M->n_rows;
+        if (dense && tma_eligible(M) && (M->value_type == RGCSR_F32 || short_rows))
+            kernel = RGCSR_KERNEL_TMA;
+        else if (dense)
+            kernel = RGCSR_KERNEL_LEAN;
+        else
+            kernel = RGCSR_KERNEL_SPLIT;
+    }
+    if (kernel == RGCSR_KERNEL_TMA) {
+        if (!tma_eligible(M)) return RGCSR_ERR_INVALID_ARG;
+        return launch_spmv_tma(M, x, y, launch ? launch->variant : 0, s);
+    }
+    rgcsr_launch resolved = launch ? *launch : rgcsr_launch{};
+    resolved.kernel = kernel;
+    launch = &resolved;
     switch (M->value_type) {
         case RGCSR_F64:
             return launch_spmv<double>(M, static_cast<const double *>(x), static_cast<double *>(y), launch, s);

@@ -141,15 +141,16 @@ class RgCSRMatrix:
     # -- products --------------------------------------------------------------
     def spmv(self, x: torch.Tensor, out: torch.Tensor | None = None,
              kernel: int = L.KERNEL_AUTO, x_load: int = L.XLOAD_NC, block_threads: int = 0,
-             split_weight: int = 0, stream=None) -> torch.Tensor:
+             split_weight: int = 0, variant: int = 0, stream=None) -> torch.Tensor:
         """y = A x (overwrites ``out`` if given)."""
         if x.dtype != self.x_dtype or x.numel() != self.s.n_cols or not x.is_contiguous():
             raise ValueError(f"x must be a contiguous {self.x_dtype} vector of length {self.s.n_cols}")
         y = out if out is not None else torch.empty(self.s.n_rows, dtype=self.x_dtype, device=x.device)
-        if kernel == L.KERNEL_AUTO and x_load == L.XLOAD_NC and not block_threads and not split_weight:
+        if (kernel == L.KERNEL_AUTO and x_load == L.XLOAD_NC and not block_threads
+                and not split_weight and not variant):
             L.call("rgcsr_spmv", ctypes.byref(self.s), _ptr(x), _ptr(y), _stream_ptr(stream))
         else:
-            ln = L.Launch(kernel, block_threads, x_load, split_weight)
+            ln = L.Launch(kernel, block_threads, x_load, split_weight, variant)
             L.call("rgcsr_spmv_ex", ctypes.byref(self.s), _ptr(x), _ptr(y), ctypes.byref(ln),
                    _stream_ptr(stream))
         return y

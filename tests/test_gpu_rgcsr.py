@@ -17,7 +17,28 @@ pytestmark = pytest.mark.gpu
 NP = {"f32": np.float32, "f64": np.float64}
 TT = {"f32": torch.float32, "f64": torch.float64}
 VARIANTS = [dict(), dict(kernel=L.KERNEL_PAPER), dict(kernel=L.KERNEL_SPLIT, x_load=L.XLOAD_PLAIN),
-            dict(kernel=L.KERNEL_SPLIT, block_threads=64, split_weight=4)]
+            dict(kernel=L.KERNEL_SPLIT, block_threads=64, split_weight=4), dict(kernel=L.KERNEL_LEAN)]
+VARIANTS += [dict(kernel=L.KERNEL_TMA, variant=v) for v in range(0, 4)]
+VARIANTS += [dict(kernel=L.KERNEL_LEAN, variant=1)]
+
+
+def variants(M):
+    """Kernel variants valid for M (the TMA kernel needs G = 32, n >= 32)."""
+    out = []
+    for kw in VARIANTS:
+        if kw.get("kernel") == L.KERNEL_TMA and (M.group_size != 32 or M.shape[0] < 32):
+            continue
+        if kw.get("kernel") == L.KERNEL_PAPER and M.group_size > 1024:
+            continue
+        out.append(kw)
+    return out
+
+
+def device_status():
+    import ctypes
+    st = ctypes.c_int(-1)
+    L.call("rgcsr_get_status", ctypes.byref(st), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return st.value
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -69,9 +90,7 @@ def test_layout_bit_exact_and_spmv_ragged(dtype, G):
     M = to_gpu_matrix(A, dtype, G)
     check_layout(M, A, dtype, G)
     x = synth.uniform_vector(A.n_cols, seed=1)
-    for kw in VARIANTS:
-        if kw.get("kernel") == L.KERNEL_PAPER and G > 1024:
-            continue
+    for kw in variants(M):
         check_spmv(M, A, dtype, x, **kw)
 
 
@@ -81,7 +100,7 @@ def test_small_laplacian_int32_rowptr(dtype):
     M = to_gpu_matrix(A, dtype, 32, rowptr_i32=True)
     check_layout(M, A, dtype, 32)
     x = synth.uniform_vector(A.n_cols, seed=0)
-    for kw in VARIANTS:
+    for kw in variants(M):
         check_spmv(M, A, dtype, x, **kw)
 
 
@@ -99,7 +118,7 @@ def test_long_rows_and_rectangular(dtype):
     M = to_gpu_matrix(A, dtype, 32)
     check_layout(M, A, dtype, 32)
     x = synth.uniform_vector(m, seed=3)
-    for kw in VARIANTS:
+    for kw in variants(M):
         check_spmv(M, A, dtype, x, **kw)
 
 
@@ -120,7 +139,7 @@ def test_padding_never_multiplied_nan_canary():
         M = to_gpu_matrix(B, dtype, 32)
         assert M.n_stored > M.nnz                  # there is padding
         xd = torch.from_numpy(x.astype(NP[dtype])).cuda()
-        for kw in VARIANTS:
+        for kw in variants(M):
             assert torch.isfinite(M.spmv(xd, **kw)).all(), kw
 
 
@@ -197,6 +216,10 @@ def test_full_size_spmv(name, dtype):
     sample_groups_bit_exact(M, A, dtype, 32, seed=0)
     x = synth.uniform_vector(A.n_cols, seed=0)
     check_spmv(M, A, dtype, x)
+    if name != "b":
+        check_spmv(M, A, dtype, x, kernel=L.KERNEL_SPLIT)
+    check_spmv(M, A, dtype, x, kernel=L.KERNEL_TMA)
+    assert device_status() == 0
 
 
 def oracle_sizes(A, G):
@@ -223,3 +246,18 @@ def sample_groups_bit_exact(M, A, dtype, G, seed, count=300):
         assert lay.n_stored == gp[g + 1] - gp[g]
         assert np.array_equal(cols[gp[g]:gp[g + 1]], lay.columns)
         assert np.array_equal(vals[gp[g]:gp[g + 1]].view(ui), lay.values.view(ui))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("n", [32, 33, 63, 64, 65, 4095, 100_003])
+def test_tma_sizes_and_partial_group(dtype, n):
+    # 7-point-like rows with a few longer ones (chunked beyond CAP slot-rows)
+    rng = np.random.default_rng(n)
+    L_ = rng.integers(5, 8, n)
+    L_[rng.integers(0, n, 3)] = rng.integers(20, 60, 3)
+    A = synth.random_csr(n, max(n, 64), L_, seed=n)
+    M = to_gpu_matrix(A, dtype, 32, slot_map=False)
+    x = synth.uniform_vector(A.n_cols, seed=5)
+    check_spmv(M, A, dtype, x, kernel=L.KERNEL_TMA)
+    check_spmv(M, A, dtype, x)
+    assert device_status() == 0
