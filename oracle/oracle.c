@@ -291,6 +291,10 @@ float orc_row_scale(double maxabs)
     double m = frexp(maxabs, &e);         /* maxabs = m * 2^e, m in [0.5, 1) */
     /* ceil(log2(maxabs)) is e-1 when maxabs is a power of two, else e */
     int c = (m == 0.5) ? e - 1 : e;
+    /* the scale is stored as a binary32 number: its exponent is kept in the
+       normal range [-126, 127] so that it is finite, non-zero and exact */
+    if (c < -126) c = -126;
+    if (c > 127) c = 127;
     return (float)ldexp(1.0, c);
 }
 

@@ -10,7 +10,10 @@ import oracle
 
 @pytest.mark.parametrize("mx,s", [(0.0, 1.0), (1.0, 1.0), (0.75, 1.0), (1.5, 2.0), (3.0, 4.0),
                                   (4.0, 4.0), (4.000001, 8.0), (1e-3, 2.0 ** -9),
-                                  (2.0 ** -20, 2.0 ** -20), (6.0, 8.0), (1e30, 2.0 ** 100)])
+                                  (2.0 ** -20, 2.0 ** -20), (6.0, 8.0), (1e30, 2.0 ** 100),
+                                  # exponent clamped to the binary32 normal range
+                                  (1e-45, 2.0 ** -126), (2.0 ** -126, 2.0 ** -126),
+                                  (2.0 ** 127, 2.0 ** 127), (1e300, 2.0 ** 127)])
 def test_row_scale_closed_form(mx, s):
     assert oracle.row_scale(mx) == s
 
