@@ -111,8 +111,7 @@ typedef struct {
                                    relative to one thread-per-row step, x 4        */
     int32_t variant;            /* configuration of the chosen kernel, 0 = default:
                                    TMA: 0..3 = (slot-rows per chunk, ring stages)
-                                   (8,2), (8,4), (16,2), (4,4); LEAN: 0..1 = 4 or 8
-                                   slots in flight per thread                     */
+                                   (8,2), (8,4), (16,2), (4,4); other kernels: 0 */
 } rgcsr_launch;
 
 /* ----------------------------------------------------------------------- */
@@ -168,6 +167,23 @@ int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
  * the copies asynchronous; the caller synchronises before reading y_host. */
 int rgcsr_spmv_host(const rgcsr_matrix *M, const void *x_host, void *y_host,
                     void *x_dev, void *y_dev, rgcsr_stream_t stream);
+
+/* ----------------------------------------------------------------------- */
+/* Reduced-precision value storage (not in the paper, which stores single  */
+/* or double precision).  Per row i the scale is                            */
+/*   s_i = 2^ceil(log2 max_j |a_ij|)  (1 for an empty or all-zero row,     */
+/*         exponent clamped to the binary32 normal range [-126, 127]),      */
+/* and each stored value becomes q_ij = round-to-nearest-even(a_ij / s_i)  */
+/* in bfloat16 (RGCSR_BF16) or IEEE binary16 (RGCSR_F16), computed from the */
+/* exact double quotient, subnormals kept; padding becomes +0.  The SpMV of */
+/* such a matrix computes y_i = s_i * sum_j q_ij x_j in float.              */
+/*                                                                          */
+/* src: an F64 or F32 matrix.  dst: dst->value_type (BF16/F16), dst->values */
+/* (n_stored 2-byte elements) and dst->row_scale (n_rows floats) allocated  */
+/* by the caller; dst->columns, group_ptr and row_lengths normally point to */
+/* src's arrays.  The size fields of dst are copied from src.  Async.      */
+/* ----------------------------------------------------------------------- */
+int rgcsr_quantize(const rgcsr_matrix *src, rgcsr_matrix *dst, rgcsr_stream_t stream);
 
 /* ----------------------------------------------------------------------- */
 /* Hybrid ELLPACK + COO (Sec. 3.3), the paper's comparison format.  The ELL */

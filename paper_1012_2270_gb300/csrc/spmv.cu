@@ -1,23 +1,31 @@
 // spmv.cu -- y = A x for a matrix in Row-grouped CSR (Sec. 3.4 of the paper).
 //
-// Two kernels here (the TMA-staged kernel for G = 32 is in spmv_tma.cu):
+// Kernels here (the TMA-staged kernel for G = 32 is in spmv_tma.cu):
 //  * rgcsr_spmv_paper: the paper's mapping -- one block per group, one thread
 //    per row, the row's slots visited with stride R_g (currentGroupSize).
-//  * rgcsr_spmv_split (default): one thread per row as well, but a warp
-//    first agrees on a split slot j0.  Every row runs its slots [0, j0) on
-//    its own thread (coalesced: the j-th slots of a group's rows are
-//    adjacent), and the slots [j0, len) of the few rows longer than j0 are
-//    then finished by the whole warp, one row at a time, with a shuffle
-//    reduction.  A warp whose rows have similar lengths (the usual case)
-//    skips the split logic: j0 = its longest row.  This removes the
-//    paper's weak point, where one very long row in a group serialises its
-//    warp (Sec. 4.4.2, Table 6: trans4 and Raj1).
+//  * rgcsr_spmv_split: one thread per row, but a warp first agrees on a
+//    split slot j0.  Every row runs its slots [0, j0) on its own thread
+//    (coalesced: the j-th slots of a group's rows are adjacent), and the
+//    slots [j0, len) of the few rows longer than j0 are then finished by the
+//    whole warp, one row at a time, with a shuffle reduction.  A warp whose
+//    rows have similar lengths skips the split logic (j0 = its longest row).
+//    This removes the paper's weak point, where one very long row in a
+//    group serialises its warp (Sec. 4.4.2, Table 6: trans4 and Raj1).
+//  * rgcsr_spmv_lean: one thread per row, no split, sized for full
+//    occupancy; for matrices whose rows in a warp have similar lengths.
+//
+// Value storage V is double, float, or (reduced storage, not in the paper)
+// bfloat16 / half with a per-row float scale: y_i = s_i * sum_j q_ij x_j
+// with x, y and the sum in float.
 //
 // Loads: value and column slabs are streamed once (evict-first); x is read
 // through the read-only path so it stays cached for reuse (the paper's
 // texture binding of x, Sec. 3.4 and Sec. 4.3).
 #include "common.cuh"
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <climits>
+#include <type_traits>
 
 namespace rgcsr {
 namespace {
@@ -25,10 +33,39 @@ namespace {
 constexpr int kDefaultThreads = 256;
 constexpr int kUnroll = 8;          // slots in flight per thread
 
-template <typename T, bool NC>
-__device__ __forceinline__ T gather(const T *x, int c) {
+// Storage type V -> arithmetic type A, streaming load, per-row scale flag.
+template <typename V> struct VT;
+template <> struct VT<double> {
+    using A = double;
+    static constexpr bool scaled = false;
+    static __device__ __forceinline__ double ld(const double *p) { return __ldcs(p); }
+};
+template <> struct VT<float> {
+    using A = float;
+    static constexpr bool scaled = false;
+    static __device__ __forceinline__ float ld(const float *p) { return __ldcs(p); }
+};
+template <> struct VT<__nv_bfloat16> {
+    using A = float;
+    static constexpr bool scaled = true;
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldcs(p)); }
+};
+template <> struct VT<__half> {
+    using A = float;
+    static constexpr bool scaled = true;
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldcs(p)); }
+};
+
+template <typename A, bool NC>
+__device__ __forceinline__ A gather(const A *x, int c) {
     if constexpr (NC) return __ldg(x + c);
     else return x[c];
+}
+
+template <typename V>
+__device__ __forceinline__ typename VT<V>::A finish(typename VT<V>::A acc, const float *scale, int64_t row) {
+    if constexpr (VT<V>::scaled) return acc * __ldg(scale + row);
+    else return acc;
 }
 
 template <typename T, bool NC>
@@ -72,11 +109,13 @@ __device__ __forceinline__ int choose_split(int len, int w4) {
     return cand;
 }
 
-template <typename T, bool NC>
+template <typename V, bool NC>
 __global__ void __launch_bounds__(kDefaultThreads)
-rgcsr_spmv_split(int64_t n, int32_t G, const T *__restrict__ val, const int32_t *__restrict__ col,
+rgcsr_spmv_split(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *__restrict__ col,
                  const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
-                 const T *__restrict__ x, T *__restrict__ y, int w4) {
+                 const float *__restrict__ scale, const typename VT<V>::A *__restrict__ x,
+                 typename VT<V>::A *__restrict__ y, int w4) {
+    using A = typename VT<V>::A;
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = row < n;
@@ -95,22 +134,22 @@ rgcsr_spmv_split(int64_t n, int32_t G, const T *__restrict__ val, const int32_t 
     if (lmax - lmin > 32) j0 = choose_split(len, w4);
 
     // Phase 1: thread per row over slots [0, min(len, j0)).
-    T acc = 0;
+    A acc = 0;
     const int jend = min(len, j0);
     for (int j = 0; j < jend; j += kUnroll) {
-        T v[kUnroll];
+        A v[kUnroll];
         int c[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             if (j + u < jend) {
                 const int64_t p = ptr + (int64_t)(j + u) * stride;
-                v[u] = ld_stream(val + p);
+                v[u] = VT<V>::ld(val + p);
                 c[u] = ld_stream(col + p);
             }
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u)
-            if (j + u < jend) acc = fma(v[u], gather<T, NC>(x, c[u]), acc);
+            if (j + u < jend) acc = fma(v[u], gather<A, NC>(x, c[u]), acc);
     }
 
     // Phase 2: the whole warp finishes each row longer than j0.
@@ -121,55 +160,57 @@ rgcsr_spmv_split(int64_t n, int32_t G, const T *__restrict__ val, const int32_t 
         const int Lr = __shfl_sync(kFull, len, r);
         const int sr = __shfl_sync(kFull, stride, r);
         const int64_t pr = shfl_i64(ptr, r);
-        T part = 0;
+        A part = 0;
         for (int j = j0 + lane; j < Lr; j += 32 * kUnroll) {
-            T v[kUnroll];
+            A v[kUnroll];
             int c[kUnroll];
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
                 const int jj = j + 32 * u;
                 if (jj < Lr) {
                     const int64_t p = pr + (int64_t)jj * sr;
-                    v[u] = ld_stream(val + p);
+                    v[u] = VT<V>::ld(val + p);
                     c[u] = ld_stream(col + p);
                 }
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u)
-                if (j + 32 * u < Lr) part = fma(v[u], gather<T, NC>(x, c[u]), part);
+                if (j + 32 * u < Lr) part = fma(v[u], gather<A, NC>(x, c[u]), part);
         }
         part = warp_sum(part);
         if (lane == r) acc += part;
     }
-    if (valid) y[row] = acc;
+    if (valid) y[row] = finish<V>(acc, scale, row);
 }
 
 // One thread per row and no long-row split, sized for full occupancy
 // (FP32: <= 32 registers, 64 warps per SM; FP64: 48 warps per SM) so that
-// enough loads stay in flight.  For
-// matrices whose rows within a warp have similar lengths.
-template <typename T, int U, int MIN_BLOCKS>
+// enough loads stay in flight.  For matrices whose rows within a warp have
+// similar lengths.
+template <typename V, int U, int MIN_BLOCKS>
 __global__ void __launch_bounds__(kDefaultThreads, MIN_BLOCKS)
-rgcsr_spmv_lean(int64_t n, int32_t G, const T *__restrict__ val, const int32_t *__restrict__ col,
+rgcsr_spmv_lean(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *__restrict__ col,
                 const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
-                const T *__restrict__ x, T *__restrict__ y) {
+                const float *__restrict__ scale, const typename VT<V>::A *__restrict__ x,
+                typename VT<V>::A *__restrict__ y) {
+    using A = typename VT<V>::A;
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= n) return;
     const int64_t g = row / G;
     const int64_t first = g * G;
     const int stride = (int)min((int64_t)G, n - first);
     const int64_t off = __ldg(gp + g) + (row - first);
-    const T *vp = val + off;
+    const V *vp = val + off;
     const int32_t *cp = col + off;
     const int len = __ldg(rl + row);
-    T acc = 0;
+    A acc = 0;
     for (int j = 0; j < len; j += U) {
-        T v[U];
+        A v[U];
         int c[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (j + u < len) {
-                v[u] = ld_stream(vp + (int64_t)u * stride);
+                v[u] = VT<V>::ld(vp + (int64_t)u * stride);
                 c[u] = ld_stream(cp + (int64_t)u * stride);
             }
         }
@@ -179,52 +220,55 @@ rgcsr_spmv_lean(int64_t n, int32_t G, const T *__restrict__ val, const int32_t *
         vp += (int64_t)U * stride;
         cp += (int64_t)U * stride;
     }
-    y[row] = acc;
+    y[row] = finish<V>(acc, scale, row);
 }
 
-template <typename T>
-int launch_spmv(const rgcsr_matrix *M, const T *x, T *y, const rgcsr_launch *L, cudaStream_t s) {
+template <typename V>
+int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V>::A *y,
+                const rgcsr_launch *L, cudaStream_t s) {
     const int kernel = L ? L->kernel : RGCSR_KERNEL_AUTO;
     const bool nc = !L || L->x_load == RGCSR_XLOAD_NC;
-    const T *val = static_cast<const T *>(M->values);
+    const V *val = static_cast<const V *>(M->values);
     const int64_t n = M->n_rows;
     const int32_t G = M->group_size;
+    const float *scale = M->row_scale;
+    if (VT<V>::scaled && !scale) return RGCSR_ERR_INVALID_ARG;
     if (kernel == RGCSR_KERNEL_LEAN) {
         const int64_t blocks = ceil_div(n, kDefaultThreads);
         if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
-        const int variant = L ? L->variant : 0;
-        if (variant == 0)
-            rgcsr_spmv_lean<T, 4, (sizeof(T) == 4 ? 8 : 6)><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
-                n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y);
-        else if (variant == 1)
-            rgcsr_spmv_lean<T, 8, (sizeof(T) == 4 ? 6 : 4)><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
-                n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y);
-        else
-            return RGCSR_ERR_INVALID_ARG;
+        if (L && L->variant != 0) return RGCSR_ERR_INVALID_ARG;
+        // 8 blocks (32 registers) fit plain FP32; FP64 and scaled storage need 6
+        constexpr int min_blocks = (std::is_same<V, float>::value) ? 8 : 6;
+        rgcsr_spmv_lean<V, 4, min_blocks><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
+            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y);
         return launch_status();
     }
     if (kernel == RGCSR_KERNEL_PAPER) {
-        if (G > 1024) return RGCSR_ERR_INVALID_ARG;
-        if (nc)
-            rgcsr_spmv_paper<T, true><<<(unsigned)M->n_groups, G, 0, s>>>(
-                n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y);
-        else
-            rgcsr_spmv_paper<T, false><<<(unsigned)M->n_groups, G, 0, s>>>(
-                n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y);
-        return launch_status();
+        if constexpr (VT<V>::scaled) {
+            return RGCSR_ERR_UNSUPPORTED_DTYPE;
+        } else {
+            if (G > 1024) return RGCSR_ERR_INVALID_ARG;
+            if (nc)
+                rgcsr_spmv_paper<V, true><<<(unsigned)M->n_groups, G, 0, s>>>(
+                    n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y);
+            else
+                rgcsr_spmv_paper<V, false><<<(unsigned)M->n_groups, G, 0, s>>>(
+                    n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y);
+            return launch_status();
+        }
     }
-    if (kernel != RGCSR_KERNEL_AUTO && kernel != RGCSR_KERNEL_SPLIT) return RGCSR_ERR_INVALID_ARG;
+    if (kernel != RGCSR_KERNEL_SPLIT) return RGCSR_ERR_INVALID_ARG;
     int threads = (L && L->block_threads) ? L->block_threads : kDefaultThreads;
     if (threads % 32 || threads < 32 || threads > kDefaultThreads) return RGCSR_ERR_INVALID_ARG;
     const int w4 = (L && L->split_weight > 0) ? L->split_weight : 8;
     const int64_t blocks = ceil_div(n, threads);
     if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
     if (nc)
-        rgcsr_spmv_split<T, true><<<(unsigned)blocks, threads, 0, s>>>(
-            n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y, w4);
+        rgcsr_spmv_split<V, true><<<(unsigned)blocks, threads, 0, s>>>(
+            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, w4);
     else
-        rgcsr_spmv_split<T, false><<<(unsigned)blocks, threads, 0, s>>>(
-            n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y, w4);
+        rgcsr_spmv_split<V, false><<<(unsigned)blocks, threads, 0, s>>>(
+            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, w4);
     return launch_status();
 }
 
@@ -253,8 +297,8 @@ RGCSR_API int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
     if (kernel == RGCSR_KERNEL_AUTO) {
         // Dense groups (padding <= 25% of the stored slots): the TMA-staged
         // kernel for FP32 and for short FP64 rows, the full-occupancy
-        // thread-per-row kernel for long FP64 rows; anything else (uneven
-        // rows, long rows) takes the warp-split kernel.
+        // thread-per-row kernel otherwise; uneven or long rows take the
+        // warp-split kernel.
         const bool dense = M->n_stored * 4 <= M->nnz * 5;
         const bool short_rows = M->nnz <= 8 * M->n_rows;
         if (dense && tma_eligible(M) && (M->value_type == RGCSR_F32 || short_rows))
@@ -270,12 +314,15 @@ RGCSR_API int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
     }
     rgcsr_launch resolved = launch ? *launch : rgcsr_launch{};
     resolved.kernel = kernel;
-    launch = &resolved;
     switch (M->value_type) {
         case RGCSR_F64:
-            return launch_spmv<double>(M, static_cast<const double *>(x), static_cast<double *>(y), launch, s);
+            return launch_spmv<double>(M, static_cast<const double *>(x), static_cast<double *>(y), &resolved, s);
         case RGCSR_F32:
-            return launch_spmv<float>(M, static_cast<const float *>(x), static_cast<float *>(y), launch, s);
+            return launch_spmv<float>(M, static_cast<const float *>(x), static_cast<float *>(y), &resolved, s);
+        case RGCSR_BF16:
+            return launch_spmv<__nv_bfloat16>(M, static_cast<const float *>(x), static_cast<float *>(y), &resolved, s);
+        case RGCSR_F16:
+            return launch_spmv<__half>(M, static_cast<const float *>(x), static_cast<float *>(y), &resolved, s);
         default:
             return RGCSR_ERR_UNSUPPORTED_DTYPE;
     }

@@ -106,6 +106,25 @@ class RgCSRMatrix:
         L.call("rgcsr_convert", ctypes.byref(A), ctypes.byref(M), st)
         return self
 
+    def quantized(self, fmt: str = "bf16", stream=None) -> "RgCSRMatrix":
+        """The same matrix with values stored as bfloat16 ("bf16") or half
+        ("f16") and a per-row power-of-two float scale; shares columns, group
+        pointers and row lengths with this matrix."""
+        q = RgCSRMatrix()
+        q.columns, q.group_ptr, q.row_lengths = self.columns, self.group_ptr, self.row_lengths
+        q.slot_to_csr = self.slot_to_csr
+        dt = {"bf16": torch.bfloat16, "f16": torch.float16}[fmt]
+        dev = self.group_ptr.device
+        q.values = torch.empty(self.s.n_stored, dtype=dt, device=dev)
+        q.row_scale = torch.empty(self.s.n_rows, dtype=torch.float32, device=dev)
+        D = q.s
+        D.value_type = L.BF16 if fmt == "bf16" else L.F16
+        D.values, D.row_scale = _ptr(q.values), _ptr(q.row_scale)
+        D.columns, D.group_ptr, D.row_lengths = self.s.columns, self.s.group_ptr, self.s.row_lengths
+        D.slot_to_csr = self.s.slot_to_csr
+        L.call("rgcsr_quantize", ctypes.byref(self.s), ctypes.byref(D), _stream_ptr(stream))
+        return q
+
     # -- properties ----------------------------------------------------------
     @property
     def shape(self):

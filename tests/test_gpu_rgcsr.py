@@ -19,7 +19,6 @@ TT = {"f32": torch.float32, "f64": torch.float64}
 VARIANTS = [dict(), dict(kernel=L.KERNEL_PAPER), dict(kernel=L.KERNEL_SPLIT, x_load=L.XLOAD_PLAIN),
             dict(kernel=L.KERNEL_SPLIT, block_threads=64, split_weight=4), dict(kernel=L.KERNEL_LEAN)]
 VARIANTS += [dict(kernel=L.KERNEL_TMA, variant=v) for v in range(0, 4)]
-VARIANTS += [dict(kernel=L.KERNEL_LEAN, variant=1)]
 
 
 def variants(M):
