@@ -168,6 +168,14 @@ int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
 int rgcsr_spmv_host(const rgcsr_matrix *M, const void *x_host, void *y_host,
                     void *x_dev, void *y_dev, rgcsr_stream_t stream);
 
+/* Y = A X for k right-hand sides (the SpMV of Sec. 3.4 applied to several
+ * vectors at once; not in the paper).  X: row-major [n_cols x k] with row
+ * stride ldx >= k elements; Y: row-major [n_rows x k], stride ldy >= k,
+ * overwritten.  Element types as for rgcsr_spmv.  The matrix is streamed
+ * once per chunk of up to 32 columns (16 for F64).  Async. */
+int rgcsr_spmm(const rgcsr_matrix *M, int32_t k, const void *X, int64_t ldx, void *Y,
+               int64_t ldy, rgcsr_stream_t stream);
+
 /* ----------------------------------------------------------------------- */
 /* Reduced-precision value storage (not in the paper, which stores single  */
 /* or double precision).  Per row i the scale is                            */

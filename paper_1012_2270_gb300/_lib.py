@@ -65,6 +65,7 @@ SIGNATURES = {
     "rgcsr_spmv_ex": (ctypes.c_int, [_PM, P, P, _PL, P]),
     "rgcsr_spmv_host": (ctypes.c_int, [_PM, P, P, P, P, P]),
     "rgcsr_quantize": (ctypes.c_int, [_PM, _PM, P]),
+    "rgcsr_spmm": (ctypes.c_int, [_PM, I32, P, I64, P, I64, P]),
     "hyb_workspace_bytes": (SZ, [I64, I64]),
     "hyb_plan": (ctypes.c_int, [_PCSR, I32, _PH, P, SZ, P]),
     "hyb_convert": (ctypes.c_int, [_PCSR, _PH, P, SZ, P]),

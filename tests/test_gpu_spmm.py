@@ -1,0 +1,82 @@
+"""GPU parity of the multi-RHS product Y = A X against the oracle's CSR
+SpMM, elementwise within tau*(|A||X|): column counts that exercise every
+chunk width and ragged remainders, strided X and Y, long rows, reduced
+precision storage, and matrix (b) at k = 1, 4, 8, 16, 32."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import TAU, assert_within_bound, rounded_values
+from paper_1012_2270_gb300 import synth
+from paper_1012_2270_gb300.rgcsr import RgCSRMatrix
+
+pytestmark = pytest.mark.gpu
+
+NP = {"f32": np.float32, "f64": np.float64}
+TT = {"f32": torch.float32, "f64": torch.float64}
+
+
+def check(A, M, dtype, X, tau, vals=None, X_dev=None, Y_out=None):
+    Xd = X_dev if X_dev is not None else torch.from_numpy(X.astype(NP[dtype])).cuda()
+    Y = M.spmm(Xd, out=Y_out).cpu().numpy()
+    v = rounded_values(A.val, dtype) if vals is None else vals
+    Y_ref, aY = oracle.csr_spmm(A.rowptr, A.col, v, X.astype(NP[dtype]).astype(np.float64))
+    assert_within_bound(Y.ravel(), Y_ref.ravel(), aY.ravel(), tau, f"{A.name} {dtype} k={X.shape[1]}")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 8, 16, 17, 32, 33, 40])
+def test_spmm_ragged(dtype, k):
+    rng = np.random.default_rng(k)
+    Ls = rng.integers(0, 30, 1500)
+    Ls[[3, 700, 701]] = [2000, 900, 35]
+    A = synth.random_csr(1500, 2500, Ls, seed=k)
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dtype]), A.n_cols, dtype=TT[dtype])
+    X = synth.uniform_matrix(A.n_cols, k, seed=k)
+    check(A, M, dtype, X, TAU[dtype])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_spmm_strided_operands_and_group_sizes(dtype):
+    rng = np.random.default_rng(9)
+    A = synth.random_csr(777, 500, rng.integers(0, 20, 777), seed=9)
+    for G in (1, 16, 32, 64):
+        M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dtype]), A.n_cols, group_size=G,
+                                 dtype=TT[dtype])
+        wide = synth.uniform_matrix(A.n_cols, 11, seed=G)
+        X = wide[:, 2:9]                                     # k = 7, row stride 11
+        Xd = torch.from_numpy(wide.astype(NP[dtype])).cuda()[:, 2:9]
+        Yw = torch.full((A.n_rows, 10), 7.0, dtype=TT[dtype], device="cuda")
+        check(A, M, dtype, X, TAU[dtype], X_dev=Xd, Y_out=Yw[:, 1:8])
+        assert (Yw[:, 0] == 7.0).all() and (Yw[:, 8:] == 7.0).all()   # untouched
+
+
+def test_spmm_matches_spmv_columns():
+    A = synth.workload_small_laplacian()
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val, A.n_cols, dtype=torch.float64)
+    X = torch.from_numpy(synth.uniform_matrix(A.n_cols, 4, seed=0)).cuda()
+    Y = M.spmm(X)
+    for b in range(4):
+        y = M.spmv(X[:, b].contiguous())
+        assert torch.allclose(Y[:, b], y, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_spmm_quantized(fmt):
+    rng = np.random.default_rng(5)
+    A = synth.random_csr(900, 600, rng.integers(0, 25, 900), seed=5)
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val, A.n_cols, dtype=torch.float64)
+    Q = M.quantized(fmt)
+    q, s = oracle.quantize_rows(A.rowptr, A.val, oracle.BF16 if fmt == "bf16" else oracle.F16)
+    deq = oracle.dequantized_values(A.rowptr, q, s, oracle.BF16 if fmt == "bf16" else oracle.F16)
+    X = synth.uniform_matrix(A.n_cols, 8, seed=1)
+    check(A, Q, "f32", X, 2e-6, vals=deq)
+
+
+@pytest.mark.parametrize("k", [1, 4, 8, 16, 32])
+def test_spmm_full_size_b(k):
+    A = synth.workload_b()
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(np.float32), A.n_cols, dtype=torch.float32)
+    X = synth.uniform_matrix(A.n_cols, k, seed=k)
+    check(A, M, "f32", X, TAU["f32"])
