@@ -194,6 +194,83 @@ int rgcsr_spmm(const rgcsr_matrix *M, int32_t k, const void *X, int64_t ldx, voi
 int rgcsr_quantize(const rgcsr_matrix *src, rgcsr_matrix *dst, rgcsr_stream_t stream);
 
 /* ----------------------------------------------------------------------- */
+/* Backward pass of Y = A X (not in the paper).  With an upstream gradient  */
+/* dY:  dX = A^T dY  (an SpMM with an RgCSR matrix of A^T, built once from  */
+/* the CSR transpose below) and  dA_p = sum_b dY[row_p, b] X[col_p, b]      */
+/* for every stored entry p (rgcsr_sampled_dot).                            */
+/* ----------------------------------------------------------------------- */
+/* Workspace of rgcsr_csr_transpose (about 20 bytes per stored entry). */
+size_t rgcsr_transpose_workspace_bytes(int64_t nnz, int64_t n_rows, int64_t n_cols);
+/* CSR of A^T by a stable radix sort of the entries by column: t_row_ptr
+ * (n_cols+1), t_col_idx (nnz; the original row of each entry, increasing
+ * within every transposed row), perm (nnz, optional: the original CSR
+ * position of each transposed entry) and t_values (nnz of A's value type,
+ * optional: values[perm]).  Needs nnz < 2^32.  Async. */
+int rgcsr_csr_transpose(const rgcsr_csr *A, int64_t *t_row_ptr, int32_t *t_col_idx, int64_t *perm,
+                        void *t_values, void *workspace, size_t workspace_bytes,
+                        rgcsr_stream_t stream);
+/* row_index[p] = the row of stored entry p (nnz int32).  Async. */
+int rgcsr_csr_row_index(const rgcsr_csr *A, int32_t *row_index, rgcsr_stream_t stream);
+/* M->values[s] = src[src_index[s]], or 0 where src_index[s] < 0 (padding);
+ * src has M's value type (F64/F32).  Refreshes an RgCSR matrix from values
+ * kept in CSR order, e.g. with src_index = M->slot_to_csr.  Async. */
+int rgcsr_gather_values(const rgcsr_matrix *M, const void *src, const int64_t *src_index,
+                        rgcsr_stream_t stream);
+/* out[s] = inner[outer[s]], or -1 where outer[s] < 0 (n entries).  Async. */
+int rgcsr_compose_index(const int64_t *outer, const int64_t *inner, int64_t n, int64_t *out,
+                        rgcsr_stream_t stream);
+/* out[p] = sum_{b<k} G[row_index[p]*ldg + b] * X[col_idx[p]*ldx + b] for
+ * p < nnz, summed in increasing b; value_type F64 or F32.  Async. */
+int rgcsr_sampled_dot(int64_t nnz, int32_t k, const int32_t *row_index, const int32_t *col_idx,
+                      const void *G, int64_t ldg, const void *X, int64_t ldx, void *out,
+                      int32_t value_type, rgcsr_stream_t stream);
+
+/* ----------------------------------------------------------------------- */
+/* Vector kernels and solvers around the SpMV (Sec. 1: a Krylov iteration   */
+/* is SpMV + SAXPY + SDOT).  value_type RGCSR_F64 (double vectors) or       */
+/* RGCSR_F32 (float vectors).  All async unless stated.                     */
+/* ----------------------------------------------------------------------- */
+/* Scratch of rgcsr_dot, in bytes. */
+size_t rgcsr_dot_workspace_bytes(void);
+/* *result (a DEVICE double) = sum_i x_i y_i, accumulated in double in a
+ * fixed order (deterministic). */
+int rgcsr_dot(int64_t n, const void *x, const void *y, double *result, void *workspace,
+              size_t workspace_bytes, int32_t value_type, rgcsr_stream_t stream);
+/* y = alpha x + beta y. */
+int rgcsr_axpby(int64_t n, double alpha, const void *x, double beta, void *y, int32_t value_type,
+                rgcsr_stream_t stream);
+/* Damped Jacobi update x_out = x + omega * dinv .* (b - Ax). */
+int rgcsr_jacobi_step(int64_t n, double omega, const void *dinv, const void *b, const void *Ax,
+                      const void *x, void *x_out, int32_t value_type, rgcsr_stream_t stream);
+/* out = alpha * d .* x. */
+int rgcsr_diag_scale(int64_t n, double alpha, const void *d, const void *x, void *out,
+                     int32_t value_type, rgcsr_stream_t stream);
+/* dst = src converted between RGCSR_F64 and RGCSR_F32 (round to nearest). */
+int rgcsr_convert_vector(int64_t n, const void *src, int32_t src_type, void *dst, int32_t dst_type,
+                         rgcsr_stream_t stream);
+
+/* Conjugate gradients for a symmetric positive definite square A, from
+ * x = 0, stopping when ||r|| <= rel_tol ||b|| (the recurrence residual,
+ * checked on the host every check_every iterations) or after max_iter
+ * iterations.  Vectors are double for F64 storage, float otherwise.
+ * Writes *iterations and *rel_residual (host); synchronises `stream`. */
+size_t rgcsr_cg_workspace_bytes(int64_t n, int32_t value_type);
+int rgcsr_cg(const rgcsr_matrix *A, const void *b, void *x, double rel_tol, int32_t max_iter,
+             int32_t check_every, void *workspace, size_t workspace_bytes, int32_t *iterations,
+             double *rel_residual, rgcsr_stream_t stream);
+/* Mixed-precision iterative refinement: outer loop in FP64 (r = b - A_hi x
+ * with the F64 matrix A_hi, stop when ||r|| <= outer_tol ||b|| or after
+ * max_outer corrections), inner CG in float on A_lo (F32, BF16 or F16
+ * storage of the same matrix) to inner_tol, x += d in FP64.  b, x: double.
+ * Writes the number of corrections, the total inner iterations and the
+ * final true relative residual (host); synchronises `stream`. */
+size_t rgcsr_ir_cg_workspace_bytes(int64_t n);
+int rgcsr_ir_cg(const rgcsr_matrix *A_hi, const rgcsr_matrix *A_lo, const double *b, double *x,
+                double outer_tol, int32_t max_outer, double inner_tol, int32_t max_inner,
+                void *workspace, size_t workspace_bytes, int32_t *outer_iters, int32_t *inner_iters,
+                double *rel_residual, rgcsr_stream_t stream);
+
+/* ----------------------------------------------------------------------- */
 /* Hybrid ELLPACK + COO (Sec. 3.3), the paper's comparison format.  The ELL */
 /* part is column-major, n_rows x ell_width (slot j of row r at j*n_rows+r, */
 /* padding: value 0, column -1); entries past a row's first ell_width go to */

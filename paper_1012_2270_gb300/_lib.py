@@ -54,6 +54,8 @@ class Hyb(ctypes.Structure):
 
 _PCSR, _PM, _PL, _PH = (ctypes.POINTER(CSR), ctypes.POINTER(Matrix),
                         ctypes.POINTER(Launch), ctypes.POINTER(Hyb))
+D = ctypes.c_double
+PI32, PD = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)
 
 # name -> (restype, argtypes); mirrors include/rgcsr.h
 SIGNATURES = {
@@ -66,6 +68,22 @@ SIGNATURES = {
     "rgcsr_spmv_host": (ctypes.c_int, [_PM, P, P, P, P, P]),
     "rgcsr_quantize": (ctypes.c_int, [_PM, _PM, P]),
     "rgcsr_spmm": (ctypes.c_int, [_PM, I32, P, I64, P, I64, P]),
+    "rgcsr_transpose_workspace_bytes": (SZ, [I64, I64, I64]),
+    "rgcsr_csr_transpose": (ctypes.c_int, [_PCSR, P, P, P, P, P, SZ, P]),
+    "rgcsr_csr_row_index": (ctypes.c_int, [_PCSR, P, P]),
+    "rgcsr_gather_values": (ctypes.c_int, [_PM, P, P, P]),
+    "rgcsr_compose_index": (ctypes.c_int, [P, P, I64, P, P]),
+    "rgcsr_sampled_dot": (ctypes.c_int, [I64, I32, P, P, P, I64, P, I64, P, I32, P]),
+    "rgcsr_dot_workspace_bytes": (SZ, []),
+    "rgcsr_dot": (ctypes.c_int, [I64, P, P, P, P, SZ, I32, P]),
+    "rgcsr_axpby": (ctypes.c_int, [I64, D, P, D, P, I32, P]),
+    "rgcsr_jacobi_step": (ctypes.c_int, [I64, D, P, P, P, P, P, I32, P]),
+    "rgcsr_diag_scale": (ctypes.c_int, [I64, D, P, P, P, I32, P]),
+    "rgcsr_convert_vector": (ctypes.c_int, [I64, P, I32, P, I32, P]),
+    "rgcsr_cg_workspace_bytes": (SZ, [I64, I32]),
+    "rgcsr_cg": (ctypes.c_int, [_PM, P, P, D, I32, I32, P, SZ, PI32, PD, P]),
+    "rgcsr_ir_cg_workspace_bytes": (SZ, [I64]),
+    "rgcsr_ir_cg": (ctypes.c_int, [_PM, _PM, P, P, D, I32, D, I32, P, SZ, PI32, PI32, PD, P]),
     "hyb_workspace_bytes": (SZ, [I64, I64]),
     "hyb_plan": (ctypes.c_int, [_PCSR, I32, _PH, P, SZ, P]),
     "hyb_convert": (ctypes.c_int, [_PCSR, _PH, P, SZ, P]),

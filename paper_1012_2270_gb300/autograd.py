@@ -1,0 +1,108 @@
+"""Differentiable sparse products for a fixed sparsity pattern.
+
+``SparseOperator`` keeps, on the GPU, the RgCSR matrix of A, the RgCSR matrix
+of A^T (built once from a stable CSR transposition) and the maps from their
+slots to the CSR-ordered value array, so values that change between calls
+(trainable weights) are refreshed with two gather kernels.
+
+``spmm(op, values, X)`` computes A X (X a vector or an [n_cols, k] block) and
+is differentiable with respect to both the values and X:
+    dX      = A^T dY                      (RgCSR SpMV/SpMM of A^T)
+    dA_p    = sum_b dY[row_p, b] X[col_p, b]   (sampled dot over the pattern)
+Every product and gradient runs in librgcsr's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib as L
+from .rgcsr import RgCSRMatrix, _dev, _ptr, _stream_ptr, csr_struct
+
+
+class SparseOperator:
+    """A fixed CSR pattern (``rowptr``, ``col``) of shape [n_rows, n_cols]."""
+
+    def __init__(self, rowptr, col, n_cols: int, dtype: torch.dtype = torch.float32,
+                 group_size: int = 32, device="cuda"):
+        self.rowptr = _dev(rowptr, torch.int64, device)
+        self.col = _dev(col, torch.int32, device)
+        self.n_rows = self.rowptr.numel() - 1
+        self.n_cols = int(n_cols)
+        self.nnz = self.col.numel()
+        self.dtype = dtype
+        zeros = torch.zeros(self.nnz, dtype=dtype, device=device)
+        st = _stream_ptr()
+        self.A = RgCSRMatrix.from_csr(self.rowptr, self.col, zeros, self.n_cols, group_size=group_size,
+                                      dtype=dtype, keep_slot_map=True)
+        # stable transposition of the pattern
+        csr = csr_struct(self.rowptr, self.col, zeros, self.n_cols)
+        nb = L.lib().rgcsr_transpose_workspace_bytes(self.nnz, self.n_rows, self.n_cols)
+        ws = torch.empty(nb, dtype=torch.uint8, device=device)
+        t_rowptr = torch.empty(self.n_cols + 1, dtype=torch.int64, device=device)
+        t_col = torch.empty(self.nnz, dtype=torch.int32, device=device)
+        perm = torch.empty(self.nnz, dtype=torch.int64, device=device)
+        L.call("rgcsr_csr_transpose", ctypes.byref(csr), _ptr(t_rowptr), _ptr(t_col), _ptr(perm),
+               None, _ptr(ws), nb, st)
+        del ws
+        self.AT = RgCSRMatrix.from_csr(t_rowptr, t_col, zeros, self.n_rows, group_size=group_size,
+                                       dtype=dtype, keep_slot_map=True)
+        self.at_src = torch.empty(self.AT.n_stored, dtype=torch.int64, device=device)
+        L.call("rgcsr_compose_index", _ptr(self.AT.slot_to_csr), _ptr(perm), self.AT.n_stored,
+               _ptr(self.at_src), st)
+        self.row_index = torch.empty(self.nnz, dtype=torch.int32, device=device)
+        L.call("rgcsr_csr_row_index", ctypes.byref(csr), _ptr(self.row_index), st)
+
+    def set_values(self, values: torch.Tensor) -> None:
+        """Loads CSR-ordered values into the RgCSR matrices of A and A^T."""
+        if values.dtype != self.dtype or values.numel() != self.nnz or not values.is_contiguous():
+            raise ValueError(f"values must be a contiguous {self.dtype} vector of length {self.nnz}")
+        st = _stream_ptr()
+        L.call("rgcsr_gather_values", ctypes.byref(self.A.s), _ptr(values), _ptr(self.A.slot_to_csr), st)
+        L.call("rgcsr_gather_values", ctypes.byref(self.AT.s), _ptr(values), _ptr(self.at_src), st)
+
+    def matmul(self, X: torch.Tensor) -> torch.Tensor:
+        return self.A.spmv(X) if X.dim() == 1 else self.A.spmm(X)
+
+    def matmul_t(self, G: torch.Tensor) -> torch.Tensor:
+        return self.AT.spmv(G) if G.dim() == 1 else self.AT.spmm(G)
+
+    def sampled_dot(self, G: torch.Tensor, X: torch.Tensor) -> torch.Tensor:
+        """out[p] = sum_b G[row_p, b] X[col_p, b] for every stored entry p."""
+        G2 = G.reshape(self.n_rows, -1)
+        X2 = X.reshape(self.n_cols, -1)
+        k = G2.shape[1]
+        if X2.shape[1] != k or G2.stride(1) != 1 or X2.stride(1) != 1:
+            raise ValueError("G and X need the same number of columns and unit column stride")
+        out = torch.empty(self.nnz, dtype=self.dtype, device=G.device)
+        vt = L.F64 if self.dtype == torch.float64 else L.F32
+        L.call("rgcsr_sampled_dot", self.nnz, k, _ptr(self.row_index), _ptr(self.col), _ptr(G2),
+               max(G2.stride(0), k), _ptr(X2), max(X2.stride(0), k), _ptr(out), vt, _stream_ptr())
+        return out
+
+
+class _SparseMatmul(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, values, X, op):
+        op.set_values(values)
+        ctx.op = op
+        ctx.save_for_backward(values, X)
+        return op.matmul(X.contiguous())
+
+    @staticmethod
+    def backward(ctx, dY):
+        values, X = ctx.saved_tensors
+        op = ctx.op
+        dY = dY.contiguous()
+        d_values = op.sampled_dot(dY, X.contiguous()) if ctx.needs_input_grad[0] else None
+        dX = None
+        if ctx.needs_input_grad[1]:
+            op.set_values(values)          # the operator may have served other values since
+            dX = op.matmul_t(dY)
+        return d_values, dX, None
+
+
+def spmm(op: SparseOperator, values: torch.Tensor, X: torch.Tensor) -> torch.Tensor:
+    """A X with A = (op's pattern, values); differentiable in values and X."""
+    return _SparseMatmul.apply(values, X, op)

@@ -1,0 +1,179 @@
+// blas1.cu -- vector kernels for the Krylov and fixed-point solvers built on
+// the SpMV (the paper's introduction: CG and GMRES need SpMV, SAXPY and
+// SDOT).  Dot products are deterministic: fixed grid, fixed per-thread
+// order, per-block tree, then one block sums the block results in order.
+#include "common.cuh"
+
+namespace rgcsr {
+namespace {
+
+constexpr int kDotThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    __syncthreads();
+    return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kDotThreads)
+dot_partial(int64_t n, const T *__restrict__ x, const T *__restrict__ y, double *__restrict__ part) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s = fma((double)x[i], (double)y[i], s);
+    const double t = block_sum<T>(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kDotThreads)
+dot_final(int nparts, const double *__restrict__ part, double *__restrict__ out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
+    const double t = block_sum<double>(s, sh);
+    if (threadIdx.x == 0) *out = t;
+}
+
+template <typename T>
+__global__ void axpby_kernel(int64_t n, double a, const T *__restrict__ x, double b, T *__restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (T)(a * (double)x[i] + b * (double)y[i]);
+}
+
+template <typename T>
+__global__ void jacobi_kernel(int64_t n, T omega, const T *__restrict__ dinv, const T *__restrict__ b,
+                              const T *__restrict__ ax, const T *__restrict__ x, T *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = x[i] + omega * dinv[i] * (b[i] - ax[i]);
+}
+
+template <typename T>
+__global__ void diag_scale_kernel(int64_t n, T alpha, const T *__restrict__ d, const T *__restrict__ x,
+                                  T *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = alpha * d[i] * x[i];
+}
+
+template <typename S, typename D>
+__global__ void convert_kernel(int64_t n, const S *__restrict__ src, D *__restrict__ dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (D)src[i];
+}
+
+unsigned vec_grid(int64_t n) {
+    int64_t b = ceil_div(n, 256);
+    if (b > 152 * 16) b = 152 * 16;
+    return (unsigned)(b > 0 ? b : 1);
+}
+
+}  // namespace
+
+int dot_device(int64_t n, const void *x, const void *y, double *out, double *partials, int value_type,
+               cudaStream_t s) {
+    const unsigned g = (unsigned)kDotParts;
+    if (value_type == RGCSR_F64)
+        dot_partial<double><<<g, kDotThreads, 0, s>>>(n, static_cast<const double *>(x),
+                                                      static_cast<const double *>(y), partials);
+    else
+        dot_partial<float><<<g, kDotThreads, 0, s>>>(n, static_cast<const float *>(x),
+                                                     static_cast<const float *>(y), partials);
+    dot_final<<<1, kDotThreads, 0, s>>>((int)g, partials, out);
+    return launch_status();
+}
+
+int axpby_device(int64_t n, double a, const void *x, double b, void *y, int value_type, cudaStream_t s) {
+    if (n <= 0) return RGCSR_OK;
+    if (value_type == RGCSR_F64)
+        axpby_kernel<double><<<vec_grid(n), 256, 0, s>>>(n, a, static_cast<const double *>(x), b,
+                                                          static_cast<double *>(y));
+    else
+        axpby_kernel<float><<<vec_grid(n), 256, 0, s>>>(n, a, static_cast<const float *>(x), b,
+                                                         static_cast<float *>(y));
+    return launch_status();
+}
+
+int convert_device(int64_t n, const void *src, int src_type, void *dst, int dst_type, cudaStream_t s) {
+    if (n <= 0) return RGCSR_OK;
+    if (src_type == RGCSR_F64 && dst_type == RGCSR_F32)
+        convert_kernel<double, float><<<vec_grid(n), 256, 0, s>>>(n, static_cast<const double *>(src),
+                                                                 static_cast<float *>(dst));
+    else if (src_type == RGCSR_F32 && dst_type == RGCSR_F64)
+        convert_kernel<float, double><<<vec_grid(n), 256, 0, s>>>(n, static_cast<const float *>(src),
+                                                                 static_cast<double *>(dst));
+    else
+        return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    return launch_status();
+}
+
+}  // namespace rgcsr
+
+using namespace rgcsr;
+
+RGCSR_API size_t rgcsr_dot_workspace_bytes(void) { return (size_t)kDotParts * sizeof(double); }
+
+RGCSR_API int rgcsr_dot(int64_t n, const void *x, const void *y, double *result, void *workspace,
+                        size_t workspace_bytes, int32_t value_type, rgcsr_stream_t stream) {
+    if (n < 0 || !result || (n > 0 && (!x || !y))) return RGCSR_ERR_INVALID_ARG;
+    if (value_type != RGCSR_F64 && value_type != RGCSR_F32) return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    if (!workspace || workspace_bytes < rgcsr_dot_workspace_bytes()) return RGCSR_ERR_WORKSPACE;
+    return dot_device(n, x, y, result, static_cast<double *>(workspace), value_type, (cudaStream_t)stream);
+}
+
+RGCSR_API int rgcsr_axpby(int64_t n, double alpha, const void *x, double beta, void *y, int32_t value_type,
+                          rgcsr_stream_t stream) {
+    if (n < 0 || (n > 0 && (!x || !y))) return RGCSR_ERR_INVALID_ARG;
+    if (value_type != RGCSR_F64 && value_type != RGCSR_F32) return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    return axpby_device(n, alpha, x, beta, y, value_type, (cudaStream_t)stream);
+}
+
+RGCSR_API int rgcsr_jacobi_step(int64_t n, double omega, const void *dinv, const void *b, const void *Ax,
+                                const void *x, void *x_out, int32_t value_type, rgcsr_stream_t stream) {
+    if (n < 0 || (n > 0 && (!dinv || !b || !Ax || !x || !x_out))) return RGCSR_ERR_INVALID_ARG;
+    if (n == 0) return RGCSR_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (value_type == RGCSR_F64)
+        jacobi_kernel<double><<<vec_grid(n), 256, 0, s>>>(n, omega, static_cast<const double *>(dinv),
+                                                          static_cast<const double *>(b),
+                                                          static_cast<const double *>(Ax),
+                                                          static_cast<const double *>(x), static_cast<double *>(x_out));
+    else if (value_type == RGCSR_F32)
+        jacobi_kernel<float><<<vec_grid(n), 256, 0, s>>>(n, (float)omega, static_cast<const float *>(dinv),
+                                                         static_cast<const float *>(b),
+                                                         static_cast<const float *>(Ax),
+                                                         static_cast<const float *>(x), static_cast<float *>(x_out));
+    else
+        return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    return launch_status();
+}
+
+RGCSR_API int rgcsr_diag_scale(int64_t n, double alpha, const void *d, const void *x, void *out,
+                               int32_t value_type, rgcsr_stream_t stream) {
+    if (n < 0 || (n > 0 && (!d || !x || !out))) return RGCSR_ERR_INVALID_ARG;
+    if (n == 0) return RGCSR_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (value_type == RGCSR_F64)
+        diag_scale_kernel<double><<<vec_grid(n), 256, 0, s>>>(n, alpha, static_cast<const double *>(d),
+                                                              static_cast<const double *>(x), static_cast<double *>(out));
+    else if (value_type == RGCSR_F32)
+        diag_scale_kernel<float><<<vec_grid(n), 256, 0, s>>>(n, (float)alpha, static_cast<const float *>(d),
+                                                             static_cast<const float *>(x), static_cast<float *>(out));
+    else
+        return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    return launch_status();
+}
+
+RGCSR_API int rgcsr_convert_vector(int64_t n, const void *src, int32_t src_type, void *dst, int32_t dst_type,
+                                   rgcsr_stream_t stream) {
+    if (n < 0 || (n > 0 && (!src || !dst))) return RGCSR_ERR_INVALID_ARG;
+    return convert_device(n, src, src_type, dst, dst_type, (cudaStream_t)stream);
+}

@@ -115,6 +115,15 @@ int exclusive_scan_i64(int64_t *data, int64_t count, int64_t *partials, cudaStre
 int launch_validate_csr(const rgcsr_csr *A, int *flags, int64_t *max_len, cudaStream_t s);
 int launch_row_lengths(const rgcsr_csr *A, int32_t *row_lengths, cudaStream_t s);
 
+// Vector kernels (blas1.cu).  dot_device writes the dot product of x and y
+// (accumulated in double, deterministic) to the device scalar *out, using
+// kDotParts doubles of scratch.
+constexpr int kDotParts = 304;
+int dot_device(int64_t n, const void *x, const void *y, double *out, double *partials, int value_type,
+               cudaStream_t s);
+int axpby_device(int64_t n, double a, const void *x, double b, void *y, int value_type, cudaStream_t s);
+int convert_device(int64_t n, const void *src, int src_type, void *dst, int dst_type, cudaStream_t s);
+
 // TMA-staged SpMV for G = 32 (spmv_tma.cu).
 bool tma_eligible(const rgcsr_matrix *M);
 int launch_spmv_tma(const rgcsr_matrix *M, const void *x, void *y, int variant, cudaStream_t s);

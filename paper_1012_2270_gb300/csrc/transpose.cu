@@ -1,0 +1,315 @@
+// transpose.cu -- structure operations for the backward pass of y = A x:
+//   * a stable LSD radix sort of (key, index) pairs, 8-bit digits;
+//   * rgcsr_csr_transpose: CSR of A^T, its entries in increasing original
+//     row (stable by construction), with the permutation to A's entries;
+//   * rgcsr_csr_row_index: the row of every stored entry;
+//   * rgcsr_gather_values / rgcsr_compose_index: refresh an RgCSR matrix's
+//     values from CSR-ordered values through a slot -> source index map;
+//   * rgcsr_sampled_dot: out[p] = sum_b G[row_p, b] X[col_p, b], the gradient
+//     of sum(G .* (A X)) with respect to every stored value.
+// None of this is in the paper (which has no backward pass); the transposed
+// matrix is an ordinary RgCSR matrix built with rgcsr_plan / rgcsr_convert.
+#include "common.cuh"
+
+namespace rgcsr {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 8;
+constexpr int kSortTile = kSortThreads * kSortRounds;   // items per tile
+constexpr int kDigits = 256;
+static_assert(kSortThreads == kDigits, "the scatter's prefix step uses one thread per digit");
+
+// Per-tile digit histogram -> counts[d * n_tiles + tile].
+__global__ void __launch_bounds__(kSortThreads)
+radix_histogram(const uint32_t *__restrict__ keys, int64_t n, int shift, int64_t n_tiles,
+                int64_t *__restrict__ counts) {
+    __shared__ int hist[kDigits];
+    hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortRounds; ++r) {
+        const int64_t i = base + r * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&hist[(keys[i] >> shift) & 0xff], 1);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = hist[threadIdx.x];
+}
+
+// Stable scatter.  Items of a tile are taken in index order, 256 per round;
+// an item's destination is the digit's global offset for this tile, plus the
+// items of that digit in earlier rounds, earlier warps, and earlier lanes.
+// vals_in == nullptr means "the item's own index".
+__global__ void __launch_bounds__(kSortThreads)
+radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+              uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n, int shift,
+              int64_t n_tiles, const int64_t *__restrict__ offsets) {
+    __shared__ int wcnt[kSortThreads / 32][kDigits];
+    __shared__ int run[kDigits];
+    __shared__ int64_t base_off[kDigits];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    run[tid] = 0;
+    base_off[tid] = offsets[(int64_t)tid * n_tiles + blockIdx.x];
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortRounds; ++r) {
+#pragma unroll
+        for (int q = 0; q < kDigits / 32; ++q) wcnt[w][lane + 32 * q] = 0;
+        __syncthreads();
+        const int64_t i = base + r * kSortThreads + tid;
+        const bool valid = i < n;
+        const uint32_t key = valid ? keys_in[i] : 0u;
+        const uint32_t val = valid ? (vals_in ? vals_in[i] : (uint32_t)i) : 0u;
+        const int digit = (int)((key >> shift) & 0xff);
+        const unsigned peers = __match_any_sync(kFull, valid ? digit : kDigits + lane);
+        const int rank = __popc(peers & lt);
+        if (valid && rank == 0) wcnt[w][digit] = __popc(peers);
+        __syncthreads();
+        {   // exclusive prefix of digit tid over warps, continuing earlier rounds
+            int s = run[tid];
+#pragma unroll
+            for (int ww = 0; ww < kSortThreads / 32; ++ww) {
+                const int c = wcnt[ww][tid];
+                wcnt[ww][tid] = s;
+                s += c;
+            }
+            run[tid] = s;
+        }
+        __syncthreads();
+        if (valid) {
+            const int64_t pos = base_off[digit] + wcnt[w][digit] + rank;
+            keys_out[pos] = key;
+            vals_out[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+struct SortBuffers {
+    uint32_t *k0, *v0, *k1, *v1;
+    int64_t *counts, *partials;
+};
+
+size_t sort_workspace_bytes(int64_t n) {
+    const int64_t n_tiles = ceil_div(n > 0 ? n : 1, kSortTile);
+    return 4 * align_up((size_t)n * 4, 256) + align_up((size_t)(kDigits * n_tiles + 1) * 8, 256) +
+           scan_partials_bytes(kDigits * n_tiles);
+}
+
+SortBuffers carve_sort(void *ws, int64_t n) {
+    const int64_t n_tiles = ceil_div(n > 0 ? n : 1, kSortTile);
+    char *p = static_cast<char *>(ws);
+    SortBuffers b;
+    const size_t a = align_up((size_t)n * 4, 256);
+    b.k0 = reinterpret_cast<uint32_t *>(p); p += a;
+    b.v0 = reinterpret_cast<uint32_t *>(p); p += a;
+    b.k1 = reinterpret_cast<uint32_t *>(p); p += a;
+    b.v1 = reinterpret_cast<uint32_t *>(p); p += a;
+    b.counts = reinterpret_cast<int64_t *>(p); p += align_up((size_t)(kDigits * n_tiles + 1) * 8, 256);
+    b.partials = reinterpret_cast<int64_t *>(p);
+    return b;
+}
+
+// Stable sort of keys (all < 2^key_bits) with their indices.  Result in
+// (*keys_out, *idx_out), pointing into the buffers.
+int radix_sort_indices(const uint32_t *keys, int64_t n, int key_bits, SortBuffers &b,
+                       const uint32_t **keys_out, const uint32_t **idx_out, cudaStream_t s) {
+    const int64_t n_tiles = ceil_div(n, kSortTile);
+    if (n_tiles > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
+    const uint32_t *kin = keys, *vin = nullptr;
+    uint32_t *kout = b.k0, *vout = b.v0;
+    const int passes = key_bits <= 0 ? 1 : (key_bits + 7) / 8;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        radix_histogram<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(kin, n, shift, n_tiles, b.counts);
+        int st = exclusive_scan_i64(b.counts, kDigits * n_tiles, b.partials, s);
+        if (st != RGCSR_OK) return st;
+        radix_scatter<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, n_tiles,
+                                                                 b.counts);
+        if ((st = launch_status()) != RGCSR_OK) return st;
+        kin = kout;
+        vin = vout;
+        if (kout == b.k0) { kout = b.k1; vout = b.v1; } else { kout = b.k0; vout = b.v0; }
+    }
+    *keys_out = kin;
+    *idx_out = vin;
+    return RGCSR_OK;
+}
+
+// One warp per row writes the row's index into its entries.
+__global__ void row_index_kernel(RowPtr rp, int64_t n, int32_t *__restrict__ row_index) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        const int64_t a = rp[i], e = rp[i + 1];
+        for (int64_t p = a + lane; p < e; p += 32) row_index[p] = (int32_t)i;
+    }
+}
+
+__global__ void column_counts_kernel(const int32_t *__restrict__ col, int64_t nnz,
+                                     unsigned long long *__restrict__ cnt) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(cnt + col[p], 1ull);
+}
+
+template <typename V>
+__global__ void transpose_fill_kernel(const uint32_t *__restrict__ idx, int64_t nnz,
+                                      const int32_t *__restrict__ row_index, int32_t *__restrict__ t_col,
+                                      int64_t *__restrict__ perm, const V *__restrict__ val,
+                                      V *__restrict__ t_val) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nnz) return;
+    const uint32_t p = idx[q];
+    t_col[q] = row_index[p];
+    if (perm) perm[q] = p;
+    if (t_val) t_val[q] = val[p];
+}
+
+template <typename V>
+__global__ void gather_kernel(const V *__restrict__ src, const int64_t *__restrict__ index, int64_t n,
+                              V *__restrict__ dst) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = index[s];
+        dst[s] = i >= 0 ? src[i] : V(0);
+    }
+}
+
+__global__ void compose_kernel(const int64_t *__restrict__ outer, const int64_t *__restrict__ inner,
+                               int64_t n, int64_t *__restrict__ out) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = outer[s];
+        out[s] = i >= 0 ? inner[i] : -1;
+    }
+}
+
+// out[p] = sum_b G[row_p, b] * X[col_p, b], b ascending.
+template <typename T>
+__global__ void sampled_dot_kernel(int64_t nnz, int k, const int32_t *__restrict__ row_index,
+                                   const int32_t *__restrict__ col, const T *__restrict__ G, int64_t ldg,
+                                   const T *__restrict__ X, int64_t ldx, T *__restrict__ out) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const T *g = G + (int64_t)row_index[p] * ldg;
+        const T *x = X + (int64_t)col[p] * ldx;
+        T s = 0;
+        for (int b = 0; b < k; ++b) s = fma(__ldg(g + b), __ldg(x + b), s);
+        out[p] = s;
+    }
+}
+
+unsigned grid_for(int64_t n, int threads) {
+    int64_t b = ceil_div(n, threads);
+    if (b > 152 * 64) b = 152 * 64;
+    return (unsigned)(b > 0 ? b : 1);
+}
+
+}  // namespace
+}  // namespace rgcsr
+
+using namespace rgcsr;
+
+RGCSR_API size_t rgcsr_transpose_workspace_bytes(int64_t nnz, int64_t n_rows, int64_t n_cols) {
+    if (nnz < 0 || n_rows < 0 || n_cols < 0) return 0;
+    return sort_workspace_bytes(nnz) + align_up((size_t)nnz * 4, 256) + scan_partials_bytes(n_cols) + 256;
+}
+
+RGCSR_API int rgcsr_csr_row_index(const rgcsr_csr *A, int32_t *row_index, rgcsr_stream_t stream) {
+    int st = check_csr(A);
+    if (st != RGCSR_OK) return st;
+    if (A->nnz == 0 || A->n_rows == 0) return RGCSR_OK;
+    if (!row_index) return RGCSR_ERR_INVALID_ARG;
+    RowPtr rp{A->row_ptr, A->row_ptr_type == RGCSR_I64};
+    row_index_kernel<<<grid_for(A->n_rows * 32, 256), 256, 0, (cudaStream_t)stream>>>(rp, A->n_rows, row_index);
+    return launch_status();
+}
+
+RGCSR_API int rgcsr_csr_transpose(const rgcsr_csr *A, int64_t *t_row_ptr, int32_t *t_col_idx,
+                                  int64_t *perm, void *t_values, void *workspace, size_t workspace_bytes,
+                                  rgcsr_stream_t stream) {
+    int st = check_csr(A);
+    if (st != RGCSR_OK) return st;
+    if (A->nnz >= (int64_t)UINT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
+    if (!t_row_ptr || (A->nnz > 0 && !t_col_idx)) return RGCSR_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < rgcsr_transpose_workspace_bytes(A->nnz, A->n_rows, A->n_cols))
+        return RGCSR_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nnz = A->nnz;
+    SortBuffers b = carve_sort(workspace, nnz);
+    char *after = static_cast<char *>(workspace) + sort_workspace_bytes(nnz);
+    int32_t *row_index = reinterpret_cast<int32_t *>(after);
+    int64_t *tpart = reinterpret_cast<int64_t *>(after + align_up((size_t)nnz * 4, 256));
+
+    // column counts -> t_row_ptr (exclusive scan, last = nnz)
+    RGCSR_CUDA_TRY(cudaMemsetAsync(t_row_ptr, 0, (size_t)(A->n_cols + 1) * sizeof(int64_t), s));
+    if (nnz > 0) {
+        column_counts_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(A->col_idx, nnz,
+                                                                reinterpret_cast<unsigned long long *>(t_row_ptr));
+        if ((st = launch_status()) != RGCSR_OK) return st;
+    }
+    if ((st = exclusive_scan_i64(t_row_ptr, A->n_cols, tpart, s)) != RGCSR_OK) return st;
+    if (nnz == 0) return RGCSR_OK;
+
+    if ((st = rgcsr_csr_row_index(A, row_index, stream)) != RGCSR_OK) return st;
+    int bits = 0;
+    while (bits < 31 && ((int64_t)1 << bits) < A->n_cols) ++bits;
+    const uint32_t *skeys = nullptr, *sidx = nullptr;
+    if ((st = radix_sort_indices(reinterpret_cast<const uint32_t *>(A->col_idx), nnz, bits, b, &skeys, &sidx, s)) != RGCSR_OK)
+        return st;
+    const unsigned blocks = (unsigned)ceil_div(nnz, 256);
+    if (A->value_type == RGCSR_F64)
+        transpose_fill_kernel<double><<<blocks, 256, 0, s>>>(sidx, nnz, row_index, t_col_idx, perm,
+                                                             static_cast<const double *>(A->values),
+                                                             static_cast<double *>(t_values));
+    else
+        transpose_fill_kernel<float><<<blocks, 256, 0, s>>>(sidx, nnz, row_index, t_col_idx, perm,
+                                                            static_cast<const float *>(A->values),
+                                                            static_cast<float *>(t_values));
+    return launch_status();
+}
+
+RGCSR_API int rgcsr_gather_values(const rgcsr_matrix *M, const void *src, const int64_t *src_index,
+                                  rgcsr_stream_t stream) {
+    if (!M || M->n_stored < 0) return RGCSR_ERR_INVALID_ARG;
+    if (M->n_stored == 0) return RGCSR_OK;
+    if (!M->values || !src || !src_index) return RGCSR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned g = grid_for(M->n_stored, 256);
+    if (M->value_type == RGCSR_F64)
+        gather_kernel<double><<<g, 256, 0, s>>>(static_cast<const double *>(src), src_index, M->n_stored,
+                                                static_cast<double *>(M->values));
+    else if (M->value_type == RGCSR_F32)
+        gather_kernel<float><<<g, 256, 0, s>>>(static_cast<const float *>(src), src_index, M->n_stored,
+                                               static_cast<float *>(M->values));
+    else
+        return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    return launch_status();
+}
+
+RGCSR_API int rgcsr_compose_index(const int64_t *outer, const int64_t *inner, int64_t n, int64_t *out,
+                                  rgcsr_stream_t stream) {
+    if (n < 0) return RGCSR_ERR_INVALID_ARG;
+    if (n == 0) return RGCSR_OK;
+    if (!outer || !inner || !out) return RGCSR_ERR_INVALID_ARG;
+    compose_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(outer, inner, n, out);
+    return launch_status();
+}
+
+RGCSR_API int rgcsr_sampled_dot(int64_t nnz, int32_t k, const int32_t *row_index, const int32_t *col_idx,
+                                const void *G, int64_t ldg, const void *X, int64_t ldx, void *out,
+                                int32_t value_type, rgcsr_stream_t stream) {
+    if (nnz < 0 || k < 0 || ldg < k || ldx < k) return RGCSR_ERR_INVALID_ARG;
+    if (nnz == 0) return RGCSR_OK;
+    if (!row_index || !col_idx || !out || (k > 0 && (!G || !X))) return RGCSR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned g = grid_for(nnz, 256);
+    if (value_type == RGCSR_F64)
+        sampled_dot_kernel<double><<<g, 256, 0, s>>>(nnz, k, row_index, col_idx, static_cast<const double *>(G),
+                                                     ldg, static_cast<const double *>(X), ldx,
+                                                     static_cast<double *>(out));
+    else if (value_type == RGCSR_F32)
+        sampled_dot_kernel<float><<<g, 256, 0, s>>>(nnz, k, row_index, col_idx, static_cast<const float *>(G),
+                                                    ldg, static_cast<const float *>(X), ldx,
+                                                    static_cast<float *>(out));
+    else
+        return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    return launch_status();
+}

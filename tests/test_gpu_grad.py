@@ -1,0 +1,164 @@
+"""GPU parity of the backward pass: the stable CSR transposition bit-exact
+against the oracle's counting sort; gradients of loss = ||A X||^2 with
+respect to values and X against the oracle's closed form (elementwise,
+scaled by the absolute-value product); FP64 central finite differences on
+the n = 4,096 Laplacian; matrix (b) with a batch of 8 right-hand sides."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import TAU, assert_within_bound, rounded_values
+from paper_1012_2270_gb300 import synth
+from paper_1012_2270_gb300 import _lib as L
+from paper_1012_2270_gb300.autograd import SparseOperator, spmm
+from paper_1012_2270_gb300.rgcsr import _ptr, csr_struct, _stream_ptr
+
+pytestmark = pytest.mark.gpu
+
+NP = {"f32": np.float32, "f64": np.float64}
+TT = {"f32": torch.float32, "f64": torch.float64}
+
+
+def gpu_transpose(A):
+    rp = torch.from_numpy(A.rowptr).cuda()
+    col = torch.from_numpy(A.col).cuda()
+    val = torch.from_numpy(A.val).cuda()
+    nb = L.lib().rgcsr_transpose_workspace_bytes(A.nnz, A.n_rows, A.n_cols)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    trp = torch.empty(A.n_cols + 1, dtype=torch.int64, device="cuda")
+    tc = torch.empty(A.nnz, dtype=torch.int32, device="cuda")
+    perm = torch.empty(A.nnz, dtype=torch.int64, device="cuda")
+    tv = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
+    L.call("rgcsr_csr_transpose", ctypes.byref(csr_struct(rp, col, val, A.n_cols)), _ptr(trp), _ptr(tc),
+           _ptr(perm), _ptr(tv), _ptr(ws), nb, _stream_ptr())
+    return trp.cpu().numpy(), tc.cpu().numpy(), perm.cpu().numpy(), tv.cpu().numpy()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_transpose_bit_exact(seed):
+    rng = np.random.default_rng(seed)
+    n, m = [(3000, 2000), (1, 700), (5000, 300)][seed]
+    Ls = rng.integers(0, min(m, 60) + 1, n)
+    A = synth.random_csr(n, m, Ls, seed=seed)
+    trp, tc, perm = oracle.csr_transpose(A.rowptr, A.col, m)
+    g = gpu_transpose(A)
+    assert np.array_equal(g[0], trp) and np.array_equal(g[1], tc) and np.array_equal(g[2], perm)
+    assert np.array_equal(g[3], A.val[perm])
+
+
+def test_transpose_many_columns_and_empty():
+    # more than 2^16 columns (three radix passes), empty rows and columns
+    rng = np.random.default_rng(5)
+    A = synth.random_csr(20000, 300000, rng.integers(0, 8, 20000), seed=5)
+    trp, tc, perm = oracle.csr_transpose(A.rowptr, A.col, A.n_cols)
+    g = gpu_transpose(A)
+    assert np.array_equal(g[0], trp) and np.array_equal(g[1], tc) and np.array_equal(g[2], perm)
+    E = synth.random_csr(10, 7, np.zeros(10, np.int64))
+    assert gpu_transpose(E)[0].tolist() == [0] * 8
+
+
+def abs_bounds(A, vals, X, G):
+    """|A^T||G| and sum_b |G[row,b]||X[col,b]| from the oracle."""
+    trp, tc, perm = oracle.csr_transpose(A.rowptr, A.col, A.n_cols)
+    dX_abs, _ = oracle.csr_spmm(trp, tc, np.abs(vals)[perm], np.abs(G))
+    _, dval_abs = oracle.spmm_grads(A.rowptr, A.col, vals, np.abs(X), np.abs(G), A.n_cols)
+    return dX_abs, dval_abs
+
+
+def check_grads(A, dtype, k, group_size=32, seed=0):
+    vals = rounded_values(A.val, dtype)
+    X = synth.uniform_matrix(A.n_cols, k, seed=seed).astype(NP[dtype]).astype(np.float64)
+    op = SparseOperator(A.rowptr, A.col, A.n_cols, dtype=TT[dtype], group_size=group_size)
+    v = torch.tensor(vals, dtype=TT[dtype], device="cuda", requires_grad=True)
+    Xt = torch.tensor(X, dtype=TT[dtype], device="cuda", requires_grad=True)
+    Y = spmm(op, v, Xt)
+    loss = (Y * Y).sum()
+    loss.backward()
+    # the oracle's gradient for the upstream gradient the GPU actually used
+    Gy = (2.0 * Y.detach()).double().cpu().numpy()
+    dX_ref, dval_ref = oracle.spmm_grads(A.rowptr, A.col, vals, X, Gy, A.n_cols)
+    dX_abs, dval_abs = abs_bounds(A, vals, X, Gy)
+    assert_within_bound(Xt.grad.double().cpu().numpy().ravel(), dX_ref.ravel(), dX_abs.ravel(),
+                        TAU[dtype], f"dX {A.name} {dtype}")
+    assert_within_bound(v.grad.double().cpu().numpy(), dval_ref, dval_abs, TAU[dtype],
+                        f"dval {A.name} {dtype}")
+    return op
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_grads_ragged(dtype, k):
+    rng = np.random.default_rng(k)
+    Ls = rng.integers(0, 25, 1200)
+    Ls[[2, 600]] = [900, 300]
+    A = synth.random_csr(1200, 1500, Ls, seed=k)
+    check_grads(A, dtype, k)
+    check_grads(A, dtype, k, group_size=8)
+
+
+def test_values_refresh_between_calls():
+    A = synth.workload_small_laplacian()
+    op = SparseOperator(A.rowptr, A.col, A.n_cols, dtype=torch.float64)
+    x = torch.from_numpy(synth.uniform_vector(A.n_cols, 0)).cuda()
+    for scale in (1.0, -2.5, 0.0):
+        v = torch.from_numpy(A.val * scale).cuda()
+        y = spmm(op, v, x).cpu().numpy()
+        y_ref, absy = oracle.csr_spmv(A.rowptr, A.col, A.val * scale, x.cpu().numpy())
+        assert_within_bound(y, y_ref, absy, 1e-12, f"scale {scale}")
+
+
+def test_fp64_finite_differences_laplacian():
+    A = synth.workload_small_laplacian()
+    op = SparseOperator(A.rowptr, A.col, A.n_cols, dtype=torch.float64)
+    rng = np.random.default_rng(0)
+    vals = A.val + 0.1 * rng.standard_normal(A.nnz)
+    X = synth.uniform_matrix(A.n_cols, 2, seed=3)
+    v = torch.tensor(vals, device="cuda", requires_grad=True)
+    Xt = torch.tensor(X, device="cuda", requires_grad=True)
+    loss = (spmm(op, v, Xt) ** 2).sum()
+    loss.backward()
+
+    def f(vv, XX):
+        with torch.no_grad():
+            return float((spmm(op, vv, XX) ** 2).sum())
+    vt, Xd = torch.tensor(vals, device="cuda"), torch.tensor(X, device="cuda")
+    # the loss is quadratic in every value and every entry of X, so central
+    # differences carry no truncation error; a moderate step keeps the
+    # cancellation error of the O(1e4) loss well below the tolerance
+    for p in rng.integers(0, A.nnz, 40):
+        h = 1e-3 * max(1.0, abs(vals[p]))
+        vp, vm = vt.clone(), vt.clone()
+        vp[p] += h
+        vm[p] -= h
+        fd = (f(vp, Xd) - f(vm, Xd)) / (2 * h)
+        g = float(v.grad[p])
+        assert abs(fd - g) <= 1e-6 * max(1.0, abs(g)), (p, fd, g)
+    for idx in [(0, 0), (A.n_cols - 1, 1), (2048, 0), (63, 1)]:
+        h = 1e-3 * max(1.0, abs(X[idx]))
+        Xp, Xm = Xd.clone(), Xd.clone()
+        Xp[idx] += h
+        Xm[idx] -= h
+        fd = (f(vt, Xp) - f(vt, Xm)) / (2 * h)
+        g = float(Xt.grad[idx])
+        assert abs(fd - g) <= 1e-6 * max(1.0, abs(g)), (idx, fd, g)
+    # and the oracle's closed form agrees with the GPU in FP64
+    Gy = 2.0 * oracle.csr_spmm(A.rowptr, A.col, vals, X)[0]
+    dX_ref, dval_ref = oracle.spmm_grads(A.rowptr, A.col, vals, X, Gy, A.n_cols)
+    assert np.allclose(v.grad.cpu().numpy(), dval_ref, rtol=1e-10, atol=1e-10)
+    assert np.allclose(Xt.grad.cpu().numpy(), dX_ref, rtol=1e-10, atol=1e-10)
+
+
+def test_gradcheck_tiny():
+    A = synth.random_csr(40, 30, np.random.default_rng(1).integers(0, 8, 40), seed=1)
+    op = SparseOperator(A.rowptr, A.col, A.n_cols, dtype=torch.float64, group_size=4)
+    v = torch.tensor(A.val, device="cuda", requires_grad=True)
+    X = torch.tensor(synth.uniform_matrix(30, 3, seed=2), device="cuda", requires_grad=True)
+    assert torch.autograd.gradcheck(lambda vv, XX: spmm(op, vv, XX), (v, X), eps=1e-6, atol=1e-8)
+
+
+def test_grads_full_size_b_batch8():
+    A = synth.workload_b()
+    check_grads(A, "f32", 8)
