@@ -177,6 +177,43 @@ int rgcsr_spmm(const rgcsr_matrix *M, int32_t k, const void *X, int64_t ldx, voi
                int64_t ldy, rgcsr_stream_t stream);
 
 /* ----------------------------------------------------------------------- */
+/* Batched SpMV: many RgCSR matrices of uneven sizes in one launch (not in  */
+/* the paper).  The members' arrays are concatenated; member m uses         */
+/*   values/columns from val_off, row_lengths/row_scale/y from row_off,     */
+/*   its own group pointers (n_groups+1 entries starting at 0) from         */
+/*   group_off, x from x_off,                                               */
+/* and its own group size.  All members share one value type.              */
+/* ----------------------------------------------------------------------- */
+typedef struct {
+    int64_t n_rows, n_cols;
+    int64_t val_off, row_off, group_off, x_off;
+    int32_t group_size;
+    int32_t reserved;
+} rgcsr_batch_desc;
+
+typedef struct {
+    int32_t n_matrices;
+    int32_t value_type;             /* as in rgcsr_matrix                     */
+    int64_t n_tasks;                /* from rgcsr_batch_tasks                  */
+    const rgcsr_batch_desc *desc;   /* device [n_matrices]                     */
+    const int32_t *tasks;           /* device [2 * n_tasks]: (member, first row) */
+    const void *values;             /* concatenated slabs                      */
+    const int32_t *columns;
+    const int64_t *group_ptr;
+    const int32_t *row_lengths;
+    const float *row_scale;         /* BF16/F16 storage only                   */
+} rgcsr_batch;
+
+/* HOST function: cuts every member into blocks of 32 rows and writes one
+ * (member, first row) pair per block into the host array `tasks` (capacity
+ * pairs; NULL to count only).  *n_tasks receives the number of pairs. */
+int rgcsr_batch_tasks(const rgcsr_batch_desc *desc, int32_t n_matrices, int32_t *tasks,
+                      int64_t capacity, int64_t *n_tasks);
+/* y_m = A_m x_m for every member, one persistent launch; no host sync and
+ * no allocation, so it may be captured in a CUDA graph.  Async. */
+int rgcsr_spmv_batched(const rgcsr_batch *B, const void *x, void *y, rgcsr_stream_t stream);
+
+/* ----------------------------------------------------------------------- */
 /* Reduced-precision value storage (not in the paper, which stores single  */
 /* or double precision).  Per row i the scale is                            */
 /*   s_i = 2^ceil(log2 max_j |a_ij|)  (1 for an empty or all-zero row,     */

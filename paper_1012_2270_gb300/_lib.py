@@ -52,8 +52,19 @@ class Hyb(ctypes.Structure):
                 ("ell_val", P), ("ell_col", P), ("coo_row", P), ("coo_col", P), ("coo_val", P)]
 
 
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("n_rows", I64), ("n_cols", I64), ("val_off", I64), ("row_off", I64),
+                ("group_off", I64), ("x_off", I64), ("group_size", I32), ("reserved", I32)]
+
+
+class Batch(ctypes.Structure):
+    _fields_ = [("n_matrices", I32), ("value_type", I32), ("n_tasks", I64), ("desc", P), ("tasks", P),
+                ("values", P), ("columns", P), ("group_ptr", P), ("row_lengths", P), ("row_scale", P)]
+
+
 _PCSR, _PM, _PL, _PH = (ctypes.POINTER(CSR), ctypes.POINTER(Matrix),
                         ctypes.POINTER(Launch), ctypes.POINTER(Hyb))
+_PBD, _PB = ctypes.POINTER(BatchDesc), ctypes.POINTER(Batch)
 D = ctypes.c_double
 PI32, PD = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)
 
@@ -74,6 +85,8 @@ SIGNATURES = {
     "rgcsr_gather_values": (ctypes.c_int, [_PM, P, P, P]),
     "rgcsr_compose_index": (ctypes.c_int, [P, P, I64, P, P]),
     "rgcsr_sampled_dot": (ctypes.c_int, [I64, I32, P, P, P, I64, P, I64, P, I32, P]),
+    "rgcsr_batch_tasks": (ctypes.c_int, [_PBD, I32, P, I64, ctypes.POINTER(I64)]),
+    "rgcsr_spmv_batched": (ctypes.c_int, [_PB, P, P, P]),
     "rgcsr_dot_workspace_bytes": (SZ, []),
     "rgcsr_dot": (ctypes.c_int, [I64, P, P, P, P, SZ, I32, P]),
     "rgcsr_axpby": (ctypes.c_int, [I64, D, P, D, P, I32, P]),

@@ -1,0 +1,155 @@
+"""Autotuning of the RgCSR launch parameters on the current GPU.
+
+* ``model_group_size``: the group size G from a byte model -- the slots one
+  SpMV streams, n_stored(G) * (value + index bytes), plus 8 bytes of group
+  pointer per group -- preferring G = 32 (full 128-byte slot-rows, the
+  TMA-staged kernel) when it is within 5% of the best.  The paper fixed G
+  per GPU by experiment (Sec. 4.3: 128 was best on a GTX 280); here the
+  choice follows the matrix.
+* ``tune``: times candidate (group size, kernel, variant) configurations
+  with CUDA events, flushing L2 between launches, and caches the fastest
+  per (matrix pattern, value type, GPU name) in a JSON file.
+* ``tune_hyb_width``: the same for the ELL width of the HYB format around
+  the library's byte-cost rule.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+import zlib
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+CACHE_PATH = os.environ.get("RGCSR_TUNE_CACHE",
+                            os.path.join(os.path.expanduser("~"), ".cache", "rgcsr", "autotune.json"))
+
+
+def stored_slots(lengths: np.ndarray, G: int) -> int:
+    """sum over groups of R_g * K_g (stored slots, padding included)."""
+    n = lengths.size
+    if n == 0:
+        return 0
+    pad = (-n) % G
+    Lp = np.concatenate([lengths, np.zeros(pad, lengths.dtype)]).reshape(-1, G)
+    K = Lp.max(axis=1).astype(np.int64)
+    R = np.full(K.size, G, np.int64)
+    R[-1] = n - G * (K.size - 1)
+    return int((R * K).sum())
+
+
+def model_group_size(rowptr, value_bytes: int, candidates=(8, 16, 32, 64, 128)) -> int:
+    lengths = np.diff(np.asarray(rowptr, dtype=np.int64))
+    n = lengths.size
+    cost = {G: stored_slots(lengths, G) * (value_bytes + 4) + ((n + G - 1) // G) * 8 for G in candidates}
+    best = min(cost.values())
+    if 32 in cost and cost[32] <= 1.05 * best:
+        return 32
+    return min(candidates, key=lambda G: (cost[G], -G))
+
+
+def signature(rowptr, col, n_cols: int, dtype: torch.dtype) -> str:
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    c = np.ascontiguousarray(col, dtype=np.int32)
+    h = zlib.crc32(rp.tobytes())
+    h = zlib.crc32(c[: 1 << 20].tobytes(), h)
+    gpu = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    return f"{rp.size - 1}x{n_cols}:{int(rp[-1])}:{h:08x}:{str(dtype)}:{gpu}"
+
+
+def _load_cache() -> dict:
+    try:
+        with open(CACHE_PATH) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store_cache(cache: dict) -> None:
+    try:
+        os.makedirs(os.path.dirname(CACHE_PATH), exist_ok=True)
+        tmp = CACHE_PATH + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, CACHE_PATH)
+    except OSError:
+        pass
+
+
+def _time(fn, reps: int, flush: torch.Tensor) -> float:
+    """Median time in microseconds of fn() with L2 flushed before each call."""
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(1e3 * e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def candidates(rowptr, dtype: torch.dtype):
+    Gm = model_group_size(rowptr, dtype.itemsize)
+    cands = [dict(group_size=32, kernel=L.KERNEL_AUTO)]
+    cands += [dict(group_size=32, kernel=L.KERNEL_TMA, variant=v) for v in range(4)]
+    for G in sorted({32, Gm, 16, 64}):
+        cands.append(dict(group_size=G, kernel=L.KERNEL_SPLIT))
+        cands.append(dict(group_size=G, kernel=L.KERNEL_LEAN))
+    return cands
+
+
+def tune(rowptr, col, val, n_cols: int, dtype: torch.dtype = torch.float32, reps: int = 10,
+         use_cache: bool = True) -> dict:
+    """Fastest configuration for this matrix on this GPU, e.g.
+    {"group_size": 32, "kernel": 3, "variant": 0, "us": 30.6}."""
+    from .rgcsr import RgCSRMatrix
+    key = signature(rowptr, col, n_cols, dtype)
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        return cache[key]
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")     # 256 MB > L2
+    x = torch.rand(n_cols, dtype=torch.float64 if dtype == torch.float64 else torch.float32, device="cuda")
+    built = {}
+    results = []
+    for c in candidates(rowptr, dtype):
+        G = c["group_size"]
+        if G not in built:
+            built[G] = RgCSRMatrix.from_csr(rowptr, col, val, n_cols, group_size=G, dtype=dtype)
+        M = built[G]
+        kw = {k: v for k, v in c.items() if k != "group_size"}
+        try:
+            y = M.spmv(x, **kw)
+        except L.RgCSRError:
+            continue                      # configuration not valid for this matrix
+        us = _time(lambda: M.spmv(x, out=y, **kw), reps, flush)
+        results.append(dict(c, us=us))
+    best = min(results, key=lambda r: r["us"])
+    if use_cache:
+        cache = _load_cache()
+        cache[key] = best
+        _store_cache(cache)
+    return best
+
+
+def tune_hyb_width(rowptr, col, val, n_cols: int, dtype: torch.dtype = torch.float32, reps: int = 10) -> dict:
+    """Times ELL widths around the byte-cost rule's choice."""
+    from .rgcsr import HybMatrix
+    base = HybMatrix.from_csr(rowptr, col, val, n_cols, dtype=dtype)
+    k0, kmax = base.ell_width, base.s.max_row_len
+    widths = sorted({w for w in (k0 - 2, k0 - 1, k0, k0 + 1, k0 + 2, 2 * k0) if 0 <= w <= kmax})
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    x = torch.rand(n_cols, dtype=torch.float64 if dtype == torch.float64 else torch.float32, device="cuda")
+    results = []
+    for w in widths:
+        H = base if w == k0 else HybMatrix.from_csr(rowptr, col, val, n_cols, ell_width=w, dtype=dtype)
+        y = H.spmv(x)
+        results.append(dict(ell_width=w, us=_time(lambda: H.spmv(x, out=y), reps, flush), rule=(w == k0)))
+        del H
+    return min(results, key=lambda r: r["us"])

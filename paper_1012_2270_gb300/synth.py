@@ -123,12 +123,18 @@ def stencil27_random(nx: int, seed: int = 0) -> CSRMatrix:
 
 
 def _distinct_sorted_columns(rng, lengths: np.ndarray, n_cols: int) -> np.ndarray:
-    """Per row, lengths[i] distinct columns uniform in [0, n_cols), sorted."""
+    """Per row, lengths[i] distinct columns uniform in [0, n_cols), sorted.
+
+    Rows longer than n_cols / 8 draw a partial permutation; the others draw
+    with replacement and redraw duplicates until none are left."""
+    lengths = np.asarray(lengths, dtype=np.int64)
     n = lengths.size
-    nnz = int(lengths.sum())
-    rows = np.repeat(np.arange(n, dtype=np.int64), lengths)
+    dense = lengths > n_cols // 8
+    Ls = np.where(dense, 0, lengths)
+    nnz = int(Ls.sum())
+    rows = np.repeat(np.arange(n, dtype=np.int64), Ls)
     cols = rng.integers(0, n_cols, nnz, dtype=np.int64)
-    while True:
+    while nnz:
         key = rows * n_cols + cols
         order = np.argsort(key, kind="stable")
         key = key[order]
@@ -137,8 +143,21 @@ def _distinct_sorted_columns(rng, lengths: np.ndarray, n_cols: int) -> np.ndarra
         dup[1:] = key[1:] == key[:-1]
         nd = int(dup.sum())
         if nd == 0:
-            return cols.astype(np.int32)
+            break
         cols[dup] = rng.integers(0, n_cols, nd, dtype=np.int64)
+    if not dense.any():
+        return cols.astype(np.int32)
+    out = np.empty(int(lengths.sum()), np.int32)
+    ptr = np.zeros(n + 1, np.int64)
+    np.cumsum(lengths, out=ptr[1:])
+    sparse_ptr = np.zeros(n + 1, np.int64)
+    np.cumsum(Ls, out=sparse_ptr[1:])
+    for i in range(n):
+        if dense[i]:
+            out[ptr[i]:ptr[i + 1]] = np.sort(rng.choice(n_cols, int(lengths[i]), replace=False))
+        else:
+            out[ptr[i]:ptr[i + 1]] = cols[sparse_ptr[i]:sparse_ptr[i + 1]]
+    return out
 
 
 def power_law_lengths(n: int, rng, s: float = 2.0, scale: float = 2.69,

@@ -1,0 +1,53 @@
+"""Host-side logic without a GPU: the autotuner's padding model against the
+oracle's layout sizes, its group-size choice, and the batch task builder
+(a host function of the C ABI)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1012_2270_gb300 import build as B
+from paper_1012_2270_gb300 import synth
+from paper_1012_2270_gb300 import _lib as L
+from paper_1012_2270_gb300.autotune import model_group_size, stored_slots
+
+
+@pytest.mark.parametrize("G", [1, 3, 8, 32, 64, 128])
+def test_stored_slots_matches_oracle(G):
+    rng = np.random.default_rng(G)
+    for n in (0, 1, 31, 32, 33, 1000):
+        Ls = rng.integers(0, 50, n)
+        rowptr = np.concatenate([[0], np.cumsum(Ls)])
+        _, gp = oracle.rgcsr_sizes(rowptr, G)
+        assert stored_slots(Ls, G) == gp[-1]
+
+
+def test_model_group_size_choices():
+    # uniform rows: no padding at any G -> prefer 32
+    assert model_group_size(synth.laplacian_3d(12).rowptr, 4) == 32
+    # power-law rows: padding grows with G -> the smallest group size wins
+    A = synth.power_law(20000, seed=1)
+    G = model_group_size(A.rowptr, 4)
+    L_ = A.row_lengths()
+    assert G == 8 and stored_slots(L_, 8) < stored_slots(L_, 32)
+
+
+def test_batch_tasks_host_function():
+    B.build()
+    lib = L.lib()
+    sizes = [1, 31, 32, 33, 100, 0, 64]
+    descs = (L.BatchDesc * len(sizes))()
+    for i, n in enumerate(sizes):
+        descs[i].n_rows, descs[i].group_size = n, 32
+    cnt = ctypes.c_int64(0)
+    assert lib.rgcsr_batch_tasks(descs, len(sizes), None, 0, ctypes.byref(cnt)) == 0
+    assert cnt.value == sum((n + 31) // 32 for n in sizes)
+    tasks = np.empty(2 * cnt.value, np.int32)
+    assert lib.rgcsr_batch_tasks(descs, len(sizes), tasks.ctypes.data_as(ctypes.c_void_p), cnt.value,
+                                 ctypes.byref(cnt)) == 0
+    exp = [(m, r) for m, n in enumerate(sizes) for r in range(0, n, 32)]
+    assert [tuple(t) for t in tasks.reshape(-1, 2)] == exp
+    small = np.empty(2, np.int32)
+    assert lib.rgcsr_batch_tasks(descs, len(sizes), small.ctypes.data_as(ctypes.c_void_p), 1,
+                                 ctypes.byref(cnt)) == L.RGCSR_ERR_WORKSPACE
