@@ -1,14 +1,16 @@
 #!/usr/bin/env python
 """RgCSR SpMV benchmark on GB300.
 
-One step = one RgCSR SpMV (group size 32, default kernel) of each of the
-three large synthetic matrices in FP32 and in FP64 (six SpMVs):
+One step = one RgCSR SpMV of each of the three large synthetic matrices in
+FP32 and in FP64 (six SpMVs), each in the configuration (group size,
+kernel, long-row segment schedule) the autotuner picked on this GPU:
   (a) 3D 7-point Laplacian 128^3        n = 2,097,152  nnz = 14,581,760
   (b) power-law rows, n = 10^6          nnz ~ 15.6M, longest row 10,000
   (c) 27-point stencil 96^3, U[-1,1]    n = 884,736    nnz = 23,393,656
 value = algorithmic bytes of the six SpMVs (values + columns of the
-non-zeros, row lengths, group pointers, x once, y once; padding excluded)
-per second, whole job.  Inputs stay resident in HBM; each step streams
+non-zeros, row lengths, group pointers at G = 32, x once, y once; padding
+and the segment lists excluded, so the count does not depend on the
+configuration) per second, whole job.  Inputs stay resident in HBM; each step streams
 ~1.3 GB of algorithmic data (more with padding), far more than the 129 MB
 L2, so no SpMV finds its matrix in L2.
 
@@ -46,7 +48,7 @@ CASES = [("a", synth.workload_a), ("b", synth.workload_b), ("c", synth.workload_
 DTYPES = ["f32", "f64"]
 VB = {"f32": 4, "f64": 8}
 NP = {"f32": np.float32, "f64": np.float64}
-WORKLOAD = ("RgCSR SpMV, G=32, FP32 and FP64, of (a) 3D 7-point Laplacian 128^3, "
+WORKLOAD = ("RgCSR SpMV, autotuned group size/kernel, FP32 and FP64, of (a) 3D 7-point Laplacian 128^3, "
             "(b) power-law rows n=1e6 (Zipf(2) lengths, max 10,000, natural row order), "
             "(c) 27-point stencil 96^3")
 
@@ -80,6 +82,21 @@ def load_cases():
 
 def case_bytes(A, n_groups, dtype):
     return roofline.rgcsr_spmv_bytes(A.n_rows, A.n_cols, A.nnz, n_groups, VB[dtype])
+
+
+def kernel_name(cfg, M, A, dt):
+    """The kernel that a configuration runs (the library's dispatch rules)."""
+    t = "float" if dt == "f32" else "double"
+    if "long_rows" in cfg:
+        return f"rgcsr_spmv_split+segments<{t}>"
+    k = cfg.get("kernel", 0)
+    if k == 0:
+        dense = M.n_stored * 4 <= M.nnz * 5
+        if dense and M.group_size == 32 and (dt == "f32" or A.nnz <= 8 * A.n_rows):
+            k = 3
+        else:
+            k = 4 if dense else 2
+    return {1: "rgcsr_spmv_paper", 2: "rgcsr_spmv_split", 3: "rgcsr_spmv_tma", 4: "rgcsr_spmv_lean"}[k] + f"<{t}>"
 
 
 # ---------------------------------------------------------------------------
@@ -234,28 +251,26 @@ def run_ours(args):
     mats = load_cases()
 
     # ---- convert (one-off) ----
+    from paper_1012_2270_gb300 import autotune
     cases = []
     for name, A, x in mats:
         for dt in DTYPES:
-            M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dt]), A.n_cols,
-                                     group_size=GROUP, dtype=getattr(torch, "float32" if dt == "f32" else "float64"))
+            tdt = torch.float32 if dt == "f32" else torch.float64
+            vals = A.val.astype(NP[dt])
+            # group size, kernel and long-row schedule chosen by timing on this GPU
+            cfg = autotune.tune(A.rowptr, A.col, vals, A.n_cols, dtype=tdt, reps=5, use_cache=False)
+            M, kw = autotune.build(A.rowptr, A.col, vals, A.n_cols, cfg, tdt)
             xd = torch.from_numpy(x.astype(NP[dt])).to(dev)
             yd = torch.empty(A.n_rows, dtype=xd.dtype, device=dev)
-            nb = case_bytes(A, M.s.n_groups, dt)
-            # the library's default dispatch (see RGCSR_KERNEL_AUTO)
-            dense = M.n_stored * 4 <= M.nnz * 5
-            if dense and (dt == "f32" or A.nnz <= 8 * A.n_rows):
-                kname = "rgcsr_spmv_tma"
-            else:
-                kname = "rgcsr_spmv_lean" if dense else "rgcsr_spmv_split"
-            cases.append(dict(key=f"{name}_{dt}", name=name, dt=dt, A=A, M=M, x=xd, y=yd, bytes=nb,
-                              nnz=A.nnz, kernel=f"{kname}<{'float' if dt == 'f32' else 'double'}>",
+            nb = case_bytes(A, (A.n_rows + GROUP - 1) // GROUP, dt)
+            cases.append(dict(key=f"{name}_{dt}", name=name, dt=dt, A=A, M=M, kw=kw, x=xd, y=yd, bytes=nb,
+                              nnz=A.nnz, kernel=kernel_name(cfg, M, A, dt), config=cfg,
                               pad_pct=M.artificial_zero_percent()))
     torch.cuda.synchronize()
     step_bytes = sum(c["bytes"] for c in cases)
 
     def launch(c):
-        c["M"].spmv(c["x"], out=c["y"])
+        c["M"].spmv(c["x"], out=c["y"], **c["kw"])
 
     # ---- warm-up ----
     for _ in range(args.warmup):
@@ -296,7 +311,8 @@ def run_ours(args):
     for c, ms in zip(cases, per_case_ms):
         detail[c["key"]] = {"gbs": c["bytes"] / (ms * 1e-3) / 1e9, "gflops": 2 * c["nnz"] / (ms * 1e-3) / 1e9,
                             "us": ms * 1e3, "pct_of_8tbs": 100 * c["bytes"] / (ms * 1e-3) / 1e9 / roofline.NOMINAL_HBM_GBS,
-                            "artificial_zero_pct": c["pad_pct"]}
+                            "artificial_zero_pct": c["pad_pct"], "kernel": c["kernel"],
+                            "config": {k: v for k, v in c["config"].items() if k != "us"}}
 
     # ---- roofline of the dominant kernel ----
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -328,14 +344,14 @@ def run_ours(args):
     d2h = sum(h[1].numel() * h[1].element_size() for h in host)
     Ke = max(3, K // 4)
     for c, h in zip(cases, host):
-        c["M"].spmv_host(*h)
+        c["M"].spmv_host(*h, **c["kw"])
     torch.cuda.synchronize()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(Ke):
         for c, h in zip(cases, host):
-            c["M"].spmv_host(*h)
+            c["M"].spmv_host(*h, **c["kw"])
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -348,33 +364,10 @@ def run_ours(args):
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "note": "per step and case: x host->device, SpMV, y device->host (pinned), matrix resident"}
 
-    # ---- forms beside plain: HYB comparator ----
+    # ---- forms beside plain ----
     forms = {}
-    if not args.no_forms:
-        hyb = {}
-        for name, A, x in mats:
-            for dt in DTYPES:
-                H = HybMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dt]), A.n_cols,
-                                       dtype=getattr(torch, "float32" if dt == "f32" else "float64"))
-                xd = torch.from_numpy(x.astype(NP[dt])).to(dev)
-                yd = torch.empty(A.n_rows, dtype=xd.dtype, device=dev)
-                for _ in range(3):
-                    H.spmv(xd, out=yd)
-                reps = max(5, K // 10)
-                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a0.record(stream)
-                for _ in range(reps):
-                    H.spmv(xd, out=yd)
-                a1.record(stream)
-                torch.cuda.synchronize()
-                ms = a0.elapsed_time(a1) / reps
-                nb = roofline.hyb_spmv_bytes(A.n_rows, A.n_cols, A.nnz, H.nnz_coo, VB[dt])
-                key = f"{name}_{dt}"
-                hyb[key] = {"gbs": nb / (ms * 1e-3) / 1e9, "gflops": 2 * A.nnz / (ms * 1e-3) / 1e9,
-                            "us": ms * 1e3, "ell_width": H.ell_width, "nnz_coo": H.nnz_coo,
-                            "rgcsr_over_hyb": (ms * 1e-3) / (detail[key]["us"] * 1e-6)}
-                del H
-        forms["hyb"] = hyb
+    if not args.no_forms and rank == 0:
+        forms = measure_forms(mats, cases, detail, dev, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -402,6 +395,228 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------------
+# the other forms, each beside its plain counterpart
+# ---------------------------------------------------------------------------
+def _ev():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def time_rotating(fns, reps, stream):
+    """Mean microseconds per call of each fn, calling them in turn (so that
+    consecutive calls touch different data and L2 holds none of it)."""
+    import torch
+    for f in fns:
+        f()
+    torch.cuda.synchronize()
+    ev = [[_ev() for _ in fns] for _ in range(reps)]
+    for r in range(reps):
+        for i, f in enumerate(fns):
+            ev[r][i][0].record(stream)
+            f()
+            ev[r][i][1].record(stream)
+    torch.cuda.synchronize()
+    return [1e3 * statistics.fmean(ev[r][i][0].elapsed_time(ev[r][i][1]) for r in range(reps))
+            for i in range(len(fns))]
+
+
+def time_flushed(fn, reps, flush, stream):
+    """Median microseconds of fn with L2 flushed (a 256 MB write) before each call."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = _ev()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(1e3 * e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def max_scaled_error(y, y_ref, absy):
+    import torch
+    err = (y.double() - y_ref.double()).abs()
+    den = absy.double()
+    ok = den > 0
+    return float((err[ok] / den[ok]).max()) if bool(ok.any()) else 0.0
+
+
+def measure_forms(mats, cases, detail, dev, stream):
+    import torch
+    from paper_1012_2270_gb300 import solvers
+    from paper_1012_2270_gb300.autograd import SparseOperator, spmm
+    from paper_1012_2270_gb300.autotune import model_group_size
+    from paper_1012_2270_gb300.batched import BatchedRgCSR
+    from paper_1012_2270_gb300.rgcsr import HybMatrix, RgCSRMatrix
+
+    forms = {}
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    by = {c["key"]: c for c in cases}
+    TT = {"f32": torch.float32, "f64": torch.float64}
+
+    # -- HYB (ELL + COO), the paper's comparison format -----------------------
+    hyb = []
+    for name, A, x in mats:
+        for dt in DTYPES:
+            H = HybMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dt]), A.n_cols, dtype=TT[dt])
+            c = by[f"{name}_{dt}"]
+            hyb.append((c, H, torch.empty_like(c["y"])))
+    us = time_rotating([lambda h=h: h[1].spmv(h[0]["x"], out=h[2]) for h in hyb], 30, stream)
+    forms["hyb"] = {}
+    for (c, H, _), t in zip(hyb, us):
+        A = c["A"]
+        nb = roofline.hyb_spmv_bytes(A.n_rows, A.n_cols, A.nnz, H.nnz_coo, VB[c["dt"]])
+        forms["hyb"][c["key"]] = {"gbs": nb / t / 1e3, "gflops": 2 * A.nnz / t / 1e3, "us": t,
+                                  "ell_width": H.ell_width, "nnz_coo": H.nnz_coo,
+                                  "rgcsr_speedup": t / detail[c["key"]]["us"]}
+    del hyb
+
+    # -- reduced-precision values (bf16 / fp16 + per-row scale) ----------------
+    # The error is taken against the library's FP64 product (itself within
+    # 1e-12 |A||x| of the CPU oracle in the parity tests), scaled by |A||x|.
+    quant, ref = [], {}
+    for name in ("a", "b", "c"):
+        c64, c32 = by[f"{name}_f64"], by[f"{name}_f32"]
+        A = c32["A"]
+        absA = RgCSRMatrix.from_csr(A.rowptr, A.col, np.abs(A.val), A.n_cols, dtype=torch.float64)
+        ref[name] = (c64["M"].spmv(c64["x"]), absA.spmv(c64["x"].abs()))
+        del absA
+        for fmt in ("bf16", "f16"):
+            Q = c64["M"].quantized(fmt)
+            quant.append((name, fmt, Q, c32["x"], torch.empty(A.n_rows, dtype=torch.float32, device=dev), A))
+    us = time_rotating([lambda q=q: q[2].spmv(q[3], out=q[4]) for q in quant], 30, stream)
+    forms["quantized"] = {}
+    for (name, fmt, Q, x32, y, A), t in zip(quant, us):
+        nb = roofline.rgcsr_spmv_bytes(A.n_rows, A.n_cols, A.nnz, Q.s.n_groups, 2, x_bytes=4, row_scale=True)
+        y64, absy = ref[name]
+        forms["quantized"][f"{name}_{fmt}"] = {
+            "gbs": nb / t / 1e3, "gflops": 2 * A.nnz / t / 1e3, "us": t,
+            "speedup_vs_f32": detail[f"{name}_f32"]["us"] / t,
+            "max_err_over_absAx_vs_f64": max_scaled_error(y, y64, absy)}
+    del quant, ref
+
+    # -- multi-RHS SpMM on (b) ------------------------------------------------
+    b = [m for m in mats if m[0] == "b"][0][1]
+    Mb = by["b_f32"]["M"]
+    forms["spmm_b_f32"] = {}
+    for k in (1, 4, 8, 16, 32):
+        X = torch.rand(b.n_cols, k, device=dev)
+        Y = torch.empty(b.n_rows, k, device=dev)
+        t = time_flushed(lambda: Mb.spmm(X, out=Y), 10, flush, stream)
+        nb = roofline.spmm_bytes(b.n_rows, b.n_cols, b.nnz, Mb.s.n_groups, 4, k)
+        forms["spmm_b_f32"][f"k{k}"] = {"gbs": nb / t / 1e3, "gflops": 2 * b.nnz * k / t / 1e3, "us": t}
+        del X, Y
+
+    # -- backward of Y = A X on (b), batch of 8 right-hand sides ---------------
+    G = model_group_size(b.rowptr, 4)
+    op = SparseOperator(b.rowptr, b.col, b.n_cols, dtype=torch.float32, group_size=G)
+    vals = torch.from_numpy(b.val.astype(np.float32)).to(dev).requires_grad_(True)
+    X = torch.rand(b.n_cols, 8, device=dev, requires_grad=True)
+
+    def fwd():
+        with torch.no_grad():
+            return spmm(op, vals, X)
+
+    def fwd_bwd():
+        vals.grad = None
+        X.grad = None
+        Y = spmm(op, vals, X)
+        (Y * Y).sum().backward()
+    t_f = time_flushed(fwd, 10, flush, stream)
+    t_fb = time_flushed(fwd_bwd, 10, flush, stream)
+    forms["backward_b_k8_f32"] = {"group_size": G, "forward_us": t_f, "forward_backward_us": t_fb,
+                                  "backward_over_forward": (t_fb - t_f) / t_f}
+    del op, vals, X
+
+    # -- mixed-precision iterative refinement CG, Poisson 128^3 ---------------
+    a = [m for m in mats if m[0] == "a"][0][1]
+    M64 = by["a_f64"]["M"]
+    rhs = torch.from_numpy(synth.uniform_vector(a.n_rows, seed=0)).to(dev)
+    lo = M64.quantized("bf16")
+    e0, e1 = _ev()
+    e0.record(stream)
+    x_ir, outer, inner, rel = solvers.ir_cg(M64, lo, rhs, outer_tol=1e-10, max_outer=50, inner_tol=1e-4,
+                                             max_inner=500)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ir = e0.elapsed_time(e1)
+    e0, e1 = _ev()
+    e0.record(stream)
+    x64, its64, rel64 = solvers.cg(M64, rhs, rel_tol=1e-10, max_iter=5000)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    forms["ir_cg_poisson128"] = {
+        "ms": t_ir, "corrections": outer, "inner_iterations": inner, "final_rel_residual": rel,
+        "fp64_cg_ms": e0.elapsed_time(e1), "fp64_cg_iterations": its64,
+        "rel_diff_vs_fp64_cg": float((x_ir - x64).norm() / x64.norm())}
+    del lo, x_ir, x64
+
+    # -- gradient through 100 damped-Jacobi steps, 96^3, checkpoint every 10 --
+    J = synth.laplacian_3d(96)
+    opj = SparseOperator(J.rowptr, J.col, J.n_cols, dtype=torch.float32)
+    vj = torch.from_numpy(J.val.astype(np.float32)).to(dev).requires_grad_(True)
+    bj = torch.from_numpy(synth.uniform_vector(J.n_rows, seed=0).astype(np.float32)).to(dev).requires_grad_(True)
+    dinv = torch.full((J.n_rows,), 1.0 / 6.0, device=dev)
+    res = {}
+    for ck in (0, 10):
+        def run():
+            vj.grad = None
+            bj.grad = None
+            xj = solvers.jacobi(opj, vj, bj, dinv, 2.0 / 3.0, 100, checkpoint_every=ck)
+            (xj * xj).sum().backward()
+        run()                                   # warm-up
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        e0, e1 = _ev()
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res["checkpoint_every_10" if ck else "no_checkpoint"] = {
+            "ms": e0.elapsed_time(e1),
+            "peak_extra_mem_mb": (torch.cuda.max_memory_allocated() - base) / 2**20}
+    forms["jacobi_grad_96_f32"] = res
+    del opj
+
+    # -- batched: the 512-member uneven batch in one launch vs 512 launches ---
+    members = synth.workload_batch(512)
+    Bt = BatchedRgCSR.from_csr_list(members, dtype=torch.float32, group_sizes="model")
+    xb = torch.rand(Bt.n_cols_total, device=dev)
+    yb = torch.empty(Bt.n_rows_total, device=dev)
+    g = Bt.capture(xb, yb, repeats=1)
+    nb_batch = sum(roofline.rgcsr_spmv_bytes(m.n_rows, m.n_cols, m.nnz, int(ng), 4)
+                   for m, ng in zip(members, Bt.n_groups))
+    t_b = time_flushed(lambda: g.replay(), 10, flush, stream)
+    plain = [RgCSRMatrix.from_csr(m.rowptr, m.col, m.val, m.n_cols, group_size=Gm, dtype=torch.float32)
+             for m, Gm in zip(members, Bt.group_sizes)]
+    xs = [xb[Bt.member_slices(i)[0]] for i in range(len(members))]
+    ys = [yb[Bt.member_slices(i)[1]] for i in range(len(members))]
+    gp = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for M, xi, yi in zip(plain, xs, ys):
+            M.spmv(xi, out=yi)
+        side.synchronize()
+        with torch.cuda.graph(gp, stream=side):
+            for M, xi, yi in zip(plain, xs, ys):
+                M.spmv(xi, out=yi, stream=side)
+    torch.cuda.current_stream().wait_stream(side)
+    t_p = time_flushed(lambda: gp.replay(), 10, flush, stream)
+    forms["batched_512_f32"] = {
+        "members": len(members), "rows": Bt.n_rows_total, "nnz": Bt.nnz,
+        "gbs": nb_batch / t_b / 1e3, "gflops": 2 * Bt.nnz / t_b / 1e3, "us": t_b,
+        "plain_512_launches_us": t_p, "plain_gbs": nb_batch / t_p / 1e3, "speedup_vs_plain": t_p / t_b}
+    del Bt, plain, members
+    return forms
 
 
 def main():

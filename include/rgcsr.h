@@ -161,12 +161,46 @@ int rgcsr_spmv(const rgcsr_matrix *M, const void *x, void *y, rgcsr_stream_t str
 int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
                   const rgcsr_launch *launch, rgcsr_stream_t stream);
 
+/* Long-row segments, for matrices whose row lengths vary wildly (the
+ * paper's weak point, Sec. 4.4.2: one very long row makes its whole group
+ * wait).  The slots j >= threshold of every longer row are cut into
+ * segments of `segment` slots; one warp sums each segment (deterministic
+ * per-segment partials), a final pass adds a row's partials in order, and
+ * the remaining slots of every row go through the warp-split kernel.  The
+ * RgCSR format itself is unchanged; the segment lists are a launch schedule.
+ *   1. set threshold and segment, call rgcsr_long_rows_plan (sets
+ *      n_segments, n_long_rows; synchronises `stream`);
+ *   2. allocate seg_row, seg_start (n_segments int32), long_row,
+ *      long_first, long_count (n_long_rows int32) and partials (n_segments
+ *      doubles for F64 storage, floats otherwise; scratch of the SpMV);
+ *   3. rgcsr_long_rows_build fills the lists (async);
+ *   4. rgcsr_spmv_long_rows computes y = A x (three launches, async).   */
+typedef struct {
+    int32_t threshold;          /* T >= 0                                     */
+    int32_t segment;            /* S >= 1 slots per segment                   */
+    int64_t n_segments;         /* (plan)                                     */
+    int64_t n_long_rows;        /* (plan) rows longer than T                  */
+    int32_t *seg_row, *seg_start;
+    int32_t *long_row, *long_first, *long_count;
+    void *partials;
+} rgcsr_long_rows;
+size_t rgcsr_long_rows_workspace_bytes(int64_t n_rows);
+int rgcsr_long_rows_plan(const rgcsr_matrix *M, rgcsr_long_rows *S, void *workspace,
+                         size_t workspace_bytes, rgcsr_stream_t stream);
+int rgcsr_long_rows_build(const rgcsr_matrix *M, const rgcsr_long_rows *S, void *workspace,
+                          size_t workspace_bytes, rgcsr_stream_t stream);
+int rgcsr_spmv_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *S, const void *x, void *y,
+                         rgcsr_stream_t stream);
+
 /* The same SpMV from and to HOST memory: copies x_host (n_cols elements) to
- * the caller's device buffer x_dev, runs rgcsr_spmv into y_dev, copies y_dev
- * to y_host (n_rows elements), all on `stream`.  Pinned host buffers make
- * the copies asynchronous; the caller synchronises before reading y_host. */
+ * the caller's device buffer x_dev, computes y_dev = A x_dev -- with the
+ * long-row schedule if long_rows is not NULL, else rgcsr_spmv_ex with
+ * `launch` (NULL = default) -- and copies y_dev to y_host (n_rows
+ * elements), all on `stream`.  Pinned host buffers make the copies
+ * asynchronous; the caller synchronises before reading y_host. */
 int rgcsr_spmv_host(const rgcsr_matrix *M, const void *x_host, void *y_host,
-                    void *x_dev, void *y_dev, rgcsr_stream_t stream);
+                    void *x_dev, void *y_dev, const rgcsr_launch *launch,
+                    const rgcsr_long_rows *long_rows, rgcsr_stream_t stream);
 
 /* Y = A X for k right-hand sides (the SpMV of Sec. 3.4 applied to several
  * vectors at once; not in the paper).  X: row-major [n_cols x k] with row

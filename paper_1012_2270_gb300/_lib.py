@@ -52,6 +52,12 @@ class Hyb(ctypes.Structure):
                 ("ell_val", P), ("ell_col", P), ("coo_row", P), ("coo_col", P), ("coo_val", P)]
 
 
+class LongRows(ctypes.Structure):
+    _fields_ = [("threshold", I32), ("segment", I32), ("n_segments", I64), ("n_long_rows", I64),
+                ("seg_row", P), ("seg_start", P), ("long_row", P), ("long_first", P), ("long_count", P),
+                ("partials", P)]
+
+
 class BatchDesc(ctypes.Structure):
     _fields_ = [("n_rows", I64), ("n_cols", I64), ("val_off", I64), ("row_off", I64),
                 ("group_off", I64), ("x_off", I64), ("group_size", I32), ("reserved", I32)]
@@ -76,8 +82,12 @@ SIGNATURES = {
     "rgcsr_plan_noalloc": (ctypes.c_int, [_PCSR, _PM, P]),
     "rgcsr_spmv": (ctypes.c_int, [_PM, P, P, P]),
     "rgcsr_spmv_ex": (ctypes.c_int, [_PM, P, P, _PL, P]),
-    "rgcsr_spmv_host": (ctypes.c_int, [_PM, P, P, P, P, P]),
+    "rgcsr_spmv_host": (ctypes.c_int, [_PM, P, P, P, P, _PL, ctypes.POINTER(LongRows), P]),
     "rgcsr_quantize": (ctypes.c_int, [_PM, _PM, P]),
+    "rgcsr_long_rows_workspace_bytes": (SZ, [I64]),
+    "rgcsr_long_rows_plan": (ctypes.c_int, [_PM, ctypes.POINTER(LongRows), P, SZ, P]),
+    "rgcsr_long_rows_build": (ctypes.c_int, [_PM, ctypes.POINTER(LongRows), P, SZ, P]),
+    "rgcsr_spmv_long_rows": (ctypes.c_int, [_PM, ctypes.POINTER(LongRows), P, P, P]),
     "rgcsr_spmm": (ctypes.c_int, [_PM, I32, P, I64, P, I64, P]),
     "rgcsr_transpose_workspace_bytes": (SZ, [I64, I64, I64]),
     "rgcsr_csr_transpose": (ctypes.c_int, [_PCSR, P, P, P, P, P, SZ, P]),

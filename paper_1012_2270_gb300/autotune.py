@@ -96,13 +96,30 @@ def _time(fn, reps: int, flush: torch.Tensor) -> float:
 
 
 def candidates(rowptr, dtype: torch.dtype):
-    Gm = model_group_size(rowptr, dtype.itemsize)
+    """Configurations worth timing: for dense groups the G = 32 kernels; for
+    uneven rows small group sizes, with and without the long-row segment
+    schedule (threshold T, 256 slots per segment)."""
+    lengths = np.diff(np.asarray(rowptr, dtype=np.int64))
+    nnz = int(lengths.sum())
+    irregular = stored_slots(lengths, 32) * 4 > nnz * 5
     cands = [dict(group_size=32, kernel=L.KERNEL_AUTO)]
-    cands += [dict(group_size=32, kernel=L.KERNEL_TMA, variant=v) for v in range(4)]
-    for G in sorted({32, Gm, 16, 64}):
-        cands.append(dict(group_size=G, kernel=L.KERNEL_SPLIT))
-        cands.append(dict(group_size=G, kernel=L.KERNEL_LEAN))
+    if not irregular:
+        cands += [dict(group_size=32, kernel=L.KERNEL_TMA, variant=v) for v in range(4)]
+        cands += [dict(group_size=G, kernel=k) for G in (32, 64) for k in (L.KERNEL_LEAN, L.KERNEL_SPLIT)]
+    else:
+        Gm = model_group_size(rowptr, dtype.itemsize)
+        cands += [dict(group_size=G, kernel=L.KERNEL_SPLIT) for G in sorted({1, 2, 4, 8, Gm})]
+        cands += [dict(group_size=G, long_rows=[T, 256]) for G in (1, 2, 4) for T in (16, 32, 64)]
     return cands
+
+
+def build(rowptr, col, val, n_cols: int, config: dict, dtype: torch.dtype):
+    """The RgCSR matrix and spmv keyword arguments of a configuration."""
+    from .rgcsr import RgCSRMatrix
+    M = RgCSRMatrix.from_csr(rowptr, col, val, n_cols, group_size=config["group_size"], dtype=dtype)
+    if "long_rows" in config:
+        M.split_long_rows(*config["long_rows"])
+    return M, {k: v for k, v in config.items() if k in ("kernel", "variant")}
 
 
 def tune(rowptr, col, val, n_cols: int, dtype: torch.dtype = torch.float32, reps: int = 10,
@@ -123,13 +140,17 @@ def tune(rowptr, col, val, n_cols: int, dtype: torch.dtype = torch.float32, reps
         if G not in built:
             built[G] = RgCSRMatrix.from_csr(rowptr, col, val, n_cols, group_size=G, dtype=dtype)
         M = built[G]
-        kw = {k: v for k, v in c.items() if k != "group_size"}
+        M._long = None
+        if "long_rows" in c:
+            M.split_long_rows(*c["long_rows"])
+        kw = {k: v for k, v in c.items() if k in ("kernel", "variant")}
         try:
             y = M.spmv(x, **kw)
         except L.RgCSRError:
             continue                      # configuration not valid for this matrix
         us = _time(lambda: M.spmv(x, out=y, **kw), reps, flush)
         results.append(dict(c, us=us))
+        M._long = None
     best = min(results, key=lambda r: r["us"])
     if use_cache:
         cache = _load_cache()

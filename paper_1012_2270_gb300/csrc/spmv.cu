@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kDefaultThreads)
 rgcsr_spmv_split(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *__restrict__ col,
                  const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
                  const float *__restrict__ scale, const typename VT<V>::A *__restrict__ x,
-                 typename VT<V>::A *__restrict__ y, int w4) {
+                 typename VT<V>::A *__restrict__ y, int w4, int cap) {
     using A = typename VT<V>::A;
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -126,7 +126,7 @@ rgcsr_spmv_split(int64_t n, int32_t G, const V *__restrict__ val, const int32_t 
         const int64_t first = g * G;
         stride = (int)min((int64_t)G, n - first);
         ptr = __ldg(gp + g) + (row - first);
-        len = __ldg(rl + row);
+        len = min(__ldg(rl + row), cap);      // slots >= cap are left to the long-row segments
     }
     const int lmax = warp_max_i(len);
     const int lmin = warp_min_i(valid ? len : INT_MAX);
@@ -265,10 +265,128 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
     if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
     if (nc)
         rgcsr_spmv_split<V, true><<<(unsigned)blocks, threads, 0, s>>>(
-            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, w4);
+            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, w4, INT_MAX);
     else
         rgcsr_spmv_split<V, false><<<(unsigned)blocks, threads, 0, s>>>(
-            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, w4);
+            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, w4, INT_MAX);
+    return launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// Long-row segments.  The slots j >= T of every row longer than T are cut
+// into segments of S slots; each segment is one warp's work (its slots are
+// read with the row's group stride), giving one partial sum per segment, and
+// a last pass adds a row's partials in segment order.  The rest of every row
+// (slots < T) goes through the split kernel with its length capped at T.
+// Work per warp is bounded by S slots whatever the row lengths are, so no
+// warp is held up by a very long row; the result is deterministic.
+// ---------------------------------------------------------------------------
+__global__ void seg_count_kernel(int64_t n, const int32_t *__restrict__ rl, int32_t T, int32_t S,
+                                 int64_t *__restrict__ nseg, int64_t *__restrict__ nlong) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int L = rl[i];
+    const int64_t c = L > T ? ((int64_t)L - T + S - 1) / S : 0;
+    nseg[i] = c;
+    nlong[i] = c > 0 ? 1 : 0;
+}
+
+__global__ void seg_fill_kernel(int64_t n, const int32_t *__restrict__ rl, int32_t T, int32_t S,
+                                const int64_t *__restrict__ seg_off, const int64_t *__restrict__ long_off,
+                                int32_t *__restrict__ seg_row, int32_t *__restrict__ seg_start,
+                                int32_t *__restrict__ long_row, int32_t *__restrict__ long_first,
+                                int32_t *__restrict__ long_count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int L = rl[i];
+    if (L <= T) return;
+    const int c = (L - T + S - 1) / S;
+    const int64_t base = seg_off[i];
+    for (int s = 0; s < c; ++s) {
+        seg_row[base + s] = (int32_t)i;
+        seg_start[base + s] = T + s * S;
+    }
+    const int64_t k = long_off[i];
+    long_row[k] = (int32_t)i;
+    long_first[k] = (int32_t)base;
+    long_count[k] = c;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kDefaultThreads)
+seg_spmv_kernel(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *__restrict__ col,
+                const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
+                const int32_t *__restrict__ seg_row, const int32_t *__restrict__ seg_start, int32_t S,
+                int64_t n_seg, const typename VT<V>::A *__restrict__ x, typename VT<V>::A *__restrict__ partials) {
+    using A = typename VT<V>::A;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n_seg; s += warps) {
+        const int64_t row = seg_row[s];
+        const int ja = seg_start[s];
+        const int jb = min(ja + S, __ldg(rl + row));
+        const int64_t g = row / G;
+        const int64_t first = g * G;
+        const int R = (int)min((int64_t)G, n - first);
+        const int64_t ptr = __ldg(gp + g) + (row - first);
+        A part = 0;
+        for (int j = ja + lane; j < jb; j += 32 * kUnroll) {
+            A v[kUnroll];
+            int c[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int jj = j + 32 * u;
+                if (jj < jb) {
+                    const int64_t p = ptr + (int64_t)jj * R;
+                    v[u] = VT<V>::ld(val + p);
+                    c[u] = ld_stream(col + p);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                if (j + 32 * u < jb) part = fma(v[u], __ldg(x + c[u]), part);
+        }
+        part = warp_sum(part);
+        if (lane == 0) partials[s] = part;
+    }
+}
+
+template <typename V>
+__global__ void seg_combine_kernel(int64_t n_long, const int32_t *__restrict__ long_row,
+                                   const int32_t *__restrict__ long_first, const int32_t *__restrict__ long_count,
+                                   const typename VT<V>::A *__restrict__ partials, const float *__restrict__ scale,
+                                   typename VT<V>::A *__restrict__ y) {
+    using A = typename VT<V>::A;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_long) return;
+    const int64_t row = long_row[k];
+    const int64_t f = long_first[k];
+    A s = 0;
+    for (int q = 0; q < long_count[k]; ++q) s += partials[f + q];
+    y[row] += finish<V>(s, scale, row);
+}
+
+template <typename V>
+int launch_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *S, const typename VT<V>::A *x,
+                     typename VT<V>::A *y, cudaStream_t s) {
+    using A = typename VT<V>::A;
+    const V *val = static_cast<const V *>(M->values);
+    const int64_t n = M->n_rows;
+    const float *scale = M->row_scale;
+    if (VT<V>::scaled && !scale) return RGCSR_ERR_INVALID_ARG;
+    const int64_t blocks = ceil_div(n, kDefaultThreads);
+    if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
+    rgcsr_spmv_split<V, true><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
+        n, M->group_size, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, 8, S->threshold);
+    if (S->n_segments == 0) return launch_status();
+    int64_t sb = ceil_div(S->n_segments, kDefaultThreads / 32);
+    if (sb > 152 * 16) sb = 152 * 16;
+    A *part = static_cast<A *>(S->partials);
+    seg_spmv_kernel<V><<<(unsigned)sb, kDefaultThreads, 0, s>>>(
+        n, M->group_size, val, M->columns, M->group_ptr, M->row_lengths, S->seg_row, S->seg_start,
+        S->segment, S->n_segments, x, part);
+    seg_combine_kernel<V><<<(unsigned)ceil_div(S->n_long_rows, 256), 256, 0, s>>>(
+        S->n_long_rows, S->long_row, S->long_first, S->long_count, part, scale, y);
     return launch_status();
 }
 
@@ -299,7 +417,9 @@ RGCSR_API int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
         // kernel for FP32 and for short FP64 rows, the full-occupancy
         // thread-per-row kernel otherwise; uneven or long rows take the
         // warp-split kernel.
-        const bool dense = M->n_stored * 4 <= M->nnz * 5;
+        // "dense": little padding and no row far longer than the average
+        const bool dense = M->n_stored * 4 <= M->nnz * 5 &&
+                           !(M->max_row_len > 64 && M->max_row_len * M->n_rows > 8 * M->nnz);
         const bool short_rows = M->nnz <= 8 * M->n_rows;
         if (dense && tma_eligible(M) && (M->value_type == RGCSR_F32 || short_rows))
             kernel = RGCSR_KERNEL_TMA;
@@ -332,8 +452,103 @@ RGCSR_API int rgcsr_spmv(const rgcsr_matrix *M, const void *x, void *y, rgcsr_st
     return rgcsr_spmv_ex(M, x, y, nullptr, stream);
 }
 
+namespace {
+struct SegScratch {
+    int64_t *seg_off, *long_off, *partials;
+};
+SegScratch carve_seg(void *ws, int64_t n) {
+    char *p = static_cast<char *>(ws);
+    const size_t a = align_up((size_t)(n + 1) * 8, 256);
+    SegScratch c;
+    c.seg_off = reinterpret_cast<int64_t *>(p);
+    c.long_off = reinterpret_cast<int64_t *>(p + a);
+    c.partials = reinterpret_cast<int64_t *>(p + 2 * a);
+    return c;
+}
+// counts per row, then exclusive scans: seg_off[n] / long_off[n] = totals
+int seg_scan(const rgcsr_matrix *M, const rgcsr_long_rows *S, SegScratch &c, cudaStream_t s) {
+    const int64_t n = M->n_rows;
+    if (n > 0) {
+        seg_count_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, M->row_lengths, S->threshold, S->segment,
+                                                                    c.seg_off, c.long_off);
+        int st = launch_status();
+        if (st != RGCSR_OK) return st;
+    }
+    int st = exclusive_scan_i64(c.seg_off, n, c.partials, s);
+    if (st != RGCSR_OK) return st;
+    return exclusive_scan_i64(c.long_off, n, c.partials, s);
+}
+}  // namespace
+
+RGCSR_API size_t rgcsr_long_rows_workspace_bytes(int64_t n_rows) {
+    if (n_rows < 0) return 0;
+    return 2 * align_up((size_t)(n_rows + 1) * 8, 256) + scan_partials_bytes(n_rows);
+}
+
+RGCSR_API int rgcsr_long_rows_plan(const rgcsr_matrix *M, rgcsr_long_rows *S, void *workspace,
+                                   size_t workspace_bytes, rgcsr_stream_t stream) {
+    int st = check_matrix(M);
+    if (st != RGCSR_OK) return st;
+    if (!S || S->threshold < 0 || S->segment < 1) return RGCSR_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < rgcsr_long_rows_workspace_bytes(M->n_rows)) return RGCSR_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    SegScratch c = carve_seg(workspace, M->n_rows);
+    if ((st = seg_scan(M, S, c, s)) != RGCSR_OK) return st;
+    int64_t tot[2] = {0, 0};
+    RGCSR_CUDA_TRY(cudaMemcpyAsync(&tot[0], c.seg_off + M->n_rows, 8, cudaMemcpyDeviceToHost, s));
+    RGCSR_CUDA_TRY(cudaMemcpyAsync(&tot[1], c.long_off + M->n_rows, 8, cudaMemcpyDeviceToHost, s));
+    RGCSR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (tot[0] > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
+    S->n_segments = tot[0];
+    S->n_long_rows = tot[1];
+    return RGCSR_OK;
+}
+
+RGCSR_API int rgcsr_long_rows_build(const rgcsr_matrix *M, const rgcsr_long_rows *S, void *workspace,
+                                    size_t workspace_bytes, rgcsr_stream_t stream) {
+    int st = check_matrix(M);
+    if (st != RGCSR_OK) return st;
+    if (!S || S->threshold < 0 || S->segment < 1) return RGCSR_ERR_INVALID_ARG;
+    if (S->n_segments == 0 || M->n_rows == 0) return RGCSR_OK;
+    if (!S->seg_row || !S->seg_start || !S->long_row || !S->long_first || !S->long_count)
+        return RGCSR_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < rgcsr_long_rows_workspace_bytes(M->n_rows)) return RGCSR_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    SegScratch c = carve_seg(workspace, M->n_rows);
+    if ((st = seg_scan(M, S, c, s)) != RGCSR_OK) return st;
+    seg_fill_kernel<<<(unsigned)ceil_div(M->n_rows, 256), 256, 0, s>>>(
+        M->n_rows, M->row_lengths, S->threshold, S->segment, c.seg_off, c.long_off, S->seg_row, S->seg_start,
+        S->long_row, S->long_first, S->long_count);
+    return launch_status();
+}
+
+RGCSR_API int rgcsr_spmv_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *S, const void *x, void *y,
+                                   rgcsr_stream_t stream) {
+    int st = check_matrix(M);
+    if (st != RGCSR_OK) return st;
+    if (M->n_rows == 0) return RGCSR_OK;
+    if (!S || S->threshold < 0 || S->segment < 1 || !y || (M->n_cols > 0 && !x)) return RGCSR_ERR_INVALID_ARG;
+    if (S->n_segments > 0 && (!S->seg_row || !S->seg_start || !S->long_row || !S->long_first ||
+                              !S->long_count || !S->partials))
+        return RGCSR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (M->value_type) {
+        case RGCSR_F64:
+            return launch_long_rows<double>(M, S, static_cast<const double *>(x), static_cast<double *>(y), s);
+        case RGCSR_F32:
+            return launch_long_rows<float>(M, S, static_cast<const float *>(x), static_cast<float *>(y), s);
+        case RGCSR_BF16:
+            return launch_long_rows<__nv_bfloat16>(M, S, static_cast<const float *>(x), static_cast<float *>(y), s);
+        case RGCSR_F16:
+            return launch_long_rows<__half>(M, S, static_cast<const float *>(x), static_cast<float *>(y), s);
+        default:
+            return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    }
+}
+
 RGCSR_API int rgcsr_spmv_host(const rgcsr_matrix *M, const void *x_host, void *y_host,
-                              void *x_dev, void *y_dev, rgcsr_stream_t stream) {
+                              void *x_dev, void *y_dev, const rgcsr_launch *launch,
+                              const rgcsr_long_rows *long_rows, rgcsr_stream_t stream) {
     int st = check_matrix(M);
     if (st != RGCSR_OK) return st;
     if (M->n_rows == 0) return RGCSR_OK;
@@ -341,7 +556,8 @@ RGCSR_API int rgcsr_spmv_host(const rgcsr_matrix *M, const void *x_host, void *y
     const size_t xb = M->value_type == RGCSR_F64 ? 8 : 4;
     cudaStream_t s = (cudaStream_t)stream;
     RGCSR_CUDA_TRY(cudaMemcpyAsync(x_dev, x_host, (size_t)M->n_cols * xb, cudaMemcpyHostToDevice, s));
-    st = rgcsr_spmv(M, x_dev, y_dev, stream);
+    st = long_rows ? rgcsr_spmv_long_rows(M, long_rows, x_dev, y_dev, stream)
+                   : rgcsr_spmv_ex(M, x_dev, y_dev, launch, stream);
     if (st != RGCSR_OK) return st;
     RGCSR_CUDA_TRY(cudaMemcpyAsync(y_host, y_dev, (size_t)M->n_rows * xb, cudaMemcpyDeviceToHost, s));
     return RGCSR_OK;

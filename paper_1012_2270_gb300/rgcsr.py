@@ -65,6 +65,7 @@ class RgCSRMatrix:
         self.values = self.columns = self.group_ptr = self.row_lengths = None
         self.row_scale = None
         self.slot_to_csr = None
+        self._long = None          # long-row segment schedule, if enabled
 
     # -- construction ------------------------------------------------------
     @classmethod
@@ -105,6 +106,31 @@ class RgCSRMatrix:
             M.slot_to_csr = _ptr(self.slot_to_csr)
         L.call("rgcsr_convert", ctypes.byref(A), ctypes.byref(M), st)
         return self
+
+    def split_long_rows(self, threshold: int = 64, segment: int = 256, stream=None) -> "RgCSRMatrix":
+        """Makes spmv() cut the slots >= threshold of longer rows into
+        segments of `segment` slots, one warp each (rgcsr_spmv_long_rows)."""
+        S = L.LongRows()
+        S.threshold, S.segment = int(threshold), int(segment)
+        dev = self.group_ptr.device
+        nb = L.lib().rgcsr_long_rows_workspace_bytes(self.s.n_rows)
+        ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        st = _stream_ptr(stream)
+        L.call("rgcsr_long_rows_plan", ctypes.byref(self.s), ctypes.byref(S), _ptr(ws), nb, st)
+        i32 = dict(dtype=torch.int32, device=dev)
+        bufs = dict(seg_row=torch.empty(S.n_segments, **i32), seg_start=torch.empty(S.n_segments, **i32),
+                    long_row=torch.empty(S.n_long_rows, **i32), long_first=torch.empty(S.n_long_rows, **i32),
+                    long_count=torch.empty(S.n_long_rows, **i32),
+                    partials=torch.empty(S.n_segments, dtype=self.x_dtype, device=dev))
+        for k, t in bufs.items():
+            setattr(S, k, _ptr(t))
+        L.call("rgcsr_long_rows_build", ctypes.byref(self.s), ctypes.byref(S), _ptr(ws), nb, st)
+        self._long = (S, bufs)
+        return self
+
+    @property
+    def n_long_segments(self) -> int:
+        return 0 if self._long is None else self._long[0].n_segments
 
     def quantized(self, fmt: str = "bf16", stream=None) -> "RgCSRMatrix":
         """The same matrix with values stored as bfloat16 ("bf16") or half
@@ -165,8 +191,12 @@ class RgCSRMatrix:
         if x.dtype != self.x_dtype or x.numel() != self.s.n_cols or not x.is_contiguous():
             raise ValueError(f"x must be a contiguous {self.x_dtype} vector of length {self.s.n_cols}")
         y = out if out is not None else torch.empty(self.s.n_rows, dtype=self.x_dtype, device=x.device)
-        if (kernel == L.KERNEL_AUTO and x_load == L.XLOAD_NC and not block_threads
-                and not split_weight and not variant):
+        default = (kernel == L.KERNEL_AUTO and x_load == L.XLOAD_NC and not block_threads
+                   and not split_weight and not variant)
+        if default and self._long is not None:
+            L.call("rgcsr_spmv_long_rows", ctypes.byref(self.s), ctypes.byref(self._long[0]), _ptr(x), _ptr(y),
+                   _stream_ptr(stream))
+        elif default:
             L.call("rgcsr_spmv", ctypes.byref(self.s), _ptr(x), _ptr(y), _stream_ptr(stream))
         else:
             ln = L.Launch(kernel, block_threads, x_load, split_weight, variant)
@@ -187,10 +217,15 @@ class RgCSRMatrix:
         return Y
 
     def spmv_host(self, x_host: torch.Tensor, y_host: torch.Tensor, x_dev: torch.Tensor,
-                  y_dev: torch.Tensor, stream=None) -> None:
-        """Host-to-host SpMV through caller-provided device staging buffers."""
+                  y_dev: torch.Tensor, kernel: int = L.KERNEL_AUTO, variant: int = 0, stream=None) -> None:
+        """Host-to-host SpMV through caller-provided device staging buffers
+        (the long-row schedule if enabled, else the given kernel)."""
+        if self._long is not None and kernel == L.KERNEL_AUTO and not variant:
+            launch, lr = None, ctypes.byref(self._long[0])
+        else:
+            launch, lr = ctypes.byref(L.Launch(kernel, 0, L.XLOAD_NC, 0, variant)), None
         L.call("rgcsr_spmv_host", ctypes.byref(self.s), _ptr(x_host), _ptr(y_host),
-               _ptr(x_dev), _ptr(y_dev), _stream_ptr(stream))
+               _ptr(x_dev), _ptr(y_dev), launch, lr, _stream_ptr(stream))
 
     def __matmul__(self, x):
         return self.spmv(x)

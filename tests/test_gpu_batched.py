@@ -74,10 +74,8 @@ def test_autotune_returns_a_correct_configuration(tmp_path, monkeypatch):
     A = synth.power_law(50000, seed=3)
     best = autotune.tune(A.rowptr, A.col, A.val.astype(np.float32), A.n_cols, dtype=torch.float32, reps=3)
     assert best["us"] > 0
-    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(np.float32), A.n_cols,
-                             group_size=best["group_size"], dtype=torch.float32)
+    M, kw = autotune.build(A.rowptr, A.col, A.val.astype(np.float32), A.n_cols, best, torch.float32)
     x = synth.uniform_vector(A.n_cols, seed=0).astype(np.float32)
-    kw = {k: v for k, v in best.items() if k in ("kernel", "variant")}
     y = M.spmv(torch.from_numpy(x).cuda(), **kw).cpu().numpy()
     y_ref, absy = oracle.csr_spmv(A.rowptr, A.col, rounded_values(A.val, "f32"), x.astype(np.float64))
     assert_within_bound(y, y_ref, absy, TAU["f32"], "autotuned")

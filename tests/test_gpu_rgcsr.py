@@ -260,3 +260,42 @@ def test_tma_sizes_and_partial_group(dtype, n):
     check_spmv(M, A, dtype, x, kernel=L.KERNEL_TMA)
     check_spmv(M, A, dtype, x)
     assert device_status() == 0
+
+
+# ---------------------------------------------------------------------------
+# long-row segment schedule
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("G,T,S", [(32, 64, 256), (1, 16, 32), (8, 0, 64), (33, 5, 7), (32, 100000, 256)])
+def test_long_row_segments(dtype, G, T, S):
+    rng = np.random.default_rng(G + T + S)
+    n, m = 3000, 20000
+    L_ = rng.integers(0, 10, n)
+    L_[[1, 2, 100, 2999]] = [12000, 700, 65, 3000]
+    A = synth.random_csr(n, m, L_, seed=5)
+    M = to_gpu_matrix(A, dtype, G, slot_map=False).split_long_rows(threshold=T, segment=S)
+    expected = int(sum((l - T + S - 1) // S for l in L_ if l > T))
+    assert M.n_long_segments == expected
+    check_spmv(M, A, dtype, synth.uniform_vector(m, seed=8))
+
+
+def test_long_row_segments_quantized():
+    A = synth.power_law(20000, seed=4)
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val, A.n_cols, group_size=8, dtype=torch.float64)
+    Q = M.quantized("bf16").split_long_rows(threshold=32, segment=128)
+    x = synth.uniform_vector(A.n_cols, seed=1).astype(np.float32)
+    y = Q.spmv(torch.from_numpy(x).cuda()).cpu().numpy()
+    y_plain = Q.spmv(torch.from_numpy(x).cuda(), kernel=L.KERNEL_SPLIT).cpu().numpy()
+    q, sc = oracle.quantize_rows(A.rowptr, A.val, oracle.BF16)
+    deq = oracle.dequantized_values(A.rowptr, q, sc, oracle.BF16)
+    y_ref, absy = oracle.csr_spmv(A.rowptr, A.col, deq, x.astype(np.float64))
+    assert_within_bound(y, y_ref, absy, 2e-6, "segments bf16")
+    assert_within_bound(y_plain, y_ref, absy, 2e-6, "split bf16")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("G", [1, 8, 32])
+def test_long_row_segments_full_size_b(dtype, G):
+    A = synth.workload_b()
+    M = to_gpu_matrix(A, dtype, G, slot_map=False).split_long_rows(threshold=64, segment=256)
+    check_spmv(M, A, dtype, synth.uniform_vector(A.n_cols, seed=0))
