@@ -43,6 +43,7 @@ typedef struct CUstream_st *rgcsr_stream_t;   /* identical to cudaStream_t */
 #define RGCSR_ERR_UNSUPPORTED_DTYPE -5   /* value type not valid for this call */
 #define RGCSR_ERR_CUDA              -6   /* a CUDA runtime call failed         */
 #define RGCSR_ERR_WORKSPACE         -7   /* workspace missing or too small     */
+#define RGCSR_ERR_BAD_PERM          -8   /* row_perm not a permutation of [0, n_rows) */
 
 /* element types */
 #define RGCSR_F64  0
@@ -84,6 +85,14 @@ typedef struct {
     int32_t *row_lengths;       /* n_rows       ("rowLengths")               */
     float *row_scale;           /* n_rows; BF16/F16 storage only, else NULL  */
     int64_t *slot_to_csr;       /* optional n_stored: CSR position per slot, -1 = padding */
+    int32_t *row_perm;          /* optional n_rows row order (Sec. 4.4.2, Table 7): stored row k
+                                   is CSR row row_perm[k], so groups are formed over the
+                                   reordered rows; NULL = identity.  Set before rgcsr_plan,
+                                   which checks that it is a permutation.  x, y, X and Y
+                                   stay in the CSR's own row order: kernels write row k's
+                                   result to y[row_perm[k]].  row_lengths, row_scale and
+                                   the slabs are in stored order; slot_to_csr holds
+                                   positions in the CSR as given.                    */
 } rgcsr_matrix;
 
 /* Kernel selection for rgcsr_spmv_ex (autotuning and ablations). */
@@ -124,11 +133,28 @@ typedef struct {
 /*   2. rgcsr_convert -- scatters values/columns (and slot_to_csr if non-   */
 /*                      NULL) into caller-allocated n_stored arrays.        */
 /*                      M->value_type must equal A->value_type.  Async.     */
+/* With M->row_perm set, both phases work on the rows in that order (plan   */
+/* returns RGCSR_ERR_BAD_PERM if it is not a permutation of [0, n_rows)).   */
 /* ----------------------------------------------------------------------- */
 size_t rgcsr_plan_workspace_bytes(int64_t n_rows, int32_t group_size);
 int rgcsr_plan(const rgcsr_csr *A, rgcsr_matrix *M, void *workspace,
                size_t workspace_bytes, rgcsr_stream_t stream);
 int rgcsr_convert(const rgcsr_csr *A, const rgcsr_matrix *M, rgcsr_stream_t stream);
+
+/* Row ordering (Sec. 4.4.2, Table 7).  The paper's "descending" order sorts
+ * rows by their number of non-zeros, largest first, so that each group holds
+ * rows of similar length and little padding is needed.
+ * rgcsr_descending_order writes row_perm[k] = the CSR row placed at stored
+ * position k: row lengths non-increasing in k, rows of equal length in
+ * increasing row index (a stable sort, so the order is unique).  row_perm is
+ * a caller-allocated device int32[n_rows]; the workspace (device, caller-
+ * owned) needs rgcsr_row_order_workspace_bytes(n_rows) bytes.  Asynchronous
+ * on `stream`.  Lengths are read from A->row_ptr as given; an invalid row_ptr
+ * still yields a permutation, which rgcsr_plan then rejects with the CSR.
+ * Put the result in M->row_perm before rgcsr_plan. */
+size_t rgcsr_row_order_workspace_bytes(int64_t n_rows);
+int rgcsr_descending_order(const rgcsr_csr *A, int32_t *row_perm, void *workspace,
+                           size_t workspace_bytes, rgcsr_stream_t stream);
 
 /* rgcsr_plan without a workspace argument, for callers that cannot
  * allocate device memory: code that only receives device pointers from
@@ -260,7 +286,8 @@ int rgcsr_spmv_batched(const rgcsr_batch *B, const void *x, void *y, rgcsr_strea
 /* src: an F64 or F32 matrix.  dst: dst->value_type (BF16/F16), dst->values */
 /* (n_stored 2-byte elements) and dst->row_scale (n_rows floats) allocated  */
 /* by the caller; dst->columns, group_ptr and row_lengths normally point to */
-/* src's arrays.  The size fields of dst are copied from src.  Async.      */
+/* src's arrays.  The size fields and row_perm of dst are copied from src */
+/* (row_scale is in stored row order).  Async.                              */
 /* ----------------------------------------------------------------------- */
 int rgcsr_quantize(const rgcsr_matrix *src, rgcsr_matrix *dst, rgcsr_stream_t stream);
 

@@ -14,7 +14,8 @@ format for storing the sparse matrices on GPU with implementation in CUDA"):
 * Sec. 3.4  -- RgCSR layout, its SpMV kernel semantics, sliced ELLPACK
   (``rgcsr_layout``, ``rgcsr_spmv``, ``sliced_ell_spmv``).
 * Sec. 4.3  -- artificial-zero percentage (``artificial_zero_percent``).
-* Sec. 4.4.2, Table 7 -- descending row-length ordering (``descending_order``).
+* Sec. 4.4.2, Table 7 -- descending row-length ordering (``descending_order``)
+  and layouts over reordered rows (``permute_rows``, ``rgcsr_layout(row_order=)``).
 * Not in the paper (forms added on top of the method): per-row-scaled
   bf16/fp16 value storage, transposition and gradients, damped Jacobi,
   conjugate gradients.
@@ -146,6 +147,7 @@ class RgCSRLayout:
     values: np.ndarray        # [n_stored], dtype of the input values
     columns: np.ndarray       # int32 [n_stored]
     slot_to_csr: np.ndarray   # int64 [n_stored], -1 for padding
+    row_perm: np.ndarray | None = None   # stored row k holds CSR row row_perm[k]
 
     @property
     def n_stored(self) -> int:
@@ -163,9 +165,38 @@ def rgcsr_sizes(rowptr, group_size: int):
     return rl, gp
 
 
-def rgcsr_layout(rowptr, col, val, group_size: int) -> RgCSRLayout:
+def permute_rows(rowptr, col, val, perm):
+    """The CSR of P A: row k of the result is row perm[k] of A, its entries
+    in their CSR order.  Also returns, per entry of the result, its position
+    in A's arrays."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    perm = np.ascontiguousarray(perm, dtype=np.int64)
+    n = rowptr.size - 1
+    if perm.size != n or not np.array_equal(np.sort(perm), np.arange(n)):
+        raise ValueError("perm is not a permutation of the rows")
+    new_ptr = np.zeros(n + 1, np.int64)
+    source = []
+    for k in range(n):
+        i = perm[k]
+        source.append(np.arange(rowptr[i], rowptr[i + 1], dtype=np.int64))
+        new_ptr[k + 1] = new_ptr[k] + (rowptr[i + 1] - rowptr[i])
+    source = np.concatenate(source) if n else np.zeros(0, np.int64)
+    return new_ptr, np.asarray(col)[source], np.asarray(val)[source], source
+
+
+def rgcsr_layout(rowptr, col, val, group_size: int, row_order=None) -> RgCSRLayout:
     """CSR -> RgCSR (Sec. 3.4).  ``val`` keeps its dtype; values are copied
-    bit for bit, padding is all-zero bits with column 0."""
+    bit for bit, padding is all-zero bits with column 0.
+
+    ``row_order`` (a permutation; Sec. 4.4.2, Table 7): the groups are
+    formed over the rows in that order, i.e. the layout is that of P A
+    (``permute_rows``), and slot_to_csr still points into A's arrays."""
+    if row_order is not None:
+        prp, pcol, pval, source = permute_rows(rowptr, col, val, row_order)
+        lay = rgcsr_layout(prp, pcol, pval, group_size)
+        s2c = np.where(lay.slot_to_csr >= 0, source[np.maximum(lay.slot_to_csr, 0)], -1)
+        return RgCSRLayout(lay.n, lay.group_size, lay.row_lengths, lay.group_ptr, lay.values,
+                           lay.columns, s2c, np.ascontiguousarray(row_order, dtype=np.int64))
     rowptr, col = _csr(rowptr, col)
     val = np.ascontiguousarray(val)
     n = rowptr.size - 1
@@ -193,6 +224,10 @@ def rgcsr_spmv(layout: RgCSRLayout, x):
     _load().orc_rgcsr_spmv(layout.n, layout.group_size, _p(layout.group_ptr),
                            _p(layout.row_lengths), _p(vals),
                            _p(layout.columns), _p(x), _p(y))
+    if layout.row_perm is not None:      # stored row k is CSR row row_perm[k]
+        out = np.empty_like(y)
+        out[layout.row_perm] = y
+        return out
     return y
 
 

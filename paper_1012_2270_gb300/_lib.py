@@ -19,6 +19,7 @@ RGCSR_ERR_INDEX_OVERFLOW = -4
 RGCSR_ERR_UNSUPPORTED_DTYPE = -5
 RGCSR_ERR_CUDA = -6
 RGCSR_ERR_WORKSPACE = -7
+RGCSR_ERR_BAD_PERM = -8
 
 F64, F32, BF16, F16, I32T, I64T = 0, 1, 2, 3, 4, 5
 
@@ -38,7 +39,7 @@ class Matrix(ctypes.Structure):
                 ("group_size", I32), ("value_type", I32),
                 ("n_groups", I64), ("n_stored", I64), ("max_row_len", I64),
                 ("values", P), ("columns", P), ("group_ptr", P), ("row_lengths", P),
-                ("row_scale", P), ("slot_to_csr", P)]
+                ("row_scale", P), ("slot_to_csr", P), ("row_perm", P)]
 
 
 class Launch(ctypes.Structure):
@@ -80,6 +81,8 @@ SIGNATURES = {
     "rgcsr_plan": (ctypes.c_int, [_PCSR, _PM, P, SZ, P]),
     "rgcsr_convert": (ctypes.c_int, [_PCSR, _PM, P]),
     "rgcsr_plan_noalloc": (ctypes.c_int, [_PCSR, _PM, P]),
+    "rgcsr_row_order_workspace_bytes": (SZ, [I64]),
+    "rgcsr_descending_order": (ctypes.c_int, [_PCSR, P, P, SZ, P]),
     "rgcsr_spmv": (ctypes.c_int, [_PM, P, P, P]),
     "rgcsr_spmv_ex": (ctypes.c_int, [_PM, P, P, _PL, P]),
     "rgcsr_spmv_host": (ctypes.c_int, [_PM, P, P, P, P, _PL, ctypes.POINTER(LongRows), P]),

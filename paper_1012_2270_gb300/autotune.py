@@ -98,7 +98,9 @@ def _time(fn, reps: int, flush: torch.Tensor) -> float:
 def candidates(rowptr, dtype: torch.dtype):
     """Configurations worth timing: for dense groups the G = 32 kernels; for
     uneven rows small group sizes, with and without the long-row segment
-    schedule (threshold T, 256 slots per segment)."""
+    schedule (threshold T, 256 slots per segment), and the rows in
+    descending length order (Sec. 4.4.2, Table 7), which makes the groups
+    dense again, with the G = 32 kernels and the segment schedule."""
     lengths = np.diff(np.asarray(rowptr, dtype=np.int64))
     nnz = int(lengths.sum())
     irregular = stored_slots(lengths, 32) * 4 > nnz * 5
@@ -110,13 +112,18 @@ def candidates(rowptr, dtype: torch.dtype):
         Gm = model_group_size(rowptr, dtype.itemsize)
         cands += [dict(group_size=G, kernel=L.KERNEL_SPLIT) for G in sorted({1, 2, 4, 8, Gm})]
         cands += [dict(group_size=G, long_rows=[T, 256]) for G in (1, 2, 4) for T in (16, 32, 64)]
+        desc = dict(group_size=32, row_order="descending")
+        cands += [dict(desc, kernel=k) for k in (L.KERNEL_AUTO, L.KERNEL_LEAN, L.KERNEL_SPLIT)]
+        cands += [dict(desc, kernel=L.KERNEL_TMA, variant=v) for v in range(4)]
+        cands += [dict(desc, long_rows=[T, 256]) for T in (32, 64, 128, 256)]
     return cands
 
 
 def build(rowptr, col, val, n_cols: int, config: dict, dtype: torch.dtype):
     """The RgCSR matrix and spmv keyword arguments of a configuration."""
     from .rgcsr import RgCSRMatrix
-    M = RgCSRMatrix.from_csr(rowptr, col, val, n_cols, group_size=config["group_size"], dtype=dtype)
+    M = RgCSRMatrix.from_csr(rowptr, col, val, n_cols, group_size=config["group_size"], dtype=dtype,
+                             row_order=config.get("row_order"))
     if "long_rows" in config:
         M.split_long_rows(*config["long_rows"])
     return M, {k: v for k, v in config.items() if k in ("kernel", "variant")}
@@ -136,10 +143,11 @@ def tune(rowptr, col, val, n_cols: int, dtype: torch.dtype = torch.float32, reps
     built = {}
     results = []
     for c in candidates(rowptr, dtype):
-        G = c["group_size"]
-        if G not in built:
-            built[G] = RgCSRMatrix.from_csr(rowptr, col, val, n_cols, group_size=G, dtype=dtype)
-        M = built[G]
+        fmt = (c["group_size"], c.get("row_order"))
+        if fmt not in built:
+            built[fmt] = RgCSRMatrix.from_csr(rowptr, col, val, n_cols, group_size=fmt[0], dtype=dtype,
+                                              row_order=fmt[1])
+        M = built[fmt]
         M._long = None
         if "long_rows" in c:
             M.split_long_rows(*c["long_rows"])

@@ -11,6 +11,7 @@ RGCSR_API const char *rgcsr_status_string(int status) {
         case RGCSR_ERR_UNSUPPORTED_DTYPE: return "unsupported value type for this call";
         case RGCSR_ERR_CUDA: return "CUDA runtime error";
         case RGCSR_ERR_WORKSPACE: return "workspace missing or too small";
+        case RGCSR_ERR_BAD_PERM: return "row_perm is not a permutation of the rows";
         default: return "unknown status";
     }
 }

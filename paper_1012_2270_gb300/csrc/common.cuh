@@ -66,6 +66,12 @@ __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
 template <typename T>
 __device__ __forceinline__ T ld_x(const T *p) { return __ldg(p); }
 
+// Output index of stored row `row`: the CSR row it holds under a row order
+// (rgcsr_matrix::row_perm), or the row itself without one.
+__device__ __forceinline__ int64_t out_row(const int32_t *perm, int64_t row) {
+    return perm ? (int64_t)ld_stream(perm + row) : row;
+}
+
 // ---------------------------------------------------------------------------
 // Row pointer access for int32 or int64 CSR row pointers.
 // ---------------------------------------------------------------------------
@@ -113,7 +119,10 @@ int exclusive_scan_i64(int64_t *data, int64_t count, int64_t *partials, cudaStre
 // row pointer (1) or a column outside [0, n_cols) (2); also writes the
 // longest row length to *max_len (device int64, must start at 0).
 int launch_validate_csr(const rgcsr_csr *A, int *flags, int64_t *max_len, cudaStream_t s);
-int launch_row_lengths(const rgcsr_csr *A, int32_t *row_lengths, cudaStream_t s);
+// row_lengths[k] = length of CSR row perm[k] (perm == nullptr: row k)
+int launch_row_lengths(const rgcsr_csr *A, const int32_t *perm, int32_t *row_lengths, cudaStream_t s);
+// sets bit 4 of *flags unless perm is a permutation of [0, n); seen: n ints of scratch
+int launch_check_perm(const int32_t *perm, int64_t n, int32_t *seen, int *flags, cudaStream_t s);
 
 // Vector kernels (blas1.cu).  dot_device writes the dot product of x and y
 // (accumulated in double, deterministic) to the device scalar *out, using

@@ -1,8 +1,9 @@
 // convert.cu -- CSR -> RgCSR conversion (Sec. 3.4 of the paper: row groups,
 // padding to the group's longest row, groupPointers, rowLengths).
 //
-// rgcsr_plan:    validate CSR, row lengths, per-group slab size R_g*K_g,
-//                exclusive scan -> group_ptr; returns n_stored to the host.
+// rgcsr_plan:    validate CSR (and the row order, if given), row lengths,
+//                per-group slab size R_g*K_g, exclusive scan -> group_ptr;
+//                returns n_stored to the host.
 // rgcsr_convert: one warp per group streams the group's slab
 //                [group_ptr[g], group_ptr[g+1]) with coalesced writes; slot
 //                e of the slab is (slot j, row t) = (e / R_g, e % R_g).
@@ -35,7 +36,7 @@ template <typename V>
 __global__ void __launch_bounds__(256)
 scatter_kernel(RowPtr rp, const int32_t *__restrict__ col, const V *__restrict__ val,
                int64_t n, int32_t G, int64_t n_groups, const int64_t *__restrict__ gp,
-               const int32_t *__restrict__ rl, V *__restrict__ out_val,
+               const int32_t *__restrict__ rl, const int32_t *__restrict__ perm, V *__restrict__ out_val,
                int32_t *__restrict__ out_col, int64_t *__restrict__ s2c) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -48,13 +49,14 @@ scatter_kernel(RowPtr rp, const int32_t *__restrict__ col, const V *__restrict__
         int64_t j = lane / R;
         int t = lane % R;
         for (int64_t e = lane; e < size; e += 32) {
-            const int64_t row = first + t;
+            const int64_t row = first + t;          // stored row
             const int len = rl[row];
             V v = 0;
             int c = 0;
             int64_t src = -1;
-            if (j < len) {
-                src = rp[row] + j;
+            const int64_t src_row = perm ? (int64_t)perm[row] : row;   // checked by rgcsr_plan
+            if (j < len && src_row >= 0 && src_row < n) {
+                src = rp[src_row] + j;
                 v = val[src];
                 c = col[src];
             }
@@ -94,7 +96,11 @@ RGCSR_API int rgcsr_plan(const rgcsr_csr *A, rgcsr_matrix *M, void *workspace,
     auto *partials = reinterpret_cast<int64_t *>(static_cast<char *>(workspace) + kStatusBytes);
     RGCSR_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(PlanStatus), s));
     if ((st = launch_validate_csr(A, &status->flags, &status->max_len, s)) != RGCSR_OK) return st;
-    if ((st = launch_row_lengths(A, M->row_lengths, s)) != RGCSR_OK) return st;
+    if (M->row_perm && n > 0) {
+        // row_lengths doubles as the permutation check's hit counters
+        if ((st = launch_check_perm(M->row_perm, n, M->row_lengths, &status->flags, s)) != RGCSR_OK) return st;
+    }
+    if ((st = launch_row_lengths(A, M->row_perm, M->row_lengths, s)) != RGCSR_OK) return st;
     if (n_groups > 0) {
         group_sizes_kernel<<<(unsigned)ceil_div(n_groups, 256), 256, 0, s>>>(
             M->row_lengths, n, G, n_groups, M->group_ptr);
@@ -110,6 +116,7 @@ RGCSR_API int rgcsr_plan(const rgcsr_csr *A, rgcsr_matrix *M, void *workspace,
     RGCSR_CUDA_TRY(cudaStreamSynchronize(s));
     if (host_status.flags & 1) return RGCSR_ERR_BAD_ROWPTR;
     if (host_status.flags & 2) return RGCSR_ERR_COL_OOB;
+    if (host_status.flags & 4) return RGCSR_ERR_BAD_PERM;
 
     M->n_rows = n;
     M->n_cols = A->n_cols;
@@ -134,12 +141,12 @@ RGCSR_API int rgcsr_convert(const rgcsr_csr *A, const rgcsr_matrix *M, rgcsr_str
     if (A->value_type == RGCSR_F64) {
         scatter_kernel<uint64_t><<<(unsigned)blocks, 256, 0, s>>>(
             rp, A->col_idx, static_cast<const uint64_t *>(A->values), M->n_rows, M->group_size,
-            M->n_groups, M->group_ptr, M->row_lengths, static_cast<uint64_t *>(M->values),
+            M->n_groups, M->group_ptr, M->row_lengths, M->row_perm, static_cast<uint64_t *>(M->values),
             M->columns, M->slot_to_csr);
     } else {
         scatter_kernel<uint32_t><<<(unsigned)blocks, 256, 0, s>>>(
             rp, A->col_idx, static_cast<const uint32_t *>(A->values), M->n_rows, M->group_size,
-            M->n_groups, M->group_ptr, M->row_lengths, static_cast<uint32_t *>(M->values),
+            M->n_groups, M->group_ptr, M->row_lengths, M->row_perm, static_cast<uint32_t *>(M->values),
             M->columns, M->slot_to_csr);
     }
     return launch_status();

@@ -118,6 +118,7 @@ RGCSR_API int rgcsr_quantize(const rgcsr_matrix *src, rgcsr_matrix *dst, rgcsr_s
     dst->n_groups = src->n_groups;
     dst->n_stored = src->n_stored;
     dst->max_row_len = src->max_row_len;
+    dst->row_perm = src->row_perm;        // the slabs keep src's stored row order
     if (src->n_rows == 0) return RGCSR_OK;
     if (!src->group_ptr || !src->row_lengths || !dst->row_scale) return RGCSR_ERR_INVALID_ARG;
     if (src->n_stored > 0 && (!src->values || !dst->values)) return RGCSR_ERR_INVALID_ARG;

@@ -112,9 +112,22 @@ __global__ void validate_cols_kernel(const int32_t *__restrict__ col, int64_t nn
     if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, 2);
 }
 
-__global__ void row_lengths_kernel(RowPtr rp, int64_t n, int32_t *rl) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) rl[i] = (int32_t)(rp[i + 1] - rp[i]);
+// rl[k] = length of CSR row perm[k] (row k without perm).
+__global__ void row_lengths_kernel(RowPtr rp, int64_t n, const int32_t *__restrict__ perm, int32_t *rl) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t i = perm ? perm[k] : k;
+    // an out-of-range entry is flagged by check_perm_kernel; never read past row_ptr
+    rl[k] = (i >= 0 && i < n) ? (int32_t)(rp[i + 1] - rp[i]) : 0;
+}
+
+// perm is a permutation of [0, n) iff every entry is in range and no row is
+// hit twice; seen[] (n counters, zeroed) counts the hits.
+__global__ void check_perm_kernel(const int32_t *__restrict__ perm, int64_t n, int32_t *seen, int *flags) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int32_t i = perm[k];
+    if (i < 0 || (int64_t)i >= n || atomicAdd(seen + i, 1) != 0) atomicOr(flags, 4);
 }
 
 }  // namespace
@@ -142,10 +155,17 @@ int launch_validate_csr(const rgcsr_csr *A, int *flags, int64_t *max_len, cudaSt
     return launch_status();
 }
 
-int launch_row_lengths(const rgcsr_csr *A, int32_t *row_lengths, cudaStream_t s) {
+int launch_row_lengths(const rgcsr_csr *A, const int32_t *perm, int32_t *row_lengths, cudaStream_t s) {
     if (A->n_rows == 0) return RGCSR_OK;
     RowPtr rp{A->row_ptr, A->row_ptr_type == RGCSR_I64};
-    row_lengths_kernel<<<(unsigned)ceil_div(A->n_rows, 256), 256, 0, s>>>(rp, A->n_rows, row_lengths);
+    row_lengths_kernel<<<(unsigned)ceil_div(A->n_rows, 256), 256, 0, s>>>(rp, A->n_rows, perm, row_lengths);
+    return launch_status();
+}
+
+int launch_check_perm(const int32_t *perm, int64_t n, int32_t *seen, int *flags, cudaStream_t s) {
+    if (n == 0) return RGCSR_OK;
+    RGCSR_CUDA_TRY(cudaMemsetAsync(seen, 0, (size_t)n * sizeof(int32_t), s));
+    check_perm_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(perm, n, seen, flags);
     return launch_status();
 }
 

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kThreads)
 rgcsr_spmm_kernel(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *__restrict__ col,
                   const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
                   const float *__restrict__ scale, const typename SV<V>::A *__restrict__ X, int64_t ldx,
-                  typename SV<V>::A *__restrict__ Y, int64_t ldy) {
+                  typename SV<V>::A *__restrict__ Y, int64_t ldy, const int32_t *__restrict__ perm) {
     using A = typename SV<V>::A;
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -152,7 +152,7 @@ rgcsr_spmm_kernel(int64_t n, int32_t G, const V *__restrict__ val, const int32_t
         }
     }
     if (valid) {
-        A *yr = Y + row * ldy;
+        A *yr = Y + out_row(perm, row) * ldy;
         A s = 1;
         if constexpr (SV<V>::scaled) s = __ldg(scale + row);
 #pragma unroll
@@ -171,11 +171,11 @@ int launch_chunk(const rgcsr_matrix *M, const typename SV<V>::A *X, int64_t ldx,
     if (vec)
         rgcsr_spmm_kernel<V, KC, true><<<(unsigned)blocks, kThreads, 0, s>>>(
             M->n_rows, M->group_size, val, M->columns, M->group_ptr, M->row_lengths, M->row_scale,
-            X, ldx, Y, ldy);
+            X, ldx, Y, ldy, M->row_perm);
     else
         rgcsr_spmm_kernel<V, KC, false><<<(unsigned)blocks, kThreads, 0, s>>>(
             M->n_rows, M->group_size, val, M->columns, M->group_ptr, M->row_lengths, M->row_scale,
-            X, ldx, Y, ldy);
+            X, ldx, Y, ldy, M->row_perm);
     return launch_status();
 }
 

@@ -72,7 +72,7 @@ template <typename T, bool NC>
 __global__ void rgcsr_spmv_paper(int64_t n, int32_t G, const T *__restrict__ val,
                                  const int32_t *__restrict__ col, const int64_t *__restrict__ gp,
                                  const int32_t *__restrict__ rl, const T *__restrict__ x,
-                                 T *__restrict__ y) {
+                                 T *__restrict__ y, const int32_t *__restrict__ perm) {
     const int64_t g = blockIdx.x;
     const int64_t row = g * G + threadIdx.x;
     if (row >= n) return;
@@ -84,7 +84,7 @@ __global__ void rgcsr_spmv_paper(int64_t n, int32_t G, const T *__restrict__ val
         acc += val[ptr] * gather<T, NC>(x, col[ptr]);
         ptr += R;
     }
-    y[row] = acc;
+    y[out_row(perm, row)] = acc;
 }
 
 // Split slot j0 for an irregular warp: every lane proposes its own row
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kDefaultThreads)
 rgcsr_spmv_split(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *__restrict__ col,
                  const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
                  const float *__restrict__ scale, const typename VT<V>::A *__restrict__ x,
-                 typename VT<V>::A *__restrict__ y, int w4, int cap) {
+                 typename VT<V>::A *__restrict__ y, const int32_t *__restrict__ perm, int w4, int cap) {
     using A = typename VT<V>::A;
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -180,7 +180,7 @@ rgcsr_spmv_split(int64_t n, int32_t G, const V *__restrict__ val, const int32_t 
         part = warp_sum(part);
         if (lane == r) acc += part;
     }
-    if (valid) y[row] = finish<V>(acc, scale, row);
+    if (valid) y[out_row(perm, row)] = finish<V>(acc, scale, row);
 }
 
 // One thread per row and no long-row split, sized for full occupancy
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kDefaultThreads, MIN_BLOCKS)
 rgcsr_spmv_lean(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *__restrict__ col,
                 const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
                 const float *__restrict__ scale, const typename VT<V>::A *__restrict__ x,
-                typename VT<V>::A *__restrict__ y) {
+                typename VT<V>::A *__restrict__ y, const int32_t *__restrict__ perm) {
     using A = typename VT<V>::A;
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= n) return;
@@ -220,7 +220,7 @@ rgcsr_spmv_lean(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *
         vp += (int64_t)U * stride;
         cp += (int64_t)U * stride;
     }
-    y[row] = finish<V>(acc, scale, row);
+    y[out_row(perm, row)] = finish<V>(acc, scale, row);
 }
 
 template <typename V>
@@ -240,7 +240,7 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
         // 8 blocks (32 registers) fit plain FP32; FP64 and scaled storage need 6
         constexpr int min_blocks = (std::is_same<V, float>::value) ? 8 : 6;
         rgcsr_spmv_lean<V, 4, min_blocks><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
-            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y);
+            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
         return launch_status();
     }
     if (kernel == RGCSR_KERNEL_PAPER) {
@@ -250,10 +250,10 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
             if (G > 1024) return RGCSR_ERR_INVALID_ARG;
             if (nc)
                 rgcsr_spmv_paper<V, true><<<(unsigned)M->n_groups, G, 0, s>>>(
-                    n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y);
+                    n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y, M->row_perm);
             else
                 rgcsr_spmv_paper<V, false><<<(unsigned)M->n_groups, G, 0, s>>>(
-                    n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y);
+                    n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y, M->row_perm);
             return launch_status();
         }
     }
@@ -265,10 +265,10 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
     if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
     if (nc)
         rgcsr_spmv_split<V, true><<<(unsigned)blocks, threads, 0, s>>>(
-            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, w4, INT_MAX);
+            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm, w4, INT_MAX);
     else
         rgcsr_spmv_split<V, false><<<(unsigned)blocks, threads, 0, s>>>(
-            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, w4, INT_MAX);
+            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm, w4, INT_MAX);
     return launch_status();
 }
 
@@ -355,7 +355,7 @@ template <typename V>
 __global__ void seg_combine_kernel(int64_t n_long, const int32_t *__restrict__ long_row,
                                    const int32_t *__restrict__ long_first, const int32_t *__restrict__ long_count,
                                    const typename VT<V>::A *__restrict__ partials, const float *__restrict__ scale,
-                                   typename VT<V>::A *__restrict__ y) {
+                                   typename VT<V>::A *__restrict__ y, const int32_t *__restrict__ perm) {
     using A = typename VT<V>::A;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_long) return;
@@ -363,7 +363,7 @@ __global__ void seg_combine_kernel(int64_t n_long, const int32_t *__restrict__ l
     const int64_t f = long_first[k];
     A s = 0;
     for (int q = 0; q < long_count[k]; ++q) s += partials[f + q];
-    y[row] += finish<V>(s, scale, row);
+    y[out_row(perm, row)] += finish<V>(s, scale, row);
 }
 
 template <typename V>
@@ -377,7 +377,8 @@ int launch_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *S, const type
     const int64_t blocks = ceil_div(n, kDefaultThreads);
     if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
     rgcsr_spmv_split<V, true><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
-        n, M->group_size, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, 8, S->threshold);
+        n, M->group_size, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm, 8,
+        S->threshold);
     if (S->n_segments == 0) return launch_status();
     int64_t sb = ceil_div(S->n_segments, kDefaultThreads / 32);
     if (sb > 152 * 16) sb = 152 * 16;
@@ -386,7 +387,7 @@ int launch_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *S, const type
         n, M->group_size, val, M->columns, M->group_ptr, M->row_lengths, S->seg_row, S->seg_start,
         S->segment, S->n_segments, x, part);
     seg_combine_kernel<V><<<(unsigned)ceil_div(S->n_long_rows, 256), 256, 0, s>>>(
-        S->n_long_rows, S->long_row, S->long_first, S->long_count, part, scale, y);
+        S->n_long_rows, S->long_row, S->long_first, S->long_count, part, scale, y, M->row_perm);
     return launch_status();
 }
 

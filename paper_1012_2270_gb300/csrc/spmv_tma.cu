@@ -125,7 +125,8 @@ struct SlabRing {
 // The partial last group (n not a multiple of 32) by plain loads.
 template <typename T>
 __device__ void tail_group(int64_t n, int64_t nb_full, const T *val, const int32_t *col,
-                           const int64_t *gp, const int32_t *rl, const T *x, T *y, int lane) {
+                           const int64_t *gp, const int32_t *rl, const T *x, T *y, const int32_t *perm,
+                           int lane) {
     const int64_t row = nb_full * 32 + lane;
     const int R = (int)(n - nb_full * 32);
     if (row < n) {
@@ -133,7 +134,7 @@ __device__ void tail_group(int64_t n, int64_t nb_full, const T *val, const int32
         const int L = rl[row];
         T a = 0;
         for (int j = 0; j < L; ++j, p += R) a = fma(val[p], __ldg(x + col[p]), a);
-        y[row] = a;
+        y[out_row(perm, row)] = a;
     }
 }
 
@@ -141,7 +142,7 @@ template <typename T, int CAP, int STAGES>
 __global__ void __launch_bounds__(kTmaWarps * 32)
 rgcsr_spmv_tma(int64_t n, int64_t nb_full, const T *__restrict__ val, const int32_t *__restrict__ col,
                const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
-               const T *__restrict__ x, T *__restrict__ y) {
+               const T *__restrict__ x, T *__restrict__ y, const int32_t *__restrict__ perm) {
     using C = TmaCfg<T, CAP, STAGES>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[kTmaWarps][STAGES];
@@ -192,11 +193,11 @@ rgcsr_spmv_tma(int64_t n, int64_t nb_full, const T *__restrict__ val, const int3
         for (int u = 0; u < CAP; ++u)
             if (u < cnt) acc = fma(v[u], xv[u], acc);
         if (m.w) {
-            y[(int64_t)m.x * 32 + lane] = acc;
+            y[out_row(perm, (int64_t)m.x * 32 + lane)] = acc;
             acc = 0;
         }
     }
-    if (gw == tw - 1 && nb_full * 32 < n) tail_group(n, nb_full, val, col, gp, rl, x, y, lane);
+    if (gw == tw - 1 && nb_full * 32 < n) tail_group(n, nb_full, val, col, gp, rl, x, y, perm, lane);
 }
 
 int sm_count() {
@@ -235,7 +236,7 @@ int launch_tma_cfg(const rgcsr_matrix *M, const T *x, T *y, cudaStream_t s) {
     if (need < grid) grid = need > 0 ? need : 1;
     kern<<<(unsigned)grid, kTmaWarps * 32, C::SMEM, s>>>(
         M->n_rows, nb_full, static_cast<const T *>(M->values), M->columns, M->group_ptr,
-        M->row_lengths, x, y);
+        M->row_lengths, x, y, M->row_perm);
     return launch_status();
 }
 

@@ -6,7 +6,9 @@
 //   * rgcsr_gather_values / rgcsr_compose_index: refresh an RgCSR matrix's
 //     values from CSR-ordered values through a slot -> source index map;
 //   * rgcsr_sampled_dot: out[p] = sum_b G[row_p, b] X[col_p, b], the gradient
-//     of sum(G .* (A X)) with respect to every stored value.
+//     of sum(G .* (A X)) with respect to every stored value;
+//   * rgcsr_descending_order: the rows sorted by length, longest first
+//     (stable), the row order of Sec. 4.4.2 / Table 7 (the same radix sort).
 // None of this is in the paper (which has no backward pass); the transposed
 // matrix is an ordinary RgCSR matrix built with rgcsr_plan / rgcsr_convert.
 #include "common.cuh"
@@ -196,6 +198,17 @@ __global__ void sampled_dot_kernel(int64_t nnz, int k, const int32_t *__restrict
     }
 }
 
+// Sort key of stored position k for the descending order: larger rows get
+// smaller keys; lengths are clamped to [0, mask] so that any row_ptr gives
+// keys within the sorted bits.
+__global__ void descending_keys_kernel(RowPtr rp, int64_t n, uint32_t mask, uint32_t *__restrict__ keys) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t len = rp[i + 1] - rp[i];
+    len = len < 0 ? 0 : (len > (int64_t)mask ? (int64_t)mask : len);
+    keys[i] = mask - (uint32_t)len;
+}
+
 unsigned grid_for(int64_t n, int threads) {
     int64_t b = ceil_div(n, threads);
     if (b > 152 * 64) b = 152 * 64;
@@ -312,4 +325,34 @@ RGCSR_API int rgcsr_sampled_dot(int64_t nnz, int32_t k, const int32_t *row_index
     else
         return RGCSR_ERR_UNSUPPORTED_DTYPE;
     return launch_status();
+}
+
+RGCSR_API size_t rgcsr_row_order_workspace_bytes(int64_t n_rows) {
+    if (n_rows < 0) return 0;
+    return sort_workspace_bytes(n_rows) + align_up((size_t)n_rows * 4, 256);
+}
+
+RGCSR_API int rgcsr_descending_order(const rgcsr_csr *A, int32_t *row_perm, void *workspace,
+                                     size_t workspace_bytes, rgcsr_stream_t stream) {
+    int st = check_csr(A);
+    if (st != RGCSR_OK) return st;
+    const int64_t n = A->n_rows;
+    if (n == 0) return RGCSR_OK;
+    if (n > (int64_t)INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
+    if (!row_perm) return RGCSR_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < rgcsr_row_order_workspace_bytes(n)) return RGCSR_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    SortBuffers b = carve_sort(workspace, n);
+    uint32_t *keys = reinterpret_cast<uint32_t *>(static_cast<char *>(workspace) + sort_workspace_bytes(n));
+    // a valid row has at most nnz entries: sort on just enough bits for that
+    int bits = 1;
+    while (bits < 32 && ((int64_t)1 << bits) <= A->nnz) ++bits;
+    const uint32_t mask = bits >= 32 ? 0xffffffffu : ((1u << bits) - 1u);
+    RowPtr rp{A->row_ptr, A->row_ptr_type == RGCSR_I64};
+    descending_keys_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(rp, n, mask, keys);
+    if ((st = launch_status()) != RGCSR_OK) return st;
+    const uint32_t *skeys = nullptr, *sidx = nullptr;
+    if ((st = radix_sort_indices(keys, n, bits, b, &skeys, &sidx, s)) != RGCSR_OK) return st;
+    RGCSR_CUDA_TRY(cudaMemcpyAsync(row_perm, sidx, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    return RGCSR_OK;
 }

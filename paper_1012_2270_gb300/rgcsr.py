@@ -57,7 +57,9 @@ class RgCSRMatrix:
 
     Attributes are torch tensors: ``values`` [n_stored], ``columns`` int32
     [n_stored], ``group_ptr`` int64 [n_groups+1], ``row_lengths`` int32
-    [n_rows] and optionally ``slot_to_csr`` int64 [n_stored].
+    [n_rows] and optionally ``slot_to_csr`` int64 [n_stored] and
+    ``row_perm`` int32 [n_rows] (the CSR row held by each stored row when a
+    row order was used; x and y are always in the CSR's row order).
     """
 
     def __init__(self):
@@ -65,17 +67,22 @@ class RgCSRMatrix:
         self.values = self.columns = self.group_ptr = self.row_lengths = None
         self.row_scale = None
         self.slot_to_csr = None
+        self.row_perm = None
         self._long = None          # long-row segment schedule, if enabled
 
     # -- construction ------------------------------------------------------
     @classmethod
     def from_csr(cls, rowptr, col, val, n_cols: int, group_size: int = 32,
                  dtype: torch.dtype | None = None, keep_slot_map: bool = False,
-                 device="cuda", stream=None) -> "RgCSRMatrix":
+                 row_order=None, device="cuda", stream=None) -> "RgCSRMatrix":
         """Converts a CSR matrix (host numpy or device tensors) to RgCSR.
 
         ``dtype`` (float32/float64) is the storage type of the values; the
-        CSR values are cast to it before conversion.  Synchronises once."""
+        CSR values are cast to it before conversion.  ``row_order``: None
+        (rows in CSR order), "descending" (rows by length, longest first,
+        stable -- Sec. 4.4.2, Table 7), or any permutation of the rows as an
+        int32 array (stored row k = CSR row row_order[k]).  Synchronises
+        once."""
         rowptr = _dev(rowptr, None, device)
         col = _dev(col, torch.int32, device)
         val = _dev(val, dtype, device)
@@ -93,9 +100,22 @@ class RgCSRMatrix:
         M.value_type = A.value_type
         M.row_lengths = _ptr(self.row_lengths)
         M.group_ptr = _ptr(self.group_ptr)
+        st = _stream_ptr(stream)
+        if row_order is not None and n > 0:
+            if isinstance(row_order, str):
+                if row_order != "descending":
+                    raise ValueError(f"unknown row order {row_order!r}")
+                self.row_perm = torch.empty(n, dtype=torch.int32, device=device)
+                ob = L.lib().rgcsr_row_order_workspace_bytes(n)
+                ows = torch.empty(ob, dtype=torch.uint8, device=device)
+                L.call("rgcsr_descending_order", ctypes.byref(A), _ptr(self.row_perm), _ptr(ows), ob, st)
+            else:
+                self.row_perm = _dev(row_order, torch.int32, device)
+                if self.row_perm.numel() != n:
+                    raise ValueError("row_order must have one entry per row")
+            M.row_perm = _ptr(self.row_perm)
         ws_bytes = L.lib().rgcsr_plan_workspace_bytes(n, G)
         ws = torch.empty(ws_bytes, dtype=torch.uint8, device=device)
-        st = _stream_ptr(stream)
         L.call("rgcsr_plan", ctypes.byref(A), ctypes.byref(M), _ptr(ws), ws_bytes, st)
         self.values = torch.empty(M.n_stored, dtype=val.dtype, device=device)
         self.columns = torch.empty(M.n_stored, dtype=torch.int32, device=device)
@@ -139,6 +159,7 @@ class RgCSRMatrix:
         q = RgCSRMatrix()
         q.columns, q.group_ptr, q.row_lengths = self.columns, self.group_ptr, self.row_lengths
         q.slot_to_csr = self.slot_to_csr
+        q.row_perm = self.row_perm
         dt = {"bf16": torch.bfloat16, "f16": torch.float16}[fmt]
         dev = self.group_ptr.device
         q.values = torch.empty(self.s.n_stored, dtype=dt, device=dev)

@@ -175,3 +175,58 @@ def test_full_size_counts_stencil():
     x = synth.uniform_vector(A.n_cols, 0)
     y, _ = oracle.csr_spmv(A.rowptr, A.col, A.val, x)
     assert np.array_equal(oracle.rgcsr_spmv(lay, x), y)
+
+
+def dense_of(rowptr, col, val, n_cols):
+    D = np.zeros((len(rowptr) - 1, n_cols))
+    for i in range(len(rowptr) - 1):
+        for p in range(rowptr[i], rowptr[i + 1]):
+            D[i, col[p]] += float(val[p])
+    return D
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_permute_rows_is_row_permutation_of_dense(seed):
+    # Row ordering (Sec. 4.4.2, Table 7) stores P A: row k of the reordered
+    # matrix is row perm[k] of A, entry for entry
+    rng = np.random.default_rng(seed)
+    n, m = 9, 7
+    A = csr_from_lengths(rng.integers(0, 6, n), m=m, seed=seed)
+    perm = rng.permutation(n)
+    rp, c, v, src = oracle.permute_rows(A.rowptr, A.col, A.val, perm)
+    assert np.array_equal(dense_of(rp, c, v, m), dense_of(A.rowptr, A.col, A.val, m)[perm])
+    assert np.array_equal(A.col[src], c) and np.array_equal(A.val[src], v)
+    assert sorted(src.tolist()) == list(range(A.nnz))
+    with pytest.raises(ValueError):
+        oracle.permute_rows(A.rowptr, A.col, A.val, np.zeros(n, np.int64))
+
+
+@pytest.mark.parametrize("G", [1, 2, 3, 4])
+def test_reordered_layout(G):
+    rng = np.random.default_rng(G)
+    n, m = 11, 8
+    L = rng.integers(0, 7, n)
+    A = csr_from_lengths(L, m=m, seed=G)
+    x = rng.uniform(-1, 1, m)
+    plain = oracle.rgcsr_layout(A.rowptr, A.col, A.val, G)
+    same = oracle.rgcsr_layout(A.rowptr, A.col, A.val, G, row_order=np.arange(n))
+    for f in ("row_lengths", "group_ptr", "values", "columns", "slot_to_csr"):
+        assert np.array_equal(getattr(plain, f), getattr(same, f)), f
+    perm = oracle.descending_order(A.rowptr)
+    lay = oracle.rgcsr_layout(A.rowptr, A.col, A.val, G, row_order=perm)
+    # the address map of the format applied to the reordered lengths
+    addr, total = independent_map(L[perm].tolist(), G)
+    assert lay.n_stored == total
+    assert lay.row_lengths.tolist() == L[perm].tolist()
+    for k in range(n):
+        i = perm[k]
+        for j in range(L[i]):
+            a = addr[(k, j)]
+            assert lay.slot_to_csr[a] == A.rowptr[i] + j
+            assert lay.values[a] == A.val[A.rowptr[i] + j] and lay.columns[a] == A.col[A.rowptr[i] + j]
+    pad = lay.slot_to_csr < 0
+    assert (lay.values[pad] == 0).all() and (lay.columns[pad] == 0).all()
+    # y comes back in A's row order: the same sums as the plain CSR product
+    y, _ = oracle.csr_spmv(A.rowptr, A.col, A.val, x)
+    assert np.array_equal(oracle.rgcsr_spmv(lay, x), y)
+    assert np.allclose(y, dense_of(A.rowptr, A.col, A.val, m) @ x, rtol=0, atol=1e-12)
