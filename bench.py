@@ -92,6 +92,8 @@ def case_bytes(A, n_groups, dtype):
 def kernel_name(cfg, M, A, dt):
     """The kernel that a configuration runs (the library's dispatch rules)."""
     t = "float" if dt == "f32" else "double"
+    if "tiles" in cfg:
+        return f"rgcsr_spmv_tiles_kernel<{t}>"
     if "long_rows" in cfg:
         return f"rgcsr_spmv_split+segments<{t}>"
     k = cfg.get("kernel", 0)
@@ -104,6 +106,32 @@ def kernel_name(cfg, M, A, dt):
         else:
             k = 4 if dense else 2
     return {1: "rgcsr_spmv_paper", 2: "rgcsr_spmv_split", 3: "rgcsr_spmv_tma", 4: "rgcsr_spmv_lean"}[k] + f"<{t}>"
+
+
+def measured_traffic(kernel, cases):
+    """DRAM bytes per launch of `kernel` (mean over the cases that ran it)
+    from the committed ncu summary, or None if a case is missing, ran
+    another kernel, or the kernel's source changed since the capture."""
+    import hashlib
+    try:
+        table = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except (OSError, ValueError):
+        return None
+    vals = []
+    for c in cases:
+        if c["kernel"] != kernel:
+            continue
+        e = table.get(c["key"])
+        if not e or e.get("kernel") != kernel:
+            return None
+        try:
+            sha = hashlib.sha1(open(os.path.join(ROOT, e["source"]), "rb").read()).hexdigest()
+        except OSError:
+            return None
+        if sha != e.get("source_sha1"):
+            return None
+        vals.append(float(e["dram_bytes_per_launch"]))
+    return sum(vals) / len(vals) if vals else None
 
 
 # ---------------------------------------------------------------------------
@@ -344,7 +372,8 @@ def run_ours(args):
     d = by_kernel[dom]
     achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
-            "frac": achieved / peak_hbm, "traffic": None, "kernel": dom, "peak_source": peak_src,
+            "frac": achieved / peak_hbm, "traffic": measured_traffic(dom, cases), "kernel": dom,
+            "peak_source": peak_src,
             "bytes_per_launch": d["bytes"] / d["launches"], "avg_launch_us": 1e3 * d["ms"] / d["launches"]}
 
     # ---- end to end: host x in, host y out, through rgcsr_spmv_host ----
@@ -504,6 +533,7 @@ def measure_forms(mats, cases, detail, dev, stream):
         del absA
         for fmt in ("bf16", "f16"):
             Q = c64["M"].quantized(fmt)
+            Q.copy_schedule(c64["M"])                 # same layout, same launch schedule
             quant.append((name, fmt, Q, c32["x"], torch.empty(A.n_rows, dtype=torch.float32, device=dev), A))
     us = time_rotating([lambda q=q: q[2].spmv(q[3], out=q[4]) for q in quant], 30, stream)
     forms["quantized"] = {}
@@ -517,9 +547,12 @@ def measure_forms(mats, cases, detail, dev, stream):
     del quant, ref
 
     # -- multi-RHS SpMM on (b) ------------------------------------------------
+    # natural row order at the byte model's group size: the SpMM kernel is
+    # thread-per-row, so it does not use the descending-order tiles
     b = [m for m in mats if m[0] == "b"][0][1]
-    Mb = by["b_f32"]["M"]
-    forms["spmm_b_f32"] = {}
+    Mb = RgCSRMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32,
+                              group_size=model_group_size(b.rowptr, 4))
+    forms["spmm_b_f32"] = {"group_size": Mb.group_size}
     for k in (1, 4, 8, 16, 32):
         X = torch.rand(b.n_cols, k, device=dev)
         Y = torch.empty(b.n_rows, k, device=dev)

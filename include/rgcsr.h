@@ -218,15 +218,61 @@ int rgcsr_long_rows_build(const rgcsr_matrix *M, const rgcsr_long_rows *S, void 
 int rgcsr_spmv_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *S, const void *x, void *y,
                          rgcsr_stream_t stream);
 
+/* Group tiles, a launch schedule for G <= 32 (one warp per task, lane t
+ * on row t of the group, so every load of a value or column slab is
+ * coalesced).  A group whose longest row K_g exceeds `tile` slot-rows is cut
+ * into ceil(K_g / tile) tasks of at most `tile` slot-rows each; tasks of
+ * one group write per-row partial sums, and the last of them to finish
+ * (an arrival counter per group, no waiting) adds the partials in task
+ * order and writes y, so the result does not depend on scheduling.  With
+ * rows in descending length order (row_perm, Sec. 4.4.2) the groups are
+ * dense and every warp's work is bounded by `tile` slot-rows, which removes
+ * the long-row imbalance that the paper names as the format's weak point.
+ *   1. set tile, call rgcsr_tiles_plan (sets n_extra, n_split, n_partials;
+ *      synchronises `stream`);
+ *   2. allocate first_extra, part_base (n_groups+1 int64), extra_group
+ *      (n_extra int32), arrivals (n_groups int32) and partials
+ *      (n_partials * 32 elements: double for F64 storage, float otherwise);
+ *   3. rgcsr_tiles_build fills them and zeroes `arrivals` (async);
+ *   4. rgcsr_spmv_tiles computes y = A x in one launch (async).  Tasks
+ *      0 .. n_groups-1 are the first tile of every group; task n_groups + e
+ *      is extra tile e, of group extra_group[e].  One SpMV per schedule may
+ *      be in flight at a time (partials and arrivals are its scratch; each
+ *      group's counter is back at 0 when the launch ends).
+ * RGCSR_ERR_INVALID_ARG if G > 32 or tile < 1. */
+typedef struct {
+    int32_t tile;               /* slot-rows per task, >= 1                   */
+    int32_t variant;            /* 0 = default; 1, 2: fewer / more slot-rows
+                                   in flight per lane (tuning)                */
+    int64_t n_groups;           /* (plan) the matrix's group count            */
+    int64_t n_extra;            /* (plan) tasks beyond one per group          */
+    int64_t n_split;            /* (plan) groups cut into more than one task  */
+    int64_t n_partials;         /* (plan) tasks of split groups               */
+    int64_t *first_extra;       /* n_groups+1: extra tasks of g are
+                                   first_extra[g] .. first_extra[g+1]-1      */
+    int64_t *part_base;         /* n_groups+1: partial slot of g's first task */
+    int32_t *extra_group;       /* n_extra                                    */
+    int32_t *arrivals;          /* n_groups                                   */
+    void *partials;             /* n_partials * 32                            */
+} rgcsr_tiles;
+size_t rgcsr_tiles_workspace_bytes(int64_t n_groups);
+int rgcsr_tiles_plan(const rgcsr_matrix *M, rgcsr_tiles *T, void *workspace,
+                     size_t workspace_bytes, rgcsr_stream_t stream);
+int rgcsr_tiles_build(const rgcsr_matrix *M, const rgcsr_tiles *T, rgcsr_stream_t stream);
+int rgcsr_spmv_tiles(const rgcsr_matrix *M, const rgcsr_tiles *T, const void *x, void *y,
+                     rgcsr_stream_t stream);
+
 /* The same SpMV from and to HOST memory: copies x_host (n_cols elements) to
  * the caller's device buffer x_dev, computes y_dev = A x_dev -- with the
- * long-row schedule if long_rows is not NULL, else rgcsr_spmv_ex with
- * `launch` (NULL = default) -- and copies y_dev to y_host (n_rows
- * elements), all on `stream`.  Pinned host buffers make the copies
- * asynchronous; the caller synchronises before reading y_host. */
+ * group-tile schedule if tiles is not NULL, else the long-row schedule if
+ * long_rows is not NULL, else rgcsr_spmv_ex with `launch` (NULL = default)
+ * -- and copies y_dev to y_host (n_rows elements), all on `stream`.  Pinned
+ * host buffers make the copies asynchronous; the caller synchronises before
+ * reading y_host. */
 int rgcsr_spmv_host(const rgcsr_matrix *M, const void *x_host, void *y_host,
                     void *x_dev, void *y_dev, const rgcsr_launch *launch,
-                    const rgcsr_long_rows *long_rows, rgcsr_stream_t stream);
+                    const rgcsr_long_rows *long_rows, const rgcsr_tiles *tiles,
+                    rgcsr_stream_t stream);
 
 /* Y = A X for k right-hand sides (the SpMV of Sec. 3.4 applied to several
  * vectors at once; not in the paper).  X: row-major [n_cols x k] with row

@@ -59,6 +59,12 @@ class LongRows(ctypes.Structure):
                 ("partials", P)]
 
 
+class Tiles(ctypes.Structure):
+    _fields_ = [("tile", I32), ("variant", I32), ("n_groups", I64), ("n_extra", I64), ("n_split", I64),
+                ("n_partials", I64), ("first_extra", P), ("part_base", P), ("extra_group", P),
+                ("arrivals", P), ("partials", P)]
+
+
 class BatchDesc(ctypes.Structure):
     _fields_ = [("n_rows", I64), ("n_cols", I64), ("val_off", I64), ("row_off", I64),
                 ("group_off", I64), ("x_off", I64), ("group_size", I32), ("reserved", I32)]
@@ -85,7 +91,12 @@ SIGNATURES = {
     "rgcsr_descending_order": (ctypes.c_int, [_PCSR, P, P, SZ, P]),
     "rgcsr_spmv": (ctypes.c_int, [_PM, P, P, P]),
     "rgcsr_spmv_ex": (ctypes.c_int, [_PM, P, P, _PL, P]),
-    "rgcsr_spmv_host": (ctypes.c_int, [_PM, P, P, P, P, _PL, ctypes.POINTER(LongRows), P]),
+    "rgcsr_spmv_host": (ctypes.c_int, [_PM, P, P, P, P, _PL, ctypes.POINTER(LongRows),
+                                       ctypes.POINTER(Tiles), P]),
+    "rgcsr_tiles_workspace_bytes": (SZ, [I64]),
+    "rgcsr_tiles_plan": (ctypes.c_int, [_PM, ctypes.POINTER(Tiles), P, SZ, P]),
+    "rgcsr_tiles_build": (ctypes.c_int, [_PM, ctypes.POINTER(Tiles), P]),
+    "rgcsr_spmv_tiles": (ctypes.c_int, [_PM, ctypes.POINTER(Tiles), P, P, P]),
     "rgcsr_quantize": (ctypes.c_int, [_PM, _PM, P]),
     "rgcsr_long_rows_workspace_bytes": (SZ, [I64]),
     "rgcsr_long_rows_plan": (ctypes.c_int, [_PM, ctypes.POINTER(LongRows), P, SZ, P]),

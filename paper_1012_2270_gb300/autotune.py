@@ -100,7 +100,9 @@ def candidates(rowptr, dtype: torch.dtype):
     uneven rows small group sizes, with and without the long-row segment
     schedule (threshold T, 256 slots per segment), and the rows in
     descending length order (Sec. 4.4.2, Table 7), which makes the groups
-    dense again, with the G = 32 kernels and the segment schedule."""
+    dense again, with the segment schedule or group tiles of C slot-rows
+    (a one-warp-per-row-group kernel on a very long group would serialise,
+    so those are not timed)."""
     lengths = np.diff(np.asarray(rowptr, dtype=np.int64))
     nnz = int(lengths.sum())
     irregular = stored_slots(lengths, 32) * 4 > nnz * 5
@@ -113,9 +115,10 @@ def candidates(rowptr, dtype: torch.dtype):
         cands += [dict(group_size=G, kernel=L.KERNEL_SPLIT) for G in sorted({1, 2, 4, 8, Gm})]
         cands += [dict(group_size=G, long_rows=[T, 256]) for G in (1, 2, 4) for T in (16, 32, 64)]
         desc = dict(group_size=32, row_order="descending")
-        cands += [dict(desc, kernel=k) for k in (L.KERNEL_AUTO, L.KERNEL_LEAN, L.KERNEL_SPLIT)]
-        cands += [dict(desc, kernel=L.KERNEL_TMA, variant=v) for v in range(4)]
         cands += [dict(desc, long_rows=[T, 256]) for T in (32, 64, 128, 256)]
+        cands += [dict(desc, tiles=[C, v]) for C in (32, 64, 128) for v in (0, 1, 2)]
+    if not irregular:
+        cands += [dict(group_size=32, tiles=[64, v]) for v in (0, 1, 2)]
     return cands
 
 
@@ -126,6 +129,8 @@ def build(rowptr, col, val, n_cols: int, config: dict, dtype: torch.dtype):
                              row_order=config.get("row_order"))
     if "long_rows" in config:
         M.split_long_rows(*config["long_rows"])
+    if "tiles" in config:
+        M.tile_groups(*config["tiles"])
     return M, {k: v for k, v in config.items() if k in ("kernel", "variant")}
 
 
@@ -148,9 +153,11 @@ def tune(rowptr, col, val, n_cols: int, dtype: torch.dtype = torch.float32, reps
             built[fmt] = RgCSRMatrix.from_csr(rowptr, col, val, n_cols, group_size=fmt[0], dtype=dtype,
                                               row_order=fmt[1])
         M = built[fmt]
-        M._long = None
+        M._long = M._tiles = None
         if "long_rows" in c:
             M.split_long_rows(*c["long_rows"])
+        if "tiles" in c:
+            M.tile_groups(*c["tiles"])
         kw = {k: v for k, v in c.items() if k in ("kernel", "variant")}
         try:
             y = M.spmv(x, **kw)
@@ -158,7 +165,7 @@ def tune(rowptr, col, val, n_cols: int, dtype: torch.dtype = torch.float32, reps
             continue                      # configuration not valid for this matrix
         us = _time(lambda: M.spmv(x, out=y, **kw), reps, flush)
         results.append(dict(c, us=us))
-        M._long = None
+        M._long = M._tiles = None
     best = min(results, key=lambda r: r["us"])
     if use_cache:
         cache = _load_cache()

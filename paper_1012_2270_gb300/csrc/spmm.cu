@@ -11,36 +11,13 @@
 // are spread over the whole warp and the KC partial sums are combined with
 // shuffles.
 #include "common.cuh"
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
+#include "vtraits.cuh"
 #include <climits>
 
 namespace rgcsr {
 namespace {
 
 constexpr int kThreads = 256;
-
-template <typename V> struct SV;
-template <> struct SV<double> {
-    using A = double;
-    static constexpr bool scaled = false;
-    static __device__ __forceinline__ double ld(const double *p) { return __ldcs(p); }
-};
-template <> struct SV<float> {
-    using A = float;
-    static constexpr bool scaled = false;
-    static __device__ __forceinline__ float ld(const float *p) { return __ldcs(p); }
-};
-template <> struct SV<__nv_bfloat16> {
-    using A = float;
-    static constexpr bool scaled = true;
-    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldcs(p)); }
-};
-template <> struct SV<__half> {
-    using A = float;
-    static constexpr bool scaled = true;
-    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldcs(p)); }
-};
 
 // acc[0..KC) += v * X[c, 0..KC), vectorised when VEC (16-byte aligned rows).
 template <typename A, int KC, bool VEC>
@@ -90,9 +67,9 @@ template <typename V, int KC, bool VEC>
 __global__ void __launch_bounds__(kThreads)
 rgcsr_spmm_kernel(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *__restrict__ col,
                   const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
-                  const float *__restrict__ scale, const typename SV<V>::A *__restrict__ X, int64_t ldx,
-                  typename SV<V>::A *__restrict__ Y, int64_t ldy, const int32_t *__restrict__ perm) {
-    using A = typename SV<V>::A;
+                  const float *__restrict__ scale, const typename VT<V>::A *__restrict__ X, int64_t ldx,
+                  typename VT<V>::A *__restrict__ Y, int64_t ldy, const int32_t *__restrict__ perm) {
+    using A = typename VT<V>::A;
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = row < n;
@@ -122,7 +99,7 @@ rgcsr_spmm_kernel(int64_t n, int32_t G, const V *__restrict__ val, const int32_t
         for (int u = 0; u < U; ++u) {
             if (j + u < jend) {
                 const int64_t p = ptr + (int64_t)(j + u) * stride;
-                v[u] = SV<V>::ld(val + p);
+                v[u] = VT<V>::ld(val + p);
                 c[u] = ld_stream(col + p);
             }
         }
@@ -143,7 +120,7 @@ rgcsr_spmm_kernel(int64_t n, int32_t G, const V *__restrict__ val, const int32_t
         for (int q = 0; q < KC; ++q) part[q] = 0;
         for (int j = j0 + lane; j < Lr; j += 32) {
             const int64_t p = pr + (int64_t)j * sr;
-            axpy_row<A, KC, VEC>(part, SV<V>::ld(val + p), X + (int64_t)ld_stream(col + p) * ldx);
+            axpy_row<A, KC, VEC>(part, VT<V>::ld(val + p), X + (int64_t)ld_stream(col + p) * ldx);
         }
 #pragma unroll
         for (int q = 0; q < KC; ++q) {
@@ -154,16 +131,16 @@ rgcsr_spmm_kernel(int64_t n, int32_t G, const V *__restrict__ val, const int32_t
     if (valid) {
         A *yr = Y + out_row(perm, row) * ldy;
         A s = 1;
-        if constexpr (SV<V>::scaled) s = __ldg(scale + row);
+        if constexpr (VT<V>::scaled) s = __ldg(scale + row);
 #pragma unroll
-        for (int q = 0; q < KC; ++q) yr[q] = SV<V>::scaled ? acc[q] * s : acc[q];
+        for (int q = 0; q < KC; ++q) yr[q] = VT<V>::scaled ? acc[q] * s : acc[q];
     }
 }
 
 template <typename V, int KC>
-int launch_chunk(const rgcsr_matrix *M, const typename SV<V>::A *X, int64_t ldx,
-                 typename SV<V>::A *Y, int64_t ldy, cudaStream_t s) {
-    using A = typename SV<V>::A;
+int launch_chunk(const rgcsr_matrix *M, const typename VT<V>::A *X, int64_t ldx,
+                 typename VT<V>::A *Y, int64_t ldy, cudaStream_t s) {
+    using A = typename VT<V>::A;
     const int64_t blocks = ceil_div(M->n_rows, kThreads);
     if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
     const bool vec = ((uintptr_t)X % 16 == 0) && ((ldx * (int64_t)sizeof(A)) % 16 == 0);
@@ -182,9 +159,9 @@ int launch_chunk(const rgcsr_matrix *M, const typename SV<V>::A *X, int64_t ldx,
 // Columns in chunks of 32, 16, 8, 4, 2, 1 (FP64: at most 16) -- each chunk
 // one launch that streams the matrix once.
 template <typename V>
-int spmm_t(const rgcsr_matrix *M, int k, const typename SV<V>::A *X, int64_t ldx,
-           typename SV<V>::A *Y, int64_t ldy, cudaStream_t s) {
-    constexpr int kmax = sizeof(typename SV<V>::A) == 8 ? 16 : 32;
+int spmm_t(const rgcsr_matrix *M, int k, const typename VT<V>::A *X, int64_t ldx,
+           typename VT<V>::A *Y, int64_t ldy, cudaStream_t s) {
+    constexpr int kmax = sizeof(typename VT<V>::A) == 8 ? 16 : 32;
     int c0 = 0;
     while (c0 < k) {
         const int left = k - c0;

@@ -22,8 +22,7 @@
 // through the read-only path so it stays cached for reuse (the paper's
 // texture binding of x, Sec. 3.4 and Sec. 4.3).
 #include "common.cuh"
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
+#include "vtraits.cuh"
 #include <climits>
 #include <type_traits>
 
@@ -33,39 +32,10 @@ namespace {
 constexpr int kDefaultThreads = 256;
 constexpr int kUnroll = 8;          // slots in flight per thread
 
-// Storage type V -> arithmetic type A, streaming load, per-row scale flag.
-template <typename V> struct VT;
-template <> struct VT<double> {
-    using A = double;
-    static constexpr bool scaled = false;
-    static __device__ __forceinline__ double ld(const double *p) { return __ldcs(p); }
-};
-template <> struct VT<float> {
-    using A = float;
-    static constexpr bool scaled = false;
-    static __device__ __forceinline__ float ld(const float *p) { return __ldcs(p); }
-};
-template <> struct VT<__nv_bfloat16> {
-    using A = float;
-    static constexpr bool scaled = true;
-    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldcs(p)); }
-};
-template <> struct VT<__half> {
-    using A = float;
-    static constexpr bool scaled = true;
-    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldcs(p)); }
-};
-
 template <typename A, bool NC>
 __device__ __forceinline__ A gather(const A *x, int c) {
     if constexpr (NC) return __ldg(x + c);
     else return x[c];
-}
-
-template <typename V>
-__device__ __forceinline__ typename VT<V>::A finish(typename VT<V>::A acc, const float *scale, int64_t row) {
-    if constexpr (VT<V>::scaled) return acc * __ldg(scale + row);
-    else return acc;
 }
 
 template <typename T, bool NC>
@@ -549,7 +519,8 @@ RGCSR_API int rgcsr_spmv_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows 
 
 RGCSR_API int rgcsr_spmv_host(const rgcsr_matrix *M, const void *x_host, void *y_host,
                               void *x_dev, void *y_dev, const rgcsr_launch *launch,
-                              const rgcsr_long_rows *long_rows, rgcsr_stream_t stream) {
+                              const rgcsr_long_rows *long_rows, const rgcsr_tiles *tiles,
+                              rgcsr_stream_t stream) {
     int st = check_matrix(M);
     if (st != RGCSR_OK) return st;
     if (M->n_rows == 0) return RGCSR_OK;
@@ -557,8 +528,9 @@ RGCSR_API int rgcsr_spmv_host(const rgcsr_matrix *M, const void *x_host, void *y
     const size_t xb = M->value_type == RGCSR_F64 ? 8 : 4;
     cudaStream_t s = (cudaStream_t)stream;
     RGCSR_CUDA_TRY(cudaMemcpyAsync(x_dev, x_host, (size_t)M->n_cols * xb, cudaMemcpyHostToDevice, s));
-    st = long_rows ? rgcsr_spmv_long_rows(M, long_rows, x_dev, y_dev, stream)
-                   : rgcsr_spmv_ex(M, x_dev, y_dev, launch, stream);
+    st = tiles       ? rgcsr_spmv_tiles(M, tiles, x_dev, y_dev, stream)
+         : long_rows ? rgcsr_spmv_long_rows(M, long_rows, x_dev, y_dev, stream)
+                     : rgcsr_spmv_ex(M, x_dev, y_dev, launch, stream);
     if (st != RGCSR_OK) return st;
     RGCSR_CUDA_TRY(cudaMemcpyAsync(y_host, y_dev, (size_t)M->n_rows * xb, cudaMemcpyDeviceToHost, s));
     return RGCSR_OK;

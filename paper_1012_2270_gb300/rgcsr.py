@@ -69,6 +69,7 @@ class RgCSRMatrix:
         self.slot_to_csr = None
         self.row_perm = None
         self._long = None          # long-row segment schedule, if enabled
+        self._tiles = None         # group-tile schedule, if enabled
 
     # -- construction ------------------------------------------------------
     @classmethod
@@ -148,6 +149,45 @@ class RgCSRMatrix:
         self._long = (S, bufs)
         return self
 
+    def tile_groups(self, tile: int = 64, variant: int = 0, stream=None) -> "RgCSRMatrix":
+        """Makes spmv() use the group-tile schedule (rgcsr_spmv_tiles): one
+        warp per tile of at most `tile` slot-rows of a group, long groups cut
+        into several tiles.  Needs group_size <= 32."""
+        T = L.Tiles()
+        T.tile = int(tile)
+        T.variant = int(variant)
+        dev = self.group_ptr.device
+        ng = self.s.n_groups
+        i64 = dict(dtype=torch.int64, device=dev)
+        bufs = dict(first_extra=torch.empty(ng + 1, **i64), part_base=torch.empty(ng + 1, **i64))
+        T.first_extra, T.part_base = _ptr(bufs["first_extra"]), _ptr(bufs["part_base"])
+        nb = L.lib().rgcsr_tiles_workspace_bytes(ng)
+        ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=dev)
+        st = _stream_ptr(stream)
+        L.call("rgcsr_tiles_plan", ctypes.byref(self.s), ctypes.byref(T), _ptr(ws), nb, st)
+        bufs["extra_group"] = torch.empty(T.n_extra, dtype=torch.int32, device=dev)
+        bufs["arrivals"] = torch.empty(ng if T.n_extra else 0, dtype=torch.int32, device=dev)
+        bufs["partials"] = torch.empty(T.n_partials * 32, dtype=self.x_dtype, device=dev)
+        for k in ("extra_group", "arrivals", "partials"):
+            setattr(T, k, _ptr(bufs[k]))
+        L.call("rgcsr_tiles_build", ctypes.byref(self.s), ctypes.byref(T), st)
+        self._tiles = (T, bufs)
+        return self
+
+    def copy_schedule(self, other: "RgCSRMatrix") -> "RgCSRMatrix":
+        """Builds the same launch schedule (tiles or long-row segments) as
+        `other`, a matrix with the same layout (e.g. its quantised copy)."""
+        self._long = self._tiles = None
+        if other._tiles is not None:
+            self.tile_groups(other._tiles[0].tile, other._tiles[0].variant)
+        elif other._long is not None:
+            self.split_long_rows(other._long[0].threshold, other._long[0].segment)
+        return self
+
+    @property
+    def n_extra_tiles(self) -> int:
+        return 0 if self._tiles is None else self._tiles[0].n_extra
+
     @property
     def n_long_segments(self) -> int:
         return 0 if self._long is None else self._long[0].n_segments
@@ -214,7 +254,10 @@ class RgCSRMatrix:
         y = out if out is not None else torch.empty(self.s.n_rows, dtype=self.x_dtype, device=x.device)
         default = (kernel == L.KERNEL_AUTO and x_load == L.XLOAD_NC and not block_threads
                    and not split_weight and not variant)
-        if default and self._long is not None:
+        if default and self._tiles is not None:
+            L.call("rgcsr_spmv_tiles", ctypes.byref(self.s), ctypes.byref(self._tiles[0]), _ptr(x), _ptr(y),
+                   _stream_ptr(stream))
+        elif default and self._long is not None:
             L.call("rgcsr_spmv_long_rows", ctypes.byref(self.s), ctypes.byref(self._long[0]), _ptr(x), _ptr(y),
                    _stream_ptr(stream))
         elif default:
@@ -240,13 +283,17 @@ class RgCSRMatrix:
     def spmv_host(self, x_host: torch.Tensor, y_host: torch.Tensor, x_dev: torch.Tensor,
                   y_dev: torch.Tensor, kernel: int = L.KERNEL_AUTO, variant: int = 0, stream=None) -> None:
         """Host-to-host SpMV through caller-provided device staging buffers
-        (the long-row schedule if enabled, else the given kernel)."""
-        if self._long is not None and kernel == L.KERNEL_AUTO and not variant:
-            launch, lr = None, ctypes.byref(self._long[0])
+        (the tile or long-row schedule if enabled, else the given kernel)."""
+        launch = lr = tl = None
+        default = kernel == L.KERNEL_AUTO and not variant
+        if default and self._tiles is not None:
+            tl = ctypes.byref(self._tiles[0])
+        elif default and self._long is not None:
+            lr = ctypes.byref(self._long[0])
         else:
-            launch, lr = ctypes.byref(L.Launch(kernel, 0, L.XLOAD_NC, 0, variant)), None
+            launch = ctypes.byref(L.Launch(kernel, 0, L.XLOAD_NC, 0, variant))
         L.call("rgcsr_spmv_host", ctypes.byref(self.s), _ptr(x_host), _ptr(y_host),
-               _ptr(x_dev), _ptr(y_dev), launch, lr, _stream_ptr(stream))
+               _ptr(x_dev), _ptr(y_dev), launch, lr, tl, _stream_ptr(stream))
 
     def __matmul__(self, x):
         return self.spmv(x)
