@@ -533,7 +533,10 @@ def measure_forms(mats, cases, detail, dev, stream):
         del absA
         for fmt in ("bf16", "f16"):
             Q = c64["M"].quantized(fmt)
-            Q.copy_schedule(c64["M"])                 # same layout, same launch schedule
+            # Q has c64's layout; take the FP32 case's schedule when the two
+            # layouts agree (Q computes in float), else c64's
+            same = all(c32["config"].get(k) == c64["config"].get(k) for k in ("group_size", "row_order"))
+            Q.copy_schedule(c32["M"] if same else c64["M"])
             quant.append((name, fmt, Q, c32["x"], torch.empty(A.n_rows, dtype=torch.float32, device=dev), A))
     us = time_rotating([lambda q=q: q[2].spmv(q[3], out=q[4]) for q in quant], 30, stream)
     forms["quantized"] = {}
@@ -547,23 +550,31 @@ def measure_forms(mats, cases, detail, dev, stream):
     del quant, ref
 
     # -- multi-RHS SpMM on (b) ------------------------------------------------
-    # natural row order at the byte model's group size: the SpMM kernel is
-    # thread-per-row, so it does not use the descending-order tiles
+    # natural row order, G = 1 with the long-row schedule (T = 32, 256-slot
+    # segments): the lanes-per-row kernels; the thread-per-row kernel at the
+    # byte model's group size beside it
     b = [m for m in mats if m[0] == "b"][0][1]
     Mb = RgCSRMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32,
-                              group_size=model_group_size(b.rowptr, 4))
-    forms["spmm_b_f32"] = {"group_size": Mb.group_size}
+                              group_size=1).split_long_rows(32, 256)
+    Gm = model_group_size(b.rowptr, 4)
+    Mt = RgCSRMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32,
+                              group_size=Gm)
+    forms["spmm_b_f32"] = {"config": "G=1, long-row schedule T=32 S=256, lanes-per-row kernels",
+                           "thread_per_row_group_size": Gm}
     for k in (1, 4, 8, 16, 32):
         X = torch.rand(b.n_cols, k, device=dev)
         Y = torch.empty(b.n_rows, k, device=dev)
         t = time_flushed(lambda: Mb.spmm(X, out=Y), 10, flush, stream)
-        nb = roofline.spmm_bytes(b.n_rows, b.n_cols, b.nnz, Mb.s.n_groups, 4, k)
-        forms["spmm_b_f32"][f"k{k}"] = {"gbs": nb / t / 1e3, "gflops": 2 * b.nnz * k / t / 1e3, "us": t}
+        t_old = time_flushed(lambda: Mt.spmm(X, out=Y), 5, flush, stream)
+        nb = roofline.spmm_bytes(b.n_rows, b.n_cols, b.nnz, (b.n_rows + GROUP - 1) // GROUP, 4, k)
+        forms["spmm_b_f32"][f"k{k}"] = {"gbs": nb / t / 1e3, "gflops": 2 * b.nnz * k / t / 1e3, "us": t,
+                                        "thread_per_row_us": t_old}
         del X, Y
+    del Mb, Mt
 
     # -- backward of Y = A X on (b), batch of 8 right-hand sides ---------------
-    G = model_group_size(b.rowptr, 4)
-    op = SparseOperator(b.rowptr, b.col, b.n_cols, dtype=torch.float32, group_size=G)
+    G = 1
+    op = SparseOperator(b.rowptr, b.col, b.n_cols, dtype=torch.float32, group_size=G, long_rows=(32, 256))
     vals = torch.from_numpy(b.val.astype(np.float32)).to(dev).requires_grad_(True)
     X = torch.rand(b.n_cols, 8, device=dev, requires_grad=True)
 

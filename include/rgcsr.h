@@ -282,6 +282,23 @@ int rgcsr_spmv_host(const rgcsr_matrix *M, const void *x_host, void *y_host,
 int rgcsr_spmm(const rgcsr_matrix *M, int32_t k, const void *X, int64_t ldx, void *Y,
                int64_t ldy, rgcsr_stream_t stream);
 
+/* Y = A X with a few lanes per row, for matrices whose rows vary in length.
+ * A sub-warp of S lanes owns a row; lane q holds 4 consecutive columns of
+ * its result (chunks of 32, 16, 8, 4 columns use S = 8, 4, 2, 1, then single
+ * columns), so one non-zero costs one contiguous 16*S-byte read of X.  With
+ * long_rows (a schedule built by rgcsr_long_rows_plan/build for M; NULL =
+ * none) the slots >= threshold of longer rows go to per-segment partial sums
+ * that a last pass adds in order (deterministic).  partials: device scratch
+ * of partials_count >= n_segments * min(k, 32) elements (double for F64
+ * storage, float otherwise); unused without segments.  X, Y, ldx, ldy and
+ * element types as for rgcsr_spmm; 16-byte aligned X and Y with ldx, ldy
+ * multiples of 16 bytes enable vector loads.  k = 1 with ldx = ldy = 1 runs
+ * the SpMV (rgcsr_spmv_long_rows, or rgcsr_spmv without a schedule).  Async.
+ * RGCSR_ERR_WORKSPACE if partials is too small. */
+int rgcsr_spmm_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *long_rows, int32_t k,
+                         const void *X, int64_t ldx, void *Y, int64_t ldy, void *partials,
+                         int64_t partials_count, rgcsr_stream_t stream);
+
 /* ----------------------------------------------------------------------- */
 /* Batched SpMV: many RgCSR matrices of uneven sizes in one launch (not in  */
 /* the paper).  The members' arrays are concatenated; member m uses         */

@@ -25,7 +25,9 @@ class SparseOperator:
     """A fixed CSR pattern (``rowptr``, ``col``) of shape [n_rows, n_cols]."""
 
     def __init__(self, rowptr, col, n_cols: int, dtype: torch.dtype = torch.float32,
-                 group_size: int = 32, device="cuda"):
+                 group_size: int = 32, long_rows: tuple | None = None, device="cuda"):
+        """long_rows = (threshold, segment): the long-row schedule for A and
+        A^T (their SpMV and the lanes-per-row SpMM), for uneven rows."""
         self.rowptr = _dev(rowptr, torch.int64, device)
         self.col = _dev(col, torch.int32, device)
         self.n_rows = self.rowptr.numel() - 1
@@ -53,6 +55,9 @@ class SparseOperator:
                _ptr(self.at_src), st)
         self.row_index = torch.empty(self.nnz, dtype=torch.int32, device=device)
         L.call("rgcsr_csr_row_index", ctypes.byref(csr), _ptr(self.row_index), st)
+        if long_rows is not None:
+            self.A.split_long_rows(*long_rows)
+            self.AT.split_long_rows(*long_rows)
 
     def set_values(self, values: torch.Tensor) -> None:
         """Loads CSR-ordered values into the RgCSR matrices of A and A^T."""

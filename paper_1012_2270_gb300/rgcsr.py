@@ -268,16 +268,34 @@ class RgCSRMatrix:
                    _stream_ptr(stream))
         return y
 
-    def spmm(self, X: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-        """Y = A X for X of shape [n_cols, k] with unit column stride."""
+    def spmm(self, X: torch.Tensor, out: torch.Tensor | None = None, rows: bool | None = None,
+             stream=None) -> torch.Tensor:
+        """Y = A X for X of shape [n_cols, k] with unit column stride.
+
+        rows: use the lanes-per-row kernels (rgcsr_spmm_long_rows), with the
+        long-row schedule if one was built; default: when a schedule exists."""
         if X.dim() != 2 or X.shape[0] != self.s.n_cols or X.dtype != self.x_dtype or X.stride(1) != 1:
             raise ValueError(f"X must be [{self.s.n_cols}, k] {self.x_dtype} with unit column stride")
         k = X.shape[1]
         Y = out if out is not None else torch.empty(self.s.n_rows, k, dtype=self.x_dtype, device=X.device)
         if Y.shape != (self.s.n_rows, k) or Y.stride(1) != 1:
             raise ValueError("out must be [n_rows, k] with unit column stride")
-        L.call("rgcsr_spmm", ctypes.byref(self.s), k, _ptr(X), max(X.stride(0), k), _ptr(Y),
-               max(Y.stride(0), k), _stream_ptr(stream))
+        ldx, ldy = max(X.stride(0), k), max(Y.stride(0), k)
+        if rows is None:
+            rows = self._long is not None
+        if not rows:
+            L.call("rgcsr_spmm", ctypes.byref(self.s), k, _ptr(X), ldx, _ptr(Y), ldy, _stream_ptr(stream))
+            return Y
+        lr, part = None, None
+        if self._long is not None:
+            lr = ctypes.byref(self._long[0])
+            need = self._long[0].n_segments * min(k, 32)
+            bufs = self._long[1]
+            if bufs.get("spmm_partials") is None or bufs["spmm_partials"].numel() < need:
+                bufs["spmm_partials"] = torch.empty(max(need, 1), dtype=self.x_dtype, device=X.device)
+            part = bufs["spmm_partials"]
+        L.call("rgcsr_spmm_long_rows", ctypes.byref(self.s), lr, k, _ptr(X), ldx, _ptr(Y), ldy, _ptr(part),
+               0 if part is None else part.numel(), _stream_ptr(stream))
         return Y
 
     def spmv_host(self, x_host: torch.Tensor, y_host: torch.Tensor, x_dev: torch.Tensor,

@@ -299,3 +299,14 @@ def test_long_row_segments_full_size_b(dtype, G):
     A = synth.workload_b()
     M = to_gpu_matrix(A, dtype, G, slot_map=False).split_long_rows(threshold=64, segment=256)
     check_spmv(M, A, dtype, synth.uniform_vector(A.n_cols, seed=0))
+
+
+def test_unknown_kernel_variants_rejected():
+    A = ragged(300, 200, seed=2)
+    M = to_gpu_matrix(A, "f32", 32)
+    x = torch.zeros(A.n_cols, dtype=torch.float32, device="cuda")
+    for kw in (dict(kernel=L.KERNEL_LEAN, variant=1), dict(kernel=L.KERNEL_TMA, variant=4),
+               dict(kernel=L.KERNEL_LEAN, variant=-1)):
+        with pytest.raises(L.RgCSRError) as e:
+            M.spmv(x, **kw)
+        assert e.value.status == L.RGCSR_ERR_INVALID_ARG

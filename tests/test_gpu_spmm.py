@@ -80,3 +80,78 @@ def test_spmm_full_size_b(k):
     M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(np.float32), A.n_cols, dtype=torch.float32)
     X = synth.uniform_matrix(A.n_cols, k, seed=k)
     check(A, M, "f32", X, TAU["f32"])
+
+
+# ---------------------------------------------------------------------------
+# lanes-per-row kernels (rgcsr_spmm_long_rows), with and without the
+# long-row segment schedule
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("k", [1, 3, 4, 5, 8, 16, 17, 32, 33, 40])
+@pytest.mark.parametrize("G,sched", [(1, (16, 64)), (32, (0, 7)), (3, None)])
+def test_spmm_rows_ragged(dtype, k, G, sched):
+    rng = np.random.default_rng(k + G)
+    Ls = rng.integers(0, 30, 1500)
+    Ls[[3, 700, 701]] = [2000, 900, 35]
+    A = synth.random_csr(1500, 2500, Ls, seed=k)
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dtype]), A.n_cols, group_size=G, dtype=TT[dtype])
+    if sched:
+        M.split_long_rows(*sched)
+    Xd = torch.from_numpy(synth.uniform_matrix(A.n_cols, k, seed=k).astype(NP[dtype])).cuda()
+    Y = M.spmm(Xd, rows=True).cpu().numpy()
+    Y_ref, aY = oracle.csr_spmm(A.rowptr, A.col, rounded_values(A.val, dtype), Xd.cpu().numpy().astype(np.float64))
+    assert_within_bound(Y.ravel(), Y_ref.ravel(), aY.ravel(), TAU[dtype], f"rows k={k} G={G} {sched}")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_spmm_rows_strided_and_reordered(dtype):
+    rng = np.random.default_rng(4)
+    A = synth.random_csr(901, 700, rng.integers(0, 40, 901), seed=4)
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dtype]), A.n_cols, group_size=32,
+                             dtype=TT[dtype], row_order="descending").split_long_rows(8, 16)
+    wide = synth.uniform_matrix(A.n_cols, 19, seed=2)
+    Xd = torch.from_numpy(wide.astype(NP[dtype])).cuda()[:, 3:16]        # k = 13, unaligned rows
+    Yw = torch.full((A.n_rows, 15), 5.0, dtype=TT[dtype], device="cuda")
+    M.spmm(Xd, out=Yw[:, 1:14])
+    assert (Yw[:, 0] == 5.0).all() and (Yw[:, 14] == 5.0).all()
+    Y_ref, aY = oracle.csr_spmm(A.rowptr, A.col, rounded_values(A.val, dtype), wide[:, 3:16].astype(NP[dtype]).astype(np.float64))
+    assert_within_bound(Yw[:, 1:14].cpu().numpy().ravel(), Y_ref.ravel(), aY.ravel(), TAU[dtype], "rows strided")
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_spmm_rows_quantized(fmt):
+    A = synth.power_law(20_000, seed=8)
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val, A.n_cols, group_size=1, dtype=torch.float64)
+    Q = M.quantized(fmt).split_long_rows(32, 128)
+    code = oracle.BF16 if fmt == "bf16" else oracle.F16
+    q, s = oracle.quantize_rows(A.rowptr, A.val, code)
+    deq = oracle.dequantized_values(A.rowptr, q, s, code)
+    X = synth.uniform_matrix(A.n_cols, 12, seed=3)
+    Y = Q.spmm(torch.from_numpy(X.astype(np.float32)).cuda()).cpu().numpy()
+    Y_ref, aY = oracle.csr_spmm(A.rowptr, A.col, deq, X.astype(np.float32).astype(np.float64))
+    assert_within_bound(Y.ravel(), Y_ref.ravel(), aY.ravel(), 2e-6, f"rows {fmt}")
+
+
+def test_spmm_rows_partials_too_small():
+    import ctypes
+    from paper_1012_2270_gb300 import _lib as L
+    from paper_1012_2270_gb300.rgcsr import _ptr, _stream_ptr
+    A = synth.power_law(5000, seed=1)
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(np.float32), A.n_cols, group_size=1,
+                             dtype=torch.float32).split_long_rows(16, 64)
+    assert M.n_long_segments > 0
+    X = torch.zeros(A.n_cols, 8, device="cuda")
+    Y = torch.empty(A.n_rows, 8, device="cuda")
+    part = torch.empty(M.n_long_segments * 8 - 1, device="cuda")
+    st = L.lib().rgcsr_spmm_long_rows(ctypes.byref(M.s), ctypes.byref(M._long[0]), 8, _ptr(X), 8, _ptr(Y), 8,
+                                      _ptr(part), part.numel(), _stream_ptr())
+    assert st == L.RGCSR_ERR_WORKSPACE
+
+
+@pytest.mark.parametrize("k", [4, 32])
+def test_spmm_rows_full_size_b(k):
+    A = synth.workload_b()
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(np.float32), A.n_cols, group_size=1,
+                             dtype=torch.float32).split_long_rows(32, 256)
+    X = synth.uniform_matrix(A.n_cols, k, seed=k)
+    check(A, M, "f32", X, TAU["f32"])
