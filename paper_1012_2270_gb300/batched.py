@@ -5,6 +5,13 @@ convert kernels directly into slices of shared concatenated arrays, builds
 the per-member descriptors and the 32-row task list (rgcsr_batch_tasks) and
 keeps everything on the GPU.  ``spmv`` is one rgcsr_spmv_batched launch;
 ``capture`` records it into a CUDA graph for replay.
+
+``BlockDiagonalBatch`` is the other way to batch: the members form one
+block-diagonal matrix diag(A_1, ..., A_m), so one SpMV of it with the
+concatenated x computes every member's product.  Its rows can be put in
+descending length order across the whole batch and its groups cut into
+tiles (rgcsr_spmv_tiles), so uneven members and uneven rows share one
+balanced launch.
 """
 from __future__ import annotations
 
@@ -110,17 +117,69 @@ class BatchedRgCSR:
 
     def capture(self, x_cat: torch.Tensor, y_cat: torch.Tensor, repeats: int = 1) -> torch.cuda.CUDAGraph:
         """A CUDA graph of `repeats` batched SpMVs on the given buffers."""
-        g = torch.cuda.CUDAGraph()
-        side = torch.cuda.Stream()
-        side.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(side):
-            self.spmv(x_cat, y_cat)                    # warm-up outside the capture
-            side.synchronize()
-            with torch.cuda.graph(g, stream=side):
-                for _ in range(repeats):
-                    self.spmv(x_cat, y_cat, stream=side)
-        torch.cuda.current_stream().wait_stream(side)
-        return g
+        return _capture(self.spmv, x_cat, y_cat, repeats)
+
+    def member_slices(self, i: int):
+        return (slice(int(self.x_off[i]), int(self.x_off[i + 1])),
+                slice(int(self.row_off[i]), int(self.row_off[i + 1])))
+
+
+def _capture(spmv, x_cat, y_cat, repeats):
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        spmv(x_cat, y_cat)                             # warm-up outside the capture
+        side.synchronize()
+        with torch.cuda.graph(g, stream=side):
+            for _ in range(repeats):
+                spmv(x_cat, y_cat, stream=side)
+    torch.cuda.current_stream().wait_stream(side)
+    return g
+
+
+class BlockDiagonalBatch:
+    """The batch as one RgCSR matrix diag(A_1, ..., A_m): member i's rows
+    follow member i-1's and its column indices are shifted by the column
+    counts of the members before it."""
+
+    @classmethod
+    def from_csr_list(cls, mats, dtype: torch.dtype = torch.float32, group_size: int = 32,
+                      row_order="descending", tile: int | None = 64, variant: int = 0,
+                      device="cuda") -> "BlockDiagonalBatch":
+        """``mats``: objects with rowptr, col, val, n_rows, n_cols (host
+        numpy).  ``row_order`` and ``tile`` as in RgCSRMatrix.from_csr and
+        RgCSRMatrix.tile_groups (tile=None: no tile schedule)."""
+        from .rgcsr import RgCSRMatrix
+        self = cls()
+        n_rows = np.array([A.n_rows for A in mats], np.int64)
+        n_cols = np.array([A.n_cols for A in mats], np.int64)
+        nnz = np.array([A.nnz for A in mats], np.int64)
+        self.row_off = np.concatenate([[0], np.cumsum(n_rows)])
+        self.x_off = np.concatenate([[0], np.cumsum(n_cols)])
+        nnz_off = np.concatenate([[0], np.cumsum(nnz)])
+        self.n_rows_total, self.n_cols_total = int(self.row_off[-1]), int(self.x_off[-1])
+        if self.n_cols_total > np.iinfo(np.int32).max:
+            raise ValueError("the batch has more columns than int32 indices address")
+        rowptr = np.concatenate([np.asarray(A.rowptr[:-1], np.int64) + nnz_off[i] for i, A in enumerate(mats)]
+                                + [np.array([nnz_off[-1]], np.int64)])
+        col = np.concatenate([np.asarray(A.col, np.int64) + self.x_off[i] for i, A in enumerate(mats)]).astype(np.int32)
+        npdt = np.float64 if dtype == torch.float64 else np.float32
+        val = np.concatenate([np.asarray(A.val).astype(npdt) for A in mats])
+        self.M = RgCSRMatrix.from_csr(rowptr, col, val, self.n_cols_total, group_size=group_size, dtype=dtype,
+                                      row_order=row_order, device=device)
+        del rowptr, col, val
+        if tile:
+            self.M.tile_groups(tile, variant)
+        self.n_matrices, self.nnz, self.dtype = len(mats), int(nnz_off[-1]), dtype
+        return self
+
+    def spmv(self, x_cat: torch.Tensor, y_cat: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """All members' products; x_cat and y_cat are the concatenated vectors."""
+        return self.M.spmv(x_cat, out=y_cat, stream=stream)
+
+    def capture(self, x_cat: torch.Tensor, y_cat: torch.Tensor, repeats: int = 1) -> torch.cuda.CUDAGraph:
+        return _capture(self.spmv, x_cat, y_cat, repeats)
 
     def member_slices(self, i: int):
         return (slice(int(self.x_off[i]), int(self.x_off[i + 1])),

@@ -10,7 +10,7 @@ import oracle
 from helpers import TAU, assert_within_bound, rounded_values
 from paper_1012_2270_gb300 import synth
 from paper_1012_2270_gb300 import autotune
-from paper_1012_2270_gb300.batched import BatchedRgCSR
+from paper_1012_2270_gb300.batched import BatchedRgCSR, BlockDiagonalBatch
 from paper_1012_2270_gb300.rgcsr import RgCSRMatrix
 
 pytestmark = pytest.mark.gpu
@@ -84,3 +84,20 @@ def test_autotune_returns_a_correct_configuration(tmp_path, monkeypatch):
     assert again == best
     hb = autotune.tune_hyb_width(A.rowptr, A.col, A.val.astype(np.float32), A.n_cols, reps=3)
     assert hb["ell_width"] >= 0
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("order,tile", [("descending", 64), ("descending", 8), (None, 16), (None, None)])
+def test_block_diagonal_batch(dtype, order, tile):
+    mats = small_batch(36)
+    mats.insert(5, synth.random_csr(0, 7, np.zeros(0, np.int64)))          # an empty member
+    Bd = BlockDiagonalBatch.from_csr_list(mats, dtype=TT[dtype], row_order=order, tile=tile)
+    x_cat = torch.from_numpy(synth.uniform_vector(Bd.n_cols_total, seed=6).astype(NP[dtype])).cuda()
+    y_cat = Bd.spmv(x_cat)
+    check_batch(mats, Bd, dtype, x_cat, y_cat)
+    y2 = torch.full_like(y_cat, float("nan"))
+    g = Bd.capture(x_cat, y2, repeats=2)
+    y2.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y2, y_cat)                                           # deterministic, replayable
