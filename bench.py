@@ -659,6 +659,10 @@ def measure_forms(mats, cases, detail, dev, stream):
     forms["jacobi_grad_96_f32"] = res
     del opj
 
+    # -- group-size sweep (the paper's Table 4 on these matrices), x read path
+    # on/off (the texture study of Sec. 4.3) and sliced ELLPACK (Sec. 3.4) --
+    forms.update(measure_tables(mats, flush, stream))
+
     # -- batched: the 512-member uneven batch in one launch vs 512 launches ---
     members = synth.workload_batch(512)
     Bt = BatchedRgCSR.from_csr_list(members, dtype=torch.float32, group_sizes="model")
@@ -703,6 +707,36 @@ def measure_forms(mats, cases, detail, dev, stream):
         "plain_512_launches_us": t_p, "plain_gbs": nb_batch / t_p / 1e3, "speedup_vs_plain": t_p / min(t_b, t_d)}
     del Bt, members
     return forms
+
+
+def measure_tables(mats, flush, stream):
+    """Natural row order, G in {32, 64, 128, 256}, FP32 and FP64:
+    artificial zeros and GB/s of the paper's kernel (one block per group)
+    with x through the read-only path and with plain loads, of the
+    warp-split kernel, and of sliced ELLPACK on the same slabs."""
+    import torch
+    from paper_1012_2270_gb300 import _lib as L
+    from paper_1012_2270_gb300.rgcsr import RgCSRMatrix
+    sweep = {}
+    for name, A, x in mats:
+        for dt in DTYPES:
+            tdt = torch.float32 if dt == "f32" else torch.float64
+            xd = torch.from_numpy(x.astype(NP[dt])).cuda()
+            nb = case_bytes(A, (A.n_rows + GROUP - 1) // GROUP, dt)
+            for G in (32, 64, 128, 256):
+                M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dt]), A.n_cols, group_size=G, dtype=tdt)
+                y = torch.empty(A.n_rows, dtype=tdt, device="cuda")
+                row = {"artificial_zero_pct": M.artificial_zero_percent()}
+                for key, kw in (("paper_readonly_x", dict(kernel=L.KERNEL_PAPER)),
+                                ("paper_plain_x", dict(kernel=L.KERNEL_PAPER, x_load=L.XLOAD_PLAIN)),
+                                ("split", dict(kernel=L.KERNEL_SPLIT)),
+                                ("sliced_ellpack", dict(kernel=L.KERNEL_SELL))):
+                    t = time_flushed(lambda: M.spmv(xd, out=y, **kw), 5, flush, stream)
+                    row[key] = {"us": t, "gbs": nb / t / 1e3, "gflops": 2 * A.nnz / t / 1e3}
+                sweep[f"{name}_{dt}_G{G}"] = row
+                del M, y
+                torch.cuda.empty_cache()
+    return {"group_size_sweep": sweep}
 
 
 def main():

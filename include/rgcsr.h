@@ -110,6 +110,9 @@ typedef struct {
                                     columns and row_lengths and n_rows >= 32       */
 #define RGCSR_KERNEL_LEAN   4    /* one thread per row, no long-row split, sized for
                                     full occupancy (rows of similar lengths)        */
+#define RGCSR_KERNEL_SELL   5    /* comparator, not the method: sliced ELLPACK on the
+                                    same slabs (Sec. 3.4) -- every row runs all K_g
+                                    slots of its group, padding multiplied          */
 #define RGCSR_XLOAD_NC      0    /* x through the read-only (non-coherent) path    */
 #define RGCSR_XLOAD_PLAIN   1    /* x with ordinary global loads                   */
 typedef struct {
@@ -243,7 +246,8 @@ int rgcsr_spmv_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *S, const 
 typedef struct {
     int32_t tile;               /* slot-rows per task, >= 1                   */
     int32_t variant;            /* 0 = default; 1, 2: fewer / more slot-rows
-                                   in flight per lane (tuning)                */
+                                   in flight per lane; 3, 4: software-
+                                   pipelined across a warp's tiles (tuning)   */
     int64_t n_groups;           /* (plan) the matrix's group count            */
     int64_t n_extra;            /* (plan) tasks beyond one per group          */
     int64_t n_split;            /* (plan) groups cut into more than one task  */

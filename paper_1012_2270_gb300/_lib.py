@@ -23,7 +23,7 @@ RGCSR_ERR_BAD_PERM = -8
 
 F64, F32, BF16, F16, I32T, I64T = 0, 1, 2, 3, 4, 5
 
-KERNEL_AUTO, KERNEL_PAPER, KERNEL_SPLIT, KERNEL_TMA, KERNEL_LEAN = 0, 1, 2, 3, 4
+KERNEL_AUTO, KERNEL_PAPER, KERNEL_SPLIT, KERNEL_TMA, KERNEL_LEAN, KERNEL_SELL = 0, 1, 2, 3, 4, 5
 STATUS_TIMEOUT = 1
 XLOAD_NC, XLOAD_PLAIN = 0, 1
 

@@ -13,6 +13,7 @@
 //    group serialises its warp (Sec. 4.4.2, Table 6: trans4 and Raj1).
 //  * rgcsr_spmv_lean: one thread per row, no split, sized for full
 //    occupancy; for matrices whose rows in a warp have similar lengths.
+//  * sliced_ell_spmv: the sliced ELLPACK comparator on the same slabs.
 //
 // Value storage V is double, float, or (reduced storage, not in the paper)
 // bfloat16 / half with a per-row float scale: y_i = s_i * sum_j q_ij x_j
@@ -193,6 +194,47 @@ rgcsr_spmv_lean(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *
     y[out_row(perm, row)] = finish<V>(acc, scale, row);
 }
 
+// Sliced ELLPACK on the same slabs (the related format discussed in
+// Sec. 3.4): one thread per row, but every row of group g runs all
+// K_g = (gp[g+1] - gp[g]) / R_g slots -- no rowLengths -- so the padding is
+// multiplied too (value 0 times x[column 0]).  A comparator, not the method.
+template <typename V>
+__global__ void __launch_bounds__(kDefaultThreads)
+sliced_ell_spmv(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *__restrict__ col,
+                const int64_t *__restrict__ gp, const float *__restrict__ scale,
+                const typename VT<V>::A *__restrict__ x, typename VT<V>::A *__restrict__ y,
+                const int32_t *__restrict__ perm) {
+    using A = typename VT<V>::A;
+    constexpr int U = 4;
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    const int64_t g = row / G;
+    const int64_t first = g * G;
+    const int stride = (int)min((int64_t)G, n - first);
+    const int64_t g0 = __ldg(gp + g);
+    const int64_t K = (__ldg(gp + g + 1) - g0) / stride;
+    const V *vp = val + g0 + (row - first);
+    const int32_t *cp = col + g0 + (row - first);
+    A acc = 0;
+    for (int64_t j = 0; j < K; j += U) {
+        A v[U];
+        int c[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (j + u < K) {
+                v[u] = VT<V>::ld(vp + (int64_t)u * stride);
+                c[u] = ld_stream(cp + (int64_t)u * stride);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (j + u < K) acc = fma(v[u], __ldg(x + c[u]), acc);
+        vp += (int64_t)U * stride;
+        cp += (int64_t)U * stride;
+    }
+    y[out_row(perm, row)] = finish<V>(acc, scale, row);
+}
+
 template <typename V>
 int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V>::A *y,
                 const rgcsr_launch *L, cudaStream_t s) {
@@ -211,6 +253,14 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
         constexpr int min_blocks = (std::is_same<V, float>::value) ? 8 : 6;
         rgcsr_spmv_lean<V, 4, min_blocks><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
             n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
+        return launch_status();
+    }
+    if (kernel == RGCSR_KERNEL_SELL) {
+        const int64_t blocks = ceil_div(n, kDefaultThreads);
+        if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
+        if (L && L->variant != 0) return RGCSR_ERR_INVALID_ARG;
+        sliced_ell_spmv<V><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(n, G, val, M->columns, M->group_ptr,
+                                                                       scale, x, y, M->row_perm);
         return launch_status();
     }
     if (kernel == RGCSR_KERNEL_PAPER) {

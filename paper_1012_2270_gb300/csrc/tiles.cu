@@ -124,6 +124,142 @@ rgcsr_spmv_tiles_kernel(int64_t n, int32_t G, int32_t C, int64_t n_groups, int64
     }
 }
 
+// The same tiles, software-pipelined across a warp's tasks: while the x
+// gathers of one step run, the value/column loads of the next step (the
+// next slot-rows of this tile, or the first ones of the warp's next tile)
+// are already in flight, and the next tile's metadata is fetched one tile
+// ahead.  Results and their summation order are those of the plain kernel.
+template <typename V>
+struct TileMeta {
+    int64_t base, orow, pb;
+    int g, k, R, len, nt;       // group indices fit int32 (checked at plan)
+    float sc;
+};
+
+template <typename V>
+__device__ __forceinline__ void tile_meta(int64_t t, int64_t n, int32_t G, int64_t n_groups, int64_t n_tasks,
+                                          const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
+                                          const float *__restrict__ scale, const int64_t *__restrict__ first_extra,
+                                          const int64_t *__restrict__ part_base,
+                                          const int32_t *__restrict__ extra_group,
+                                          const int32_t *__restrict__ perm, int lane, TileMeta<V> &m) {
+    m.len = 0;
+    m.nt = 1;
+    m.R = 0;
+    m.base = m.orow = m.pb = m.g = m.k = 0;
+    m.sc = 1.0f;
+    if (t >= n_tasks) return;
+    if (t < n_groups) {
+        m.g = (int)t;
+    } else {
+        m.g = __ldg(extra_group + (t - n_groups));
+        m.k = (int)(1 + (t - n_groups) - __ldg(first_extra + m.g));
+    }
+    const int64_t first = (int64_t)m.g * G;
+    m.R = (int)min((int64_t)G, n - first);
+    m.base = __ldg(gp + m.g);
+    if (lane < m.R) {
+        m.len = __ldg(rl + first + lane);
+        m.orow = out_row(perm, first + lane);
+        if (VT<V>::scaled) m.sc = __ldg(scale + first + lane);
+    }
+    if (first_extra) {
+        m.nt = (int)(1 + __ldg(first_extra + m.g + 1) - __ldg(first_extra + m.g));
+        if (m.nt > 1) m.pb = __ldg(part_base + m.g);
+    }
+}
+
+template <typename V, int U>
+__device__ __forceinline__ void tile_loads(const TileMeta<V> &m, int j, int jend, const V *__restrict__ val,
+                                           const int32_t *__restrict__ col, int lane,
+                                           typename VT<V>::A (&v)[U], int (&c)[U]) {
+    const int64_t p0 = m.base + (int64_t)j * m.R + lane;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        v[u] = 0;
+        c[u] = 0;
+        if (j + u < jend) {
+            v[u] = VT<V>::ld(val + p0 + (int64_t)u * m.R);
+            c[u] = ld_stream(col + p0 + (int64_t)u * m.R);
+        }
+    }
+}
+
+template <typename V, int U, int MIN_BLOCKS>
+__global__ void __launch_bounds__(kTileThreads, MIN_BLOCKS)
+rgcsr_spmv_tiles_pipe_kernel(int64_t n, int32_t G, int32_t C, int64_t n_groups, int64_t n_tasks,
+                             const V *__restrict__ val, const int32_t *__restrict__ col,
+                             const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
+                             const float *__restrict__ scale, const int64_t *__restrict__ first_extra,
+                             const int64_t *__restrict__ part_base, const int32_t *__restrict__ extra_group,
+                             int32_t *__restrict__ arrivals, typename VT<V>::A *partials,
+                             const typename VT<V>::A *__restrict__ x, typename VT<V>::A *__restrict__ y,
+                             const int32_t *__restrict__ perm) {
+    using A = typename VT<V>::A;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    TileMeta<V> cur, nxt;
+    tile_meta<V>(t, n, G, n_groups, n_tasks, gp, rl, scale, first_extra, part_base, extra_group, perm, lane, cur);
+    tile_meta<V>(t + warps, n, G, n_groups, n_tasks, gp, rl, scale, first_extra, part_base, extra_group, perm,
+                 lane, nxt);
+    A v[U], vn[U];
+    int c[U], cn[U];
+    {
+        const int j0 = cur.k * C;
+        tile_loads<V, U>(cur, j0, min(cur.len, j0 + C), val, col, lane, v, c);
+    }
+    while (t < n_tasks) {
+        const int j0 = cur.k * C;
+        const int jend = min(cur.len, j0 + C);
+        const int steps = (warp_max_i(jend - j0) + U - 1) / U;      // uniform over the warp
+        const int nj0 = nxt.k * C;
+        const int njend = min(nxt.len, nj0 + C);
+        A acc = 0;
+        for (int st = 0; st < steps; ++st) {
+            const int j = j0 + st * U;
+            if (st + 1 < steps) tile_loads<V, U>(cur, j + U, jend, val, col, lane, vn, cn);
+            else tile_loads<V, U>(nxt, nj0, njend, val, col, lane, vn, cn);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (j + u < jend) acc = fma(v[u], __ldg(x + c[u]), acc);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                v[u] = vn[u];
+                c[u] = cn[u];
+            }
+        }
+        if (steps == 0) tile_loads<V, U>(nxt, nj0, njend, val, col, lane, v, c);
+        const bool active = lane < cur.R;
+        if (cur.nt == 1) {
+            if (active) y[cur.orow] = VT<V>::scaled ? acc * cur.sc : acc;
+        } else {
+            if (active) partials[(cur.pb + cur.k) * 32 + lane] = acc;
+            __threadfence();
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) {
+                __threadfence();
+                last = atomicAdd(arrivals + cur.g, 1) == cur.nt - 1;
+            }
+            last = __shfl_sync(kFull, last, 0);
+            if (last) {
+                __threadfence();
+                if (active) {
+                    A s = 0;
+                    for (int q = 0; q < cur.nt; ++q) s += ld_coherent(partials + (cur.pb + q) * 32 + lane);
+                    y[cur.orow] = VT<V>::scaled ? s * cur.sc : s;
+                }
+                if (lane == 0) arrivals[cur.g] = 0;
+            }
+        }
+        t += warps;
+        cur = nxt;
+        tile_meta<V>(t + warps, n, G, n_groups, n_tasks, gp, rl, scale, first_extra, part_base, extra_group,
+                     perm, lane, nxt);
+    }
+}
+
 // Resident CTAs of `kern` on the whole current device (queried once per
 // device and kernel).
 template <typename K>
@@ -147,17 +283,20 @@ int launch_tiles(const rgcsr_matrix *M, const rgcsr_tiles *T, const typename VT<
     if (VT<V>::scaled && !M->row_scale) return RGCSR_ERR_INVALID_ARG;
     const int64_t n_tasks = M->n_groups + T->n_extra;
     // slot-rows in flight per lane (U) and CTAs per SM by variant:
-    // 0: U = 8 (FP64: 4), 5 CTAs;  1: U = 4 (FP64: 2), 6 CTAs;  2: U = 16 (FP64: 8), 4 CTAs
+    // 0: U = 8 (FP64: 4), 5 CTAs;  1: U = 4 (FP64: 2), 6 CTAs;  2: U = 16 (FP64: 8), 4 CTAs;
+    // 3, 4: software-pipelined, U = 4 (FP64: 2) with 4 CTAs, U = 8 (FP64: 4) with 3 CTAs
     constexpr int U0 = sizeof(A) == 8 ? 4 : 8;
     void (*kern)(int64_t, int32_t, int32_t, int64_t, int64_t, const V *, const int32_t *, const int64_t *,
                  const int32_t *, const float *, const int64_t *, const int64_t *, const int32_t *, int32_t *,
                  A *, const A *, A *, const int32_t *);
-    static int cache[3][64];
+    static int cache[5][64];
     int *cc;
     switch (T->variant) {
         case 0: kern = rgcsr_spmv_tiles_kernel<V, U0, 5>; cc = cache[0]; break;
         case 1: kern = rgcsr_spmv_tiles_kernel<V, U0 / 2, 6>; cc = cache[1]; break;
         case 2: kern = rgcsr_spmv_tiles_kernel<V, 2 * U0, 4>; cc = cache[2]; break;
+        case 3: kern = rgcsr_spmv_tiles_pipe_kernel<V, U0 / 2, 4>; cc = cache[3]; break;
+        case 4: kern = rgcsr_spmv_tiles_pipe_kernel<V, U0, 3>; cc = cache[4]; break;
         default: return RGCSR_ERR_INVALID_ARG;
     }
     int64_t grid = resident_ctas(kern, cc);                                 // persistent

@@ -310,3 +310,26 @@ def test_unknown_kernel_variants_rejected():
         with pytest.raises(L.RgCSRError) as e:
             M.spmv(x, **kw)
         assert e.value.status == L.RGCSR_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("G", [1, 5, 32])
+def test_sliced_ellpack_comparator(dtype, G):
+    # the comparator runs all K_g slots of every row: equal to the oracle's
+    # sliced ELLPACK product, NaN wherever x[0] = NaN meets padding, and
+    # equal to the CSR product when x is finite
+    rng = np.random.default_rng(G)
+    A = synth.random_csr(700, 90, rng.integers(0, 25, 700), seed=G)
+    M = to_gpu_matrix(A, dtype, G)
+    lay = oracle.rgcsr_layout(A.rowptr, A.col, A.val.astype(NP[dtype]), G)
+    x = synth.uniform_vector(A.n_cols, seed=4)
+    check_spmv(M, A, dtype, x, kernel=L.KERNEL_SELL)
+    x[0] = np.nan
+    y = M.spmv(torch.from_numpy(x.astype(NP[dtype])).cuda(), kernel=L.KERNEL_SELL).cpu().numpy()
+    y_sell = oracle.sliced_ell_spmv(lay, rounded_values(x, dtype))
+    assert np.array_equal(np.isnan(y), np.isnan(y_sell))
+    ok = ~np.isnan(y_sell)
+    _, absy = oracle.csr_spmv(A.rowptr, A.col, rounded_values(A.val, dtype), np.nan_to_num(rounded_values(x, dtype)))
+    assert (np.abs(y[ok] - y_sell[ok]) <= TAU[dtype] * absy[ok]).all()
+    if G > 1:
+        assert np.isnan(y_sell).any() and not np.isnan(M.spmv(torch.from_numpy(x.astype(NP[dtype])).cuda()).cpu().numpy()).all()
