@@ -93,7 +93,8 @@ def kernel_name(cfg, M, A, dt):
     """The kernel that a configuration runs (the library's dispatch rules)."""
     t = "float" if dt == "f32" else "double"
     if "tiles" in cfg:
-        return f"rgcsr_spmv_tiles_kernel<{t}>"
+        pipe = len(cfg["tiles"]) > 1 and cfg["tiles"][1] in (3, 4)
+        return f"rgcsr_spmv_tiles{'_pipe' if pipe else ''}_kernel<{t}>"
     if "long_rows" in cfg:
         return f"rgcsr_spmv_split+segments<{t}>"
     k = cfg.get("kernel", 0)
