@@ -76,6 +76,24 @@ def rank_info():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(values, device="cpu"):
+    """Element-wise maximum of per-rank timings over the process group (the
+    job takes as long as its slowest replica); the values themselves when
+    there is no group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_gbs(world, steps, step_bytes, ms):
+    """Every replica streams step_bytes per step: GB/s of the whole job."""
+    return world * steps * step_bytes / (ms * 1e-3) / 1e9
+
+
 def load_cases():
     mats = []
     for name, fn in CASES:
@@ -340,14 +358,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop() if clocks else None
-    ms_total = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total, = max_over_ranks([t_start.elapsed_time(t_end)], dev)
     per_case_ms = [statistics.fmean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(K))
                    for i in range(len(cases))]
-    value = world * K * step_bytes / (ms_total * 1e-3) / 1e9
+    value = whole_job_gbs(world, K, step_bytes, ms_total)
 
     detail = {}
     for c, ms in zip(cases, per_case_ms):
@@ -412,13 +426,10 @@ def run_ours(args):
     ms_e2e = e2e_run(Ke, True)
     ms_e2e_serial = e2e_run(Ke, False)
     barrier()
-    if world > 1:
-        t = torch.tensor([ms_e2e, ms_e2e_serial], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e, ms_e2e_serial = (float(v) for v in t.tolist())
-    e2e = {"value": world * Ke * step_bytes / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
+    ms_e2e, ms_e2e_serial = max_over_ranks([ms_e2e, ms_e2e_serial], dev)
+    e2e = {"value": whole_job_gbs(world, Ke, step_bytes, ms_e2e), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "one_stream_value": world * Ke * step_bytes / (ms_e2e_serial * 1e-3) / 1e9,
+           "one_stream_value": whole_job_gbs(world, Ke, step_bytes, ms_e2e_serial),
            "note": "per step and case: x host->device, SpMV, y device->host through rgcsr_spmv_host (pinned "
                    "buffers, matrix resident); the six cases on three streams so copies overlap SpMVs"}
 
