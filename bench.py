@@ -116,6 +116,8 @@ def kernel_name(cfg, M, A, dt):
     if "long_rows" in cfg:
         return f"rgcsr_spmv_split+segments<{t}>"
     k = cfg.get("kernel", 0)
+    if k == 4 and cfg.get("variant", 0) == 1:
+        return f"rgcsr_spmv_vec<{t}>"
     if k == 0:
         n = A.n_rows
         dense = (M.n_stored * 4 <= M.nnz * 5 and
@@ -314,7 +316,7 @@ def run_ours(args):
             tdt = torch.float32 if dt == "f32" else torch.float64
             vals = A.val.astype(NP[dt])
             # group size, kernel and long-row schedule chosen by timing on this GPU
-            cfg = autotune.tune(A.rowptr, A.col, vals, A.n_cols, dtype=tdt, reps=5,
+            cfg = autotune.tune(A.rowptr, A.col, vals, A.n_cols, dtype=tdt, reps=12,
                                  use_cache=bool(args.tune_cache))
             M, kw = autotune.build(A.rowptr, A.col, vals, A.n_cols, cfg, tdt)
             xd = torch.from_numpy(x.astype(NP[dt])).to(dev)
@@ -390,6 +392,19 @@ def run_ours(args):
             "frac": achieved / peak_hbm, "traffic": measured_traffic(dom, cases), "kernel": dom,
             "peak_source": peak_src,
             "bytes_per_launch": d["bytes"] / d["launches"], "avg_launch_us": 1e3 * d["ms"] / d["launches"]}
+    dom_cases = [(c, ms) for c, ms in zip(cases, per_case_ms) if c["kernel"] == dom]
+    if all(c["name"] == "b" for c, _ in dom_cases):
+        # random columns: every x gather is its own L2 request, and the L1
+        # issues about one request per SM clock (ncu: the L1->crossbar
+        # request path is the busiest unit) -- a second ceiling below HBM
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clk or {}).get("sm_mhz") or 1920.0
+        ceil_us = statistics.fmean(c["nnz"] / (sms * mhz) for c, _ in dom_cases)
+        t_us = 1e3 * statistics.fmean(ms for _, ms in dom_cases)
+        roof["gather_request_ceiling"] = {
+            "requests_per_launch": statistics.fmean(c["nnz"] for c, _ in dom_cases),
+            "model": "one L2 request per non-zero at one request per SM clock",
+            "sms": sms, "sm_mhz": mhz, "ceiling_us": ceil_us, "frac": ceil_us / t_us}
 
     # ---- end to end: host x in, host y out, through rgcsr_spmv_host ----
     host = []

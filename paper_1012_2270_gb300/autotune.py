@@ -80,7 +80,9 @@ def _store_cache(cache: dict) -> None:
 
 
 def _time(fn, reps: int, flush: torch.Tensor) -> float:
-    """Median time in microseconds of fn() with L2 flushed before each call."""
+    """Time in microseconds of fn() with L2 flushed before each call: the
+    mean of the middle half of the samples, which resolves differences
+    finer than the event timer's tick when the samples jitter across it."""
     fn()
     torch.cuda.synchronize()
     ts = []
@@ -92,7 +94,9 @@ def _time(fn, reps: int, flush: torch.Tensor) -> float:
         e1.record()
         e1.synchronize()
         ts.append(1e3 * e0.elapsed_time(e1))
-    return statistics.median(ts)
+    ts.sort()
+    q = len(ts) // 4
+    return statistics.fmean(ts[q:len(ts) - q])
 
 
 def candidates(rowptr, dtype: torch.dtype):
@@ -110,6 +114,8 @@ def candidates(rowptr, dtype: torch.dtype):
     if not irregular:
         cands += [dict(group_size=32, kernel=L.KERNEL_TMA, variant=v) for v in range(4)]
         cands += [dict(group_size=G, kernel=k) for G in (32, 64) for k in (L.KERNEL_LEAN, L.KERNEL_SPLIT)]
+        if dtype in (torch.float32, torch.float64):
+            cands += [dict(group_size=32, kernel=L.KERNEL_LEAN, variant=1)]
     else:
         Gm = model_group_size(rowptr, dtype.itemsize)
         cands += [dict(group_size=G, kernel=L.KERNEL_SPLIT) for G in sorted({1, 2, 4, 8, Gm})]

@@ -194,6 +194,85 @@ rgcsr_spmv_lean(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *
     y[out_row(perm, row)] = finish<V>(acc, scale, row);
 }
 
+// Vector loads for G = 32: lane q of a warp owns RPL = 16 / sizeof(V)
+// consecutive rows of a group (FP32: 4, FP64: 2), so one 16-byte load
+// brings RPL values of a slot-row and one 8- or 16-byte load their columns;
+// a warp covers 32 * RPL rows (4 or 2 full groups).  Fewer, wider requests
+// than one thread per row, with the same per-row summation order.  The
+// partial last group (R_g < 32, slot stride R_g) goes through scalar loads.
+template <typename V> struct Vec16;
+template <> struct Vec16<float> {
+    static constexpr int RPL = 4;
+    using VV = float4;
+    using CV = int4;
+    static __device__ __forceinline__ void get(const float *p, const int32_t *c, float (&v)[4], int (&k)[4]) {
+        const float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
+        const int4 b = __ldcs(reinterpret_cast<const int4 *>(c));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        k[0] = b.x; k[1] = b.y; k[2] = b.z; k[3] = b.w;
+    }
+};
+template <> struct Vec16<double> {
+    static constexpr int RPL = 2;
+    static __device__ __forceinline__ void get(const double *p, const int32_t *c, double (&v)[2], int (&k)[2]) {
+        const double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+        const int2 b = __ldcs(reinterpret_cast<const int2 *>(c));
+        v[0] = a.x; v[1] = a.y;
+        k[0] = b.x; k[1] = b.y;
+    }
+};
+
+template <typename V, int U, int MIN_BLOCKS>
+__global__ void __launch_bounds__(kDefaultThreads, MIN_BLOCKS)
+rgcsr_spmv_vec(int64_t n, const V *__restrict__ val, const int32_t *__restrict__ col,
+               const int64_t *__restrict__ gp, const int32_t *__restrict__ rl, const V *__restrict__ x,
+               V *__restrict__ y, const int32_t *__restrict__ perm) {
+    constexpr int RPL = Vec16<V>::RPL;
+    constexpr int LPG = 32 / RPL;                                   // lanes per group
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = tid / LPG;
+    const int t0 = (int)(tid % LPG) * RPL;                          // first row within the group
+    const int64_t first = g * 32;
+    if (first >= n) return;
+    const int R = (int)min((int64_t)32, n - first);
+    const int64_t base = __ldg(gp + g);
+    int len[RPL];
+    int lmax = 0;
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        len[r] = (t0 + r < R) ? __ldg(rl + first + t0 + r) : 0;
+        lmax = max(lmax, len[r]);
+    }
+    V acc[RPL];
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) acc[r] = 0;
+    if (R == 32) {
+        for (int j = 0; j < lmax; j += U) {
+            V v[U][RPL];
+            int c[U][RPL];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (j + u < lmax) Vec16<V>::get(val + base + (int64_t)(j + u) * 32 + t0,
+                                                col + base + (int64_t)(j + u) * 32 + t0, v[u], c[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int r = 0; r < RPL; ++r)
+                    if (j + u < len[r]) acc[r] = fma(v[u][r], __ldg(x + c[u][r]), acc[r]);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < RPL; ++r)
+            for (int j = 0; j < len[r]; ++j) {
+                const int64_t p = base + (int64_t)j * R + t0 + r;
+                acc[r] = fma(__ldcs(val + p), __ldg(x + __ldcs(col + p)), acc[r]);
+            }
+    }
+#pragma unroll
+    for (int r = 0; r < RPL; ++r)
+        if (t0 + r < R) y[out_row(perm, first + t0 + r)] = acc[r];
+}
+
 // Sliced ELLPACK on the same slabs (the related format discussed in
 // Sec. 3.4): one thread per row, but every row of group g runs all
 // K_g = (gp[g+1] - gp[g]) / R_g slots -- no rowLengths -- so the padding is
@@ -245,6 +324,20 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
     const int32_t G = M->group_size;
     const float *scale = M->row_scale;
     if (VT<V>::scaled && !scale) return RGCSR_ERR_INVALID_ARG;
+    if (kernel == RGCSR_KERNEL_LEAN && L && L->variant == 1) {
+        if constexpr (std::is_same<V, float>::value || std::is_same<V, double>::value) {
+            auto aligned = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+            if (G != 32 || !aligned(val) || !aligned(M->columns)) return RGCSR_ERR_INVALID_ARG;
+            constexpr int lpg = 32 / Vec16<V>::RPL;
+            const int64_t blocks = ceil_div(M->n_groups * lpg, (int64_t)kDefaultThreads);
+            if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
+            rgcsr_spmv_vec<V, 2, 5><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
+                n, val, M->columns, M->group_ptr, M->row_lengths, x, y, M->row_perm);
+            return launch_status();
+        } else {
+            return RGCSR_ERR_UNSUPPORTED_DTYPE;
+        }
+    }
     if (kernel == RGCSR_KERNEL_LEAN) {
         const int64_t blocks = ceil_div(n, kDefaultThreads);
         if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
