@@ -124,9 +124,10 @@ typedef struct {
     int32_t variant;            /* configuration of the chosen kernel, 0 = default:
                                    TMA: 0..3 = (slot-rows per chunk, ring stages)
                                    (8,2), (8,4), (16,2), (4,4); LEAN: 1 = G = 32
-                                   with 16-byte loads (a lane owns 4 FP32 or 2
-                                   FP64 rows; F32/F64 only, 16-byte aligned
-                                   values and columns); other kernels: 0       */
+                                   with vector loads (a lane owns 4 rows, 2 for
+                                   F64, of a group: 16-byte column loads and 8-
+                                   or 16-byte value loads; 16-byte aligned values
+                                   and columns); other kernels: 0             */
 } rgcsr_launch;
 
 /* ----------------------------------------------------------------------- */

@@ -194,17 +194,15 @@ rgcsr_spmv_lean(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *
     y[out_row(perm, row)] = finish<V>(acc, scale, row);
 }
 
-// Vector loads for G = 32: lane q of a warp owns RPL = 16 / sizeof(V)
-// consecutive rows of a group (FP32: 4, FP64: 2), so one 16-byte load
-// brings RPL values of a slot-row and one 8- or 16-byte load their columns;
-// a warp covers 32 * RPL rows (4 or 2 full groups).  Fewer, wider requests
-// than one thread per row, with the same per-row summation order.  The
-// partial last group (R_g < 32, slot stride R_g) goes through scalar loads.
+// Vector loads for G = 32: lane q of a warp owns RPL consecutive rows of a
+// group (4; FP64: 2), so one 8- or 16-byte load brings RPL values of a
+// slot-row and one 8- or 16-byte load their columns; a warp covers 32 * RPL
+// rows.  Fewer, wider requests than one thread per row, with the same
+// per-row summation order.  The partial last group (R_g < 32, slot stride
+// R_g) goes through scalar loads.
 template <typename V> struct Vec16;
 template <> struct Vec16<float> {
     static constexpr int RPL = 4;
-    using VV = float4;
-    using CV = int4;
     static __device__ __forceinline__ void get(const float *p, const int32_t *c, float (&v)[4], int (&k)[4]) {
         const float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
         const int4 b = __ldcs(reinterpret_cast<const int4 *>(c));
@@ -221,12 +219,30 @@ template <> struct Vec16<double> {
         k[0] = b.x; k[1] = b.y;
     }
 };
+// Reduced storage: 4 rows per lane, 8 bytes of 2-byte values, 16 of columns
+// (as many lanes per group as FP32, so as many warps in flight).
+template <typename H>
+struct Vec16Half {
+    static constexpr int RPL = 4;
+    static __device__ __forceinline__ void get(const H *p, const int32_t *c, float (&v)[4], int (&k)[4]) {
+        const uint2 a = __ldcs(reinterpret_cast<const uint2 *>(p));
+        const int4 b = __ldcs(reinterpret_cast<const int4 *>(c));
+        const H *h = reinterpret_cast<const H *>(&a);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[r] = VT<H>::to_float(h[r]);
+        k[0] = b.x; k[1] = b.y; k[2] = b.z; k[3] = b.w;
+    }
+};
+template <> struct Vec16<__nv_bfloat16> : Vec16Half<__nv_bfloat16> {};
+template <> struct Vec16<__half> : Vec16Half<__half> {};
 
 template <typename V, int U, int MIN_BLOCKS>
 __global__ void __launch_bounds__(kDefaultThreads, MIN_BLOCKS)
 rgcsr_spmv_vec(int64_t n, const V *__restrict__ val, const int32_t *__restrict__ col,
-               const int64_t *__restrict__ gp, const int32_t *__restrict__ rl, const V *__restrict__ x,
-               V *__restrict__ y, const int32_t *__restrict__ perm) {
+               const int64_t *__restrict__ gp, const int32_t *__restrict__ rl, const float *__restrict__ scale,
+               const typename VT<V>::A *__restrict__ x, typename VT<V>::A *__restrict__ y,
+               const int32_t *__restrict__ perm) {
+    using A = typename VT<V>::A;
     constexpr int RPL = Vec16<V>::RPL;
     constexpr int LPG = 32 / RPL;                                   // lanes per group
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -243,12 +259,12 @@ rgcsr_spmv_vec(int64_t n, const V *__restrict__ val, const int32_t *__restrict__
         len[r] = (t0 + r < R) ? __ldg(rl + first + t0 + r) : 0;
         lmax = max(lmax, len[r]);
     }
-    V acc[RPL];
+    A acc[RPL];
 #pragma unroll
     for (int r = 0; r < RPL; ++r) acc[r] = 0;
     if (R == 32) {
         for (int j = 0; j < lmax; j += U) {
-            V v[U][RPL];
+            A v[U][RPL];
             int c[U][RPL];
 #pragma unroll
             for (int u = 0; u < U; ++u)
@@ -265,12 +281,12 @@ rgcsr_spmv_vec(int64_t n, const V *__restrict__ val, const int32_t *__restrict__
         for (int r = 0; r < RPL; ++r)
             for (int j = 0; j < len[r]; ++j) {
                 const int64_t p = base + (int64_t)j * R + t0 + r;
-                acc[r] = fma(__ldcs(val + p), __ldg(x + __ldcs(col + p)), acc[r]);
+                acc[r] = fma(VT<V>::ld(val + p), __ldg(x + __ldcs(col + p)), acc[r]);
             }
     }
 #pragma unroll
     for (int r = 0; r < RPL; ++r)
-        if (t0 + r < R) y[out_row(perm, first + t0 + r)] = acc[r];
+        if (t0 + r < R) y[out_row(perm, first + t0 + r)] = finish<V>(acc[r], scale, first + t0 + r);
 }
 
 // Sliced ELLPACK on the same slabs (the related format discussed in
@@ -325,18 +341,14 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
     const float *scale = M->row_scale;
     if (VT<V>::scaled && !scale) return RGCSR_ERR_INVALID_ARG;
     if (kernel == RGCSR_KERNEL_LEAN && L && L->variant == 1) {
-        if constexpr (std::is_same<V, float>::value || std::is_same<V, double>::value) {
-            auto aligned = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
-            if (G != 32 || !aligned(val) || !aligned(M->columns)) return RGCSR_ERR_INVALID_ARG;
-            constexpr int lpg = 32 / Vec16<V>::RPL;
-            const int64_t blocks = ceil_div(M->n_groups * lpg, (int64_t)kDefaultThreads);
-            if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
-            rgcsr_spmv_vec<V, 2, 5><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
-                n, val, M->columns, M->group_ptr, M->row_lengths, x, y, M->row_perm);
-            return launch_status();
-        } else {
-            return RGCSR_ERR_UNSUPPORTED_DTYPE;
-        }
+        auto aligned = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+        if (G != 32 || !aligned(val) || !aligned(M->columns)) return RGCSR_ERR_INVALID_ARG;
+        constexpr int lpg = 32 / Vec16<V>::RPL;
+        const int64_t blocks = ceil_div(M->n_groups * lpg, (int64_t)kDefaultThreads);
+        if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
+        rgcsr_spmv_vec<V, 2, 5><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
+            n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
+        return launch_status();
     }
     if (kernel == RGCSR_KERNEL_LEAN) {
         const int64_t blocks = ceil_div(n, kDefaultThreads);

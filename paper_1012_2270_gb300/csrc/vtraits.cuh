@@ -24,11 +24,13 @@ template <> struct VT<float> {
 template <> struct VT<__nv_bfloat16> {
     using A = float;
     static constexpr bool scaled = true;
+    static __device__ __forceinline__ float to_float(__nv_bfloat16 h) { return __bfloat162float(h); }
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldcs(p)); }
 };
 template <> struct VT<__half> {
     using A = float;
     static constexpr bool scaled = true;
+    static __device__ __forceinline__ float to_float(__half h) { return __half2float(h); }
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldcs(p)); }
 };
 

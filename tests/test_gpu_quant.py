@@ -41,6 +41,8 @@ def check(A, src, fmt, x, G=32, kernels=({}, {"kernel": L.KERNEL_SPLIT}, {"kerne
     y_deq, a_deq = oracle.csr_spmv(A.rowptr, A.col, deq, x32.astype(np.float64))
     y_orig, a_orig = oracle.csr_spmv(A.rowptr, A.col, A.val, x)
     xd = torch.from_numpy(x32).cuda()
+    if G == 32:
+        kernels = tuple(kernels) + ({"kernel": L.KERNEL_LEAN, "variant": 1},)   # 16-byte loads
     for kw in kernels:
         y = Q.spmv(xd, **kw).cpu().numpy()
         assert_within_bound(y, y_deq, a_deq, 2e-6, f"{A.name} {fmt} kernel error {kw}")
