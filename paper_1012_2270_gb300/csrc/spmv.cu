@@ -200,50 +200,38 @@ rgcsr_spmv_lean(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *
 // rows.  Fewer, wider requests than one thread per row, with the same
 // per-row summation order.  The partial last group (R_g < 32, slot stride
 // R_g) goes through scalar loads.
-template <typename V> struct Vec16;
-template <> struct Vec16<float> {
-    static constexpr int RPL = 4;
-    static __device__ __forceinline__ void get(const float *p, const int32_t *c, float (&v)[4], int (&k)[4]) {
-        const float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
-        const int4 b = __ldcs(reinterpret_cast<const int4 *>(c));
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-        k[0] = b.x; k[1] = b.y; k[2] = b.z; k[3] = b.w;
-    }
-};
-template <> struct Vec16<double> {
-    static constexpr int RPL = 2;
-    static __device__ __forceinline__ void get(const double *p, const int32_t *c, double (&v)[2], int (&k)[2]) {
-        const double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
-        const int2 b = __ldcs(reinterpret_cast<const int2 *>(c));
-        v[0] = a.x; v[1] = a.y;
-        k[0] = b.x; k[1] = b.y;
-    }
-};
-// Reduced storage: 4 rows per lane, 8 bytes of 2-byte values, 16 of columns
-// (as many lanes per group as FP32, so as many warps in flight).
-template <typename H>
-struct Vec16Half {
-    static constexpr int RPL = 4;
-    static __device__ __forceinline__ void get(const H *p, const int32_t *c, float (&v)[4], int (&k)[4]) {
-        const uint2 a = __ldcs(reinterpret_cast<const uint2 *>(p));
-        const int4 b = __ldcs(reinterpret_cast<const int4 *>(c));
-        const H *h = reinterpret_cast<const H *>(&a);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) v[r] = VT<H>::to_float(h[r]);
-        k[0] = b.x; k[1] = b.y; k[2] = b.z; k[3] = b.w;
-    }
-};
-template <> struct Vec16<__nv_bfloat16> : Vec16Half<__nv_bfloat16> {};
-template <> struct Vec16<__half> : Vec16Half<__half> {};
+// RPL consecutive values and their columns with one load each.
+template <int BYTES> struct RawVec;
+template <> struct RawVec<4> { using T = uint32_t; };
+template <> struct RawVec<8> { using T = uint2; };
+template <> struct RawVec<16> { using T = uint4; };
+template <int RPL> struct ColVec;
+template <> struct ColVec<2> { using T = int2; };
+template <> struct ColVec<4> { using T = int4; };
 
-template <typename V, int U, int MIN_BLOCKS>
+template <typename V, int RPL>
+__device__ __forceinline__ void vec_get(const V *p, const int32_t *c, typename VT<V>::A (&v)[RPL], int (&k)[RPL]) {
+    using R = typename RawVec<RPL * sizeof(V)>::T;
+    using CV = typename ColVec<RPL>::T;
+    const R a = __ldcs(reinterpret_cast<const R *>(p));
+    const CV b = __ldcs(reinterpret_cast<const CV *>(c));
+    const V *e = reinterpret_cast<const V *>(&a);
+    const int *q = reinterpret_cast<const int *>(&b);
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        if constexpr (VT<V>::scaled) v[r] = VT<V>::to_float(e[r]);
+        else v[r] = e[r];
+        k[r] = q[r];
+    }
+}
+
+template <typename V, int RPL, int U, int MIN_BLOCKS>
 __global__ void __launch_bounds__(kDefaultThreads, MIN_BLOCKS)
 rgcsr_spmv_vec(int64_t n, const V *__restrict__ val, const int32_t *__restrict__ col,
                const int64_t *__restrict__ gp, const int32_t *__restrict__ rl, const float *__restrict__ scale,
                const typename VT<V>::A *__restrict__ x, typename VT<V>::A *__restrict__ y,
                const int32_t *__restrict__ perm) {
     using A = typename VT<V>::A;
-    constexpr int RPL = Vec16<V>::RPL;
     constexpr int LPG = 32 / RPL;                                   // lanes per group
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t g = tid / LPG;
@@ -268,8 +256,8 @@ rgcsr_spmv_vec(int64_t n, const V *__restrict__ val, const int32_t *__restrict__
             int c[U][RPL];
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (j + u < lmax) Vec16<V>::get(val + base + (int64_t)(j + u) * 32 + t0,
-                                                col + base + (int64_t)(j + u) * 32 + t0, v[u], c[u]);
+                if (j + u < lmax) vec_get<V, RPL>(val + base + (int64_t)(j + u) * 32 + t0,
+                                                  col + base + (int64_t)(j + u) * 32 + t0, v[u], c[u]);
 #pragma unroll
             for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -340,14 +328,21 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
     const int32_t G = M->group_size;
     const float *scale = M->row_scale;
     if (VT<V>::scaled && !scale) return RGCSR_ERR_INVALID_ARG;
-    if (kernel == RGCSR_KERNEL_LEAN && L && L->variant == 1) {
+    if (kernel == RGCSR_KERNEL_LEAN && L && (L->variant == 1 || L->variant == 2)) {
         auto aligned = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
         if (G != 32 || !aligned(val) || !aligned(M->columns)) return RGCSR_ERR_INVALID_ARG;
-        constexpr int lpg = 32 / Vec16<V>::RPL;
+        // variant 1: 4 rows per lane (FP64: 2), 2 slot-rows in flight;
+        // variant 2: 2 rows per lane, 4 slot-rows in flight
+        constexpr int rpl1 = sizeof(V) == 8 ? 2 : 4;
+        const int lpg = L->variant == 1 ? 32 / rpl1 : 16;
         const int64_t blocks = ceil_div(M->n_groups * lpg, (int64_t)kDefaultThreads);
         if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
-        rgcsr_spmv_vec<V, 2, 5><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
-            n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
+        if (L->variant == 1)
+            rgcsr_spmv_vec<V, rpl1, 2, 5><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
+                n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
+        else
+            rgcsr_spmv_vec<V, 2, 4, 5><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
+                n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
         return launch_status();
     }
     if (kernel == RGCSR_KERNEL_LEAN) {
