@@ -609,18 +609,25 @@ def measure_forms(mats, cases, detail, dev, stream):
     Gm = model_group_size(b.rowptr, 4)
     Mt = RgCSRMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32,
                               group_size=Gm)
-    forms["spmm_b_f32"] = {"config": "G=1, long-row schedule T=32 S=256, lanes-per-row kernels",
-                           "thread_per_row_group_size": Gm}
+    # and G = 32 in descending row order with group tiles (the tiled kernels)
+    Md = RgCSRMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32,
+                              group_size=32, row_order="descending").tile_groups(64)
+    forms["spmm_b_f32"] = {"configs": {"lanes_per_row": "G=1, long-row schedule T=32 S=256",
+                                       "tiles": "G=32, descending row order, group tiles C=64",
+                                       "thread_per_row": f"G={Gm}"}}
     for k in (1, 4, 8, 16, 32):
         X = torch.rand(b.n_cols, k, device=dev)
         Y = torch.empty(b.n_rows, k, device=dev)
-        t = time_flushed(lambda: Mb.spmm(X, out=Y), 10, flush, stream)
-        t_old = time_flushed(lambda: Mt.spmm(X, out=Y), 5, flush, stream)
+        ts = {"lanes_per_row": time_flushed(lambda: Mb.spmm(X, out=Y), 10, flush, stream),
+              "tiles": time_flushed(lambda: Md.spmm(X, out=Y), 10, flush, stream),
+              "thread_per_row": time_flushed(lambda: Mt.spmm(X, out=Y), 5, flush, stream)}
+        best = min(ts, key=ts.get)
+        t = ts[best]
         nb = roofline.spmm_bytes(b.n_rows, b.n_cols, b.nnz, (b.n_rows + GROUP - 1) // GROUP, 4, k)
         forms["spmm_b_f32"][f"k{k}"] = {"gbs": nb / t / 1e3, "gflops": 2 * b.nnz * k / t / 1e3, "us": t,
-                                        "thread_per_row_us": t_old}
+                                        "best": best, "us_by_config": ts}
         del X, Y
-    del Mb, Mt
+    del Mb, Mt, Md
 
     # -- backward of Y = A X on (b), batch of 8 right-hand sides ---------------
     G = 1

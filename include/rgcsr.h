@@ -307,6 +307,21 @@ int rgcsr_spmm_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *long_rows
                          const void *X, int64_t ldx, void *Y, int64_t ldy, void *partials,
                          int64_t partials_count, rgcsr_stream_t stream);
 
+/* Y = A X on the group-tile schedule T of M (rgcsr_tiles_plan/build; G <=
+ * 32): lane t of a warp owns row t of a tile and KC consecutive columns of
+ * its result (chunks of 8, 4, then 1 columns), so value/column loads are
+ * coalesced slot-rows and each non-zero reads one KC-wide piece of X.  Tiles
+ * of a split group add their KC partial sums per row in tile order (the last
+ * to arrive writes Y).  partials: device scratch of partials_count >=
+ * T->n_partials * 32 * min(k, 8) elements (double for F64 storage, float
+ * otherwise); unused without split groups.  X, Y, ldx, ldy and element types
+ * as for rgcsr_spmm; k = 1 with ldx = ldy = 1 runs rgcsr_spmv_tiles.  One
+ * product per schedule in flight at a time.  Async.  RGCSR_ERR_WORKSPACE if
+ * partials is too small. */
+int rgcsr_spmm_tiles(const rgcsr_matrix *M, const rgcsr_tiles *tiles, int32_t k, const void *X,
+                     int64_t ldx, void *Y, int64_t ldy, void *partials, int64_t partials_count,
+                     rgcsr_stream_t stream);
+
 /* ----------------------------------------------------------------------- */
 /* Batched SpMV: many RgCSR matrices of uneven sizes in one launch (not in  */
 /* the paper).  The members' arrays are concatenated; member m uses         */

@@ -104,6 +104,7 @@ SIGNATURES = {
     "rgcsr_spmv_long_rows": (ctypes.c_int, [_PM, ctypes.POINTER(LongRows), P, P, P]),
     "rgcsr_spmm": (ctypes.c_int, [_PM, I32, P, I64, P, I64, P]),
     "rgcsr_spmm_long_rows": (ctypes.c_int, [_PM, ctypes.POINTER(LongRows), I32, P, I64, P, I64, P, I64, P]),
+    "rgcsr_spmm_tiles": (ctypes.c_int, [_PM, ctypes.POINTER(Tiles), I32, P, I64, P, I64, P, I64, P]),
     "rgcsr_transpose_workspace_bytes": (SZ, [I64, I64, I64]),
     "rgcsr_csr_transpose": (ctypes.c_int, [_PCSR, P, P, P, P, P, SZ, P]),
     "rgcsr_csr_row_index": (ctypes.c_int, [_PCSR, P, P]),

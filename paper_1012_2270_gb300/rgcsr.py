@@ -272,8 +272,10 @@ class RgCSRMatrix:
              stream=None) -> torch.Tensor:
         """Y = A X for X of shape [n_cols, k] with unit column stride.
 
-        rows: use the lanes-per-row kernels (rgcsr_spmm_long_rows), with the
-        long-row schedule if one was built; default: when a schedule exists."""
+        With a group-tile schedule (tile_groups) and rows not set: the tiled
+        kernels (rgcsr_spmm_tiles).  rows: the lanes-per-row kernels
+        (rgcsr_spmm_long_rows), with the long-row schedule if one was built;
+        the default when a long-row schedule exists.  Else rgcsr_spmm."""
         if X.dim() != 2 or X.shape[0] != self.s.n_cols or X.dtype != self.x_dtype or X.stride(1) != 1:
             raise ValueError(f"X must be [{self.s.n_cols}, k] {self.x_dtype} with unit column stride")
         k = X.shape[1]
@@ -281,6 +283,15 @@ class RgCSRMatrix:
         if Y.shape != (self.s.n_rows, k) or Y.stride(1) != 1:
             raise ValueError("out must be [n_rows, k] with unit column stride")
         ldx, ldy = max(X.stride(0), k), max(Y.stride(0), k)
+        if rows is None and self._tiles is not None:
+            T, bufs = self._tiles
+            need = T.n_partials * 32 * min(k, 8)
+            if bufs.get("spmm_partials") is None or bufs["spmm_partials"].numel() < need:
+                bufs["spmm_partials"] = torch.empty(max(need, 1), dtype=self.x_dtype, device=X.device)
+            part = bufs["spmm_partials"]
+            L.call("rgcsr_spmm_tiles", ctypes.byref(self.s), ctypes.byref(T), k, _ptr(X), ldx, _ptr(Y), ldy,
+                   _ptr(part), part.numel(), _stream_ptr(stream))
+            return Y
         if rows is None:
             rows = self._long is not None
         if not rows:

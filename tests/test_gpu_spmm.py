@@ -155,3 +155,61 @@ def test_spmm_rows_full_size_b(k):
                              dtype=torch.float32).split_long_rows(32, 256)
     X = synth.uniform_matrix(A.n_cols, k, seed=k)
     check(A, M, "f32", X, TAU["f32"])
+
+
+# ---------------------------------------------------------------------------
+# tiled kernels (rgcsr_spmm_tiles) on the group-tile schedule
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("k", [1, 2, 4, 5, 8, 13, 32])
+@pytest.mark.parametrize("G,order,C", [(32, "descending", 16), (32, None, 1 << 20), (7, None, 3)])
+def test_spmm_tiles_ragged(dtype, k, G, order, C):
+    rng = np.random.default_rng(k * 3 + G)
+    Ls = rng.integers(0, 30, 1500)
+    Ls[[3, 700, 701]] = [2000, 900, 35]
+    A = synth.random_csr(1500, 2500, Ls, seed=k + 1)
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dtype]), A.n_cols, group_size=G, dtype=TT[dtype],
+                             row_order=order).tile_groups(C)
+    X = synth.uniform_matrix(A.n_cols, k, seed=k)
+    Xd = torch.from_numpy(X.astype(NP[dtype])).cuda()
+    Y1 = M.spmm(Xd).cpu().numpy()
+    Y2 = M.spmm(Xd).cpu().numpy()
+    assert np.array_equal(Y1, Y2)                                      # deterministic, counters reset
+    Y_ref, aY = oracle.csr_spmm(A.rowptr, A.col, rounded_values(A.val, dtype), X.astype(NP[dtype]).astype(np.float64))
+    assert_within_bound(Y1.ravel(), Y_ref.ravel(), aY.ravel(), TAU[dtype], f"tiles k={k} G={G} {order}")
+
+
+def test_spmm_tiles_strided_quantized_and_workspace():
+    import ctypes
+    from paper_1012_2270_gb300 import _lib as L
+    from paper_1012_2270_gb300.rgcsr import _ptr, _stream_ptr
+    A = synth.power_law(20_000, seed=6)
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val, A.n_cols, group_size=32, dtype=torch.float64,
+                             row_order="descending")
+    Q = M.quantized("bf16").tile_groups(32)
+    q, s = oracle.quantize_rows(A.rowptr, A.val, oracle.BF16)
+    deq = oracle.dequantized_values(A.rowptr, q, s, oracle.BF16)
+    wide = synth.uniform_matrix(A.n_cols, 9, seed=2).astype(np.float32)
+    Xd = torch.from_numpy(wide).cuda()[:, 1:7]                          # k = 6, unaligned rows
+    Yw = torch.full((A.n_rows, 8), 3.0, device="cuda")
+    Q.spmm(Xd, out=Yw[:, 1:7])
+    assert (Yw[:, 0] == 3.0).all() and (Yw[:, 7] == 3.0).all()
+    Y_ref, aY = oracle.csr_spmm(A.rowptr, A.col, deq, wide[:, 1:7].astype(np.float64))
+    assert_within_bound(Yw[:, 1:7].cpu().numpy().ravel(), Y_ref.ravel(), aY.ravel(), 2e-6, "tiles bf16")
+    T = Q._tiles[0]
+    assert T.n_partials > 0
+    part = torch.empty(T.n_partials * 32 * 6 - 1, device="cuda")
+    X = torch.zeros(A.n_cols, 6, device="cuda")
+    Y = torch.empty(A.n_rows, 6, device="cuda")
+    st = L.lib().rgcsr_spmm_tiles(ctypes.byref(Q.s), ctypes.byref(T), 6, _ptr(X), 6, _ptr(Y), 6, _ptr(part),
+                                  part.numel(), _stream_ptr())
+    assert st == L.RGCSR_ERR_WORKSPACE
+
+
+@pytest.mark.parametrize("k", [4, 8, 32])
+def test_spmm_tiles_full_size_b(k):
+    A = synth.workload_b()
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(np.float32), A.n_cols, group_size=32,
+                             dtype=torch.float32, row_order="descending").tile_groups(64)
+    X = synth.uniform_matrix(A.n_cols, k, seed=k)
+    check(A, M, "f32", X, TAU["f32"])
