@@ -630,8 +630,9 @@ def measure_forms(mats, cases, detail, dev, stream):
     del Mb, Mt, Md
 
     # -- backward of Y = A X on (b), batch of 8 right-hand sides ---------------
-    G = 1
-    op = SparseOperator(b.rowptr, b.col, b.n_cols, dtype=torch.float32, group_size=G, long_rows=(32, 256))
+    G = 32
+    op = SparseOperator(b.rowptr, b.col, b.n_cols, dtype=torch.float32, group_size=G, row_order="descending",
+                        tiles=64)
     vals = torch.from_numpy(b.val.astype(np.float32)).to(dev).requires_grad_(True)
     X = torch.rand(b.n_cols, 8, device=dev, requires_grad=True)
 
@@ -646,7 +647,7 @@ def measure_forms(mats, cases, detail, dev, stream):
         (Y * Y).sum().backward()
     t_f = time_flushed(fwd, 10, flush, stream)
     t_fb = time_flushed(fwd_bwd, 10, flush, stream)
-    forms["backward_b_k8_f32"] = {"group_size": G, "forward_us": t_f, "forward_backward_us": t_fb,
+    forms["backward_b_k8_f32"] = {"group_size": G, "schedule": "descending row order, group tiles C=64", "forward_us": t_f, "forward_backward_us": t_fb,
                                   "backward_over_forward": (t_fb - t_f) / t_f}
     del op, vals, X
 

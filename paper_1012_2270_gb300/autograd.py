@@ -25,9 +25,12 @@ class SparseOperator:
     """A fixed CSR pattern (``rowptr``, ``col``) of shape [n_rows, n_cols]."""
 
     def __init__(self, rowptr, col, n_cols: int, dtype: torch.dtype = torch.float32,
-                 group_size: int = 32, long_rows: tuple | None = None, device="cuda"):
-        """long_rows = (threshold, segment): the long-row schedule for A and
-        A^T (their SpMV and the lanes-per-row SpMM), for uneven rows."""
+                 group_size: int = 32, long_rows: tuple | None = None, row_order=None,
+                 tiles: int | None = None, device="cuda"):
+        """For uneven rows, A and A^T can take a launch schedule: long_rows =
+        (threshold, segment) for the long-row segments (lanes-per-row SpMM),
+        or row_order="descending" with tiles = C for group tiles of C
+        slot-rows (tiled SpMV/SpMM, group_size <= 32)."""
         self.rowptr = _dev(rowptr, torch.int64, device)
         self.col = _dev(col, torch.int32, device)
         self.n_rows = self.rowptr.numel() - 1
@@ -37,7 +40,7 @@ class SparseOperator:
         zeros = torch.zeros(self.nnz, dtype=dtype, device=device)
         st = _stream_ptr()
         self.A = RgCSRMatrix.from_csr(self.rowptr, self.col, zeros, self.n_cols, group_size=group_size,
-                                      dtype=dtype, keep_slot_map=True)
+                                      dtype=dtype, keep_slot_map=True, row_order=row_order)
         # stable transposition of the pattern
         csr = csr_struct(self.rowptr, self.col, zeros, self.n_cols)
         nb = L.lib().rgcsr_transpose_workspace_bytes(self.nnz, self.n_rows, self.n_cols)
@@ -49,7 +52,7 @@ class SparseOperator:
                None, _ptr(ws), nb, st)
         del ws
         self.AT = RgCSRMatrix.from_csr(t_rowptr, t_col, zeros, self.n_rows, group_size=group_size,
-                                       dtype=dtype, keep_slot_map=True)
+                                       dtype=dtype, keep_slot_map=True, row_order=row_order)
         self.at_src = torch.empty(self.AT.n_stored, dtype=torch.int64, device=device)
         L.call("rgcsr_compose_index", _ptr(self.AT.slot_to_csr), _ptr(perm), self.AT.n_stored,
                _ptr(self.at_src), st)
@@ -58,6 +61,9 @@ class SparseOperator:
         if long_rows is not None:
             self.A.split_long_rows(*long_rows)
             self.AT.split_long_rows(*long_rows)
+        if tiles is not None:
+            self.A.tile_groups(tiles)
+            self.AT.tile_groups(tiles)
 
     def set_values(self, values: torch.Tensor) -> None:
         """Loads CSR-ordered values into the RgCSR matrices of A and A^T."""

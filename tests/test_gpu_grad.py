@@ -68,10 +68,10 @@ def abs_bounds(A, vals, X, G):
     return dX_abs, dval_abs
 
 
-def check_grads(A, dtype, k, group_size=32, seed=0):
+def check_grads(A, dtype, k, group_size=32, seed=0, **schedule):
     vals = rounded_values(A.val, dtype)
     X = synth.uniform_matrix(A.n_cols, k, seed=seed).astype(NP[dtype]).astype(np.float64)
-    op = SparseOperator(A.rowptr, A.col, A.n_cols, dtype=TT[dtype], group_size=group_size)
+    op = SparseOperator(A.rowptr, A.col, A.n_cols, dtype=TT[dtype], group_size=group_size, **schedule)
     v = torch.tensor(vals, dtype=TT[dtype], device="cuda", requires_grad=True)
     Xt = torch.tensor(X, dtype=TT[dtype], device="cuda", requires_grad=True)
     Y = spmm(op, v, Xt)
@@ -97,6 +97,8 @@ def test_grads_ragged(dtype, k):
     A = synth.random_csr(1200, 1500, Ls, seed=k)
     check_grads(A, dtype, k)
     check_grads(A, dtype, k, group_size=8)
+    check_grads(A, dtype, k, group_size=32, row_order="descending", tiles=16)
+    check_grads(A, dtype, k, group_size=1, long_rows=(16, 64))
 
 
 def test_values_refresh_between_calls():
@@ -162,3 +164,4 @@ def test_gradcheck_tiny():
 def test_grads_full_size_b_batch8():
     A = synth.workload_b()
     check_grads(A, "f32", 8)
+    check_grads(A, "f32", 8, row_order="descending", tiles=64)
