@@ -14,8 +14,7 @@
 // may have its own group size.  No host synchronisation and no allocation:
 // the call can be captured in a CUDA graph.
 #include "common.cuh"
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
+#include "vtraits.cuh"
 #include <climits>
 
 namespace rgcsr {
@@ -24,46 +23,10 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kUnroll = 8;
 
-template <typename V> struct BV;
-template <> struct BV<double> {
-    using A = double;
-    static constexpr bool scaled = false;
-    static __device__ __forceinline__ double ld(const double *p) { return __ldcs(p); }
-};
-template <> struct BV<float> {
-    using A = float;
-    static constexpr bool scaled = false;
-    static __device__ __forceinline__ float ld(const float *p) { return __ldcs(p); }
-};
-template <> struct BV<__nv_bfloat16> {
-    using A = float;
-    static constexpr bool scaled = true;
-    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldcs(p)); }
-};
-template <> struct BV<__half> {
-    using A = float;
-    static constexpr bool scaled = true;
-    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldcs(p)); }
-};
-
 __device__ __forceinline__ int split_point(int len, bool valid) {
     const int lmax = warp_max_i(len);
     const int lmin = warp_min_i(valid ? len : INT_MAX);
-    if (lmax - lmin <= 32) return lmax;
-    int cand = len;
-    long long cost = 4LL * cand;
-#pragma unroll 8
-    for (int s = 0; s < 32; ++s) {
-        const int d = __shfl_sync(kFull, len, s) - cand;
-        if (d > 0) cost += 8LL * ((d + 31) >> 5);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const long long oc = __shfl_xor_sync(kFull, cost, o);
-        const int ocand = __shfl_xor_sync(kFull, cand, o);
-        if (oc < cost || (oc == cost && ocand < cand)) { cost = oc; cand = ocand; }
-    }
-    return cand;
+    return lmax - lmin <= 32 ? lmax : choose_split(len, 8);
 }
 
 template <typename V>
@@ -71,8 +34,8 @@ __global__ void __launch_bounds__(kThreads)
 spmv_batched_kernel(int64_t n_tasks, const int32_t *__restrict__ tasks, const rgcsr_batch_desc *__restrict__ desc,
                     const V *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ gp,
                     const int32_t *__restrict__ rl, const float *__restrict__ scale,
-                    const typename BV<V>::A *__restrict__ x, typename BV<V>::A *__restrict__ y) {
-    using A = typename BV<V>::A;
+                    const typename VT<V>::A *__restrict__ x, typename VT<V>::A *__restrict__ y) {
+    using A = typename VT<V>::A;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
     for (int64_t t = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5; t < n_tasks; t += warps) {
@@ -101,7 +64,7 @@ spmv_batched_kernel(int64_t n_tasks, const int32_t *__restrict__ tasks, const rg
             for (int u = 0; u < kUnroll; ++u) {
                 if (j + u < jend) {
                     const int64_t p = ptr + (int64_t)(j + u) * stride;
-                    v[u] = BV<V>::ld(val + p);
+                    v[u] = VT<V>::ld(val + p);
                     c[u] = __ldcs(col + p);
                 }
             }
@@ -119,13 +82,13 @@ spmv_batched_kernel(int64_t n_tasks, const int32_t *__restrict__ tasks, const rg
             A part = 0;
             for (int j = j0 + lane; j < Lr; j += 32) {
                 const int64_t p = pr + (int64_t)j * sr;
-                part = fma(BV<V>::ld(val + p), __ldg(xm + __ldcs(col + p)), part);
+                part = fma(VT<V>::ld(val + p), __ldg(xm + __ldcs(col + p)), part);
             }
             part = warp_sum(part);
             if (lane == r) acc += part;
         }
         if (valid) {
-            if constexpr (BV<V>::scaled) acc *= __ldg(scale + d.row_off + lrow);
+            if constexpr (VT<V>::scaled) acc *= __ldg(scale + d.row_off + lrow);
             y[d.row_off + lrow] = acc;
         }
     }

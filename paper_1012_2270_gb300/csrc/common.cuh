@@ -66,6 +66,28 @@ __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
 template <typename T>
 __device__ __forceinline__ T ld_x(const T *p) { return __ldg(p); }
 
+// Split slot j0 for a warp whose rows differ a lot in length: every lane
+// proposes its own row length as j0 and prices it as
+//   4*j0 + w4 * sum_s ceil(max(0, len_s - j0) / 32)
+// (thread-per-row steps plus weighted warp-cooperative steps); the warp
+// takes the cheapest proposal, ties to the smaller j0.  Warp-uniform result.
+__device__ __forceinline__ int choose_split(int len, int w4) {
+    int cand = len;
+    long long cost = 4LL * cand;
+#pragma unroll 8
+    for (int s = 0; s < 32; ++s) {
+        const int d = __shfl_sync(kFull, len, s) - cand;
+        if (d > 0) cost += (long long)w4 * ((d + 31) >> 5);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long oc = __shfl_xor_sync(kFull, cost, o);
+        const int ocand = __shfl_xor_sync(kFull, cand, o);
+        if (oc < cost || (oc == cost && ocand < cand)) { cost = oc; cand = ocand; }
+    }
+    return cand;
+}
+
 // Output index of stored row `row`: the CSR row it holds under a row order
 // (rgcsr_matrix::row_perm), or the row itself without one.
 __device__ __forceinline__ int64_t out_row(const int32_t *perm, int64_t row) {

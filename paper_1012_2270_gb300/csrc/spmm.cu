@@ -46,23 +46,6 @@ __device__ __forceinline__ void axpy_row(A (&acc)[KC], A v, const A *__restrict_
     }
 }
 
-__device__ __forceinline__ int choose_split_mm(int len, int w4) {
-    int cand = len;
-    long long cost = 4LL * cand;
-#pragma unroll 8
-    for (int s = 0; s < 32; ++s) {
-        int d = __shfl_sync(kFull, len, s) - cand;
-        if (d > 0) cost += (long long)w4 * ((d + 31) >> 5);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        long long oc = __shfl_xor_sync(kFull, cost, o);
-        int ocand = __shfl_xor_sync(kFull, cand, o);
-        if (oc < cost || (oc == cost && ocand < cand)) { cost = oc; cand = ocand; }
-    }
-    return cand;
-}
-
 template <typename V, int KC, bool VEC>
 __global__ void __launch_bounds__(kThreads)
 rgcsr_spmm_kernel(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *__restrict__ col,
@@ -85,7 +68,7 @@ rgcsr_spmm_kernel(int64_t n, int32_t G, const V *__restrict__ val, const int32_t
     const int lmax = warp_max_i(len);
     const int lmin = warp_min_i(valid ? len : INT_MAX);
     int j0 = lmax;
-    if (lmax - lmin > 32) j0 = choose_split_mm(len, 8);
+    if (lmax - lmin > 32) j0 = choose_split(len, 8);
 
     A acc[KC];
 #pragma unroll

@@ -58,28 +58,6 @@ __global__ void rgcsr_spmv_paper(int64_t n, int32_t G, const T *__restrict__ val
     y[out_row(perm, row)] = acc;
 }
 
-// Split slot j0 for an irregular warp: every lane proposes its own row
-// length as j0 and prices it as
-//   4*j0 + w4 * sum_s ceil(max(0, len_s - j0) / 32)
-// (thread-per-row steps plus weighted warp-cooperative steps); the warp
-// takes the cheapest proposal, ties to the smaller j0.
-__device__ __forceinline__ int choose_split(int len, int w4) {
-    int cand = len;
-    long long cost = 4LL * cand;
-#pragma unroll 8
-    for (int s = 0; s < 32; ++s) {
-        int d = __shfl_sync(kFull, len, s) - cand;
-        if (d > 0) cost += (long long)w4 * ((d + 31) >> 5);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        long long oc = __shfl_xor_sync(kFull, cost, o);
-        int ocand = __shfl_xor_sync(kFull, cand, o);
-        if (oc < cost || (oc == cost && ocand < cand)) { cost = oc; cand = ocand; }
-    }
-    return cand;
-}
-
 template <typename V, bool NC>
 __global__ void __launch_bounds__(kDefaultThreads)
 rgcsr_spmv_split(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *__restrict__ col,
