@@ -220,6 +220,11 @@ def test_full_size_spmv(name, dtype):
     check_spmv(M, A, dtype, x)
     if name != "b":
         check_spmv(M, A, dtype, x, kernel=L.KERNEL_SPLIT)
+        check_spmv(M, A, dtype, x, kernel=L.KERNEL_LEAN)
+        for v in (1, 2):                                    # vector loads
+            check_spmv(M, A, dtype, x, kernel=L.KERNEL_LEAN, variant=v)
+        for v in range(4):
+            check_spmv(M, A, dtype, x, kernel=L.KERNEL_TMA, variant=v)
     check_spmv(M, A, dtype, x, kernel=L.KERNEL_TMA)
     assert device_status() == 0
 

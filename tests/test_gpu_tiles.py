@@ -131,10 +131,16 @@ def test_tiles_errors_and_empty():
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_tiles_full_size_b_descending(dtype):
+    # every tile shape the benchmark's tuner may pick for the power-law matrix
     A = synth.workload_b()
     M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dtype]), A.n_cols, group_size=32,
-                             dtype=TT[dtype], row_order="descending").tile_groups(64)
-    check(M, A, dtype, synth.uniform_vector(A.n_cols, seed=0))
+                             dtype=TT[dtype], row_order="descending")
+    x = synth.uniform_vector(A.n_cols, seed=0)
+    for C in (32, 64, 128):
+        for v in range(5):
+            M._tiles = None
+            M.tile_groups(C, variant=v)
+            check(M, A, dtype, x)
 
 
 @pytest.mark.parametrize("name", ["a", "c"])
