@@ -91,24 +91,61 @@ int cg_run(const rgcsr_matrix *A, const void *b, void *x, double rel_tol, int ma
     if (!(bb > 0.0)) return RGCSR_OK;                 // b = 0: x = 0 is exact
     double rr = bb;
     int cur = 0, it = 0;
+    // One CG iteration: q = A d; alpha = rr / (d.q); x += alpha d; r -= alpha q;
+    // rr' = r.r; d = r + (rr' / rr) d.  `cur` selects which scalar slot holds rr.
+    auto iteration = [&](cudaStream_t st_, int cur_) -> int {
+        int e;
+        if ((e = rgcsr_spmv(A, c.d, c.q, (rgcsr_stream_t)st_)) != RGCSR_OK) return e;
+        if ((e = dot_device(n, c.d, c.q, &c.scal[2], c.partials, vt, st_)) != RGCSR_OK) return e;
+        cg_xr_kernel<T><<<grid(n), kThreads, 0, st_>>>(n, &c.scal[cur_], &c.scal[2], static_cast<T *>(x),
+                                                       static_cast<T *>(c.r), static_cast<const T *>(c.d),
+                                                       static_cast<const T *>(c.q));
+        if ((e = dot_device(n, c.r, c.r, &c.scal[1 - cur_], c.partials, vt, st_)) != RGCSR_OK) return e;
+        cg_d_kernel<T><<<grid(n), kThreads, 0, st_>>>(n, &c.scal[1 - cur_], &c.scal[cur_],
+                                                      static_cast<const T *>(c.r), static_cast<T *>(c.d));
+        return launch_status();
+    };
+    // After the first round of iterations (which also runs any one-off kernel
+    // setup), the check_every iterations between two convergence checks are
+    // recorded once into a CUDA graph (on a private stream: the caller's may
+    // be the legacy default stream, which cannot be captured) and replayed on
+    // the caller's stream.  check_every is even, so a round leaves `cur` as
+    // it found it.  If recording fails the iterations are launched directly.
+    cudaGraphExec_t round = nullptr;
+    bool tried = false;
     while (it < max_iter) {
-        if ((st = rgcsr_spmv(A, c.d, c.q, (rgcsr_stream_t)s)) != RGCSR_OK) return st;
-        if ((st = dot_device(n, c.d, c.q, &c.scal[2], c.partials, vt, s)) != RGCSR_OK) return st;
-        cg_xr_kernel<T><<<grid(n), kThreads, 0, s>>>(n, &c.scal[cur], &c.scal[2], static_cast<T *>(x),
-                                                     static_cast<T *>(c.r), static_cast<const T *>(c.d),
-                                                     static_cast<const T *>(c.q));
-        if ((st = dot_device(n, c.r, c.r, &c.scal[1 - cur], c.partials, vt, s)) != RGCSR_OK) return st;
-        cg_d_kernel<T><<<grid(n), kThreads, 0, s>>>(n, &c.scal[1 - cur], &c.scal[cur],
-                                                    static_cast<const T *>(c.r), static_cast<T *>(c.d));
-        if ((st = launch_status()) != RGCSR_OK) return st;
-        cur = 1 - cur;
-        ++it;
-        if (it % check_every == 0 || it == max_iter) {
-            RGCSR_CUDA_TRY(cudaMemcpyAsync(&rr, &c.scal[cur], sizeof(double), cudaMemcpyDeviceToHost, s));
-            RGCSR_CUDA_TRY(cudaStreamSynchronize(s));
-            if (!(rr == rr) || std::sqrt(rr) <= rel_tol * std::sqrt(bb)) break;   // converged (or NaN)
+        const int chunk = check_every < max_iter - it ? check_every : max_iter - it;
+        if (round && chunk == check_every) {
+            RGCSR_CUDA_TRY(cudaGraphLaunch(round, s));
+        } else {
+            for (int i = 0; i < chunk; ++i) {
+                if ((st = iteration(s, cur)) != RGCSR_OK) { if (round) cudaGraphExecDestroy(round); return st; }
+                cur = 1 - cur;
+            }
+        }
+        it += chunk;
+        RGCSR_CUDA_TRY(cudaMemcpyAsync(&rr, &c.scal[cur], sizeof(double), cudaMemcpyDeviceToHost, s));
+        RGCSR_CUDA_TRY(cudaStreamSynchronize(s));
+        if (!(rr == rr) || std::sqrt(rr) <= rel_tol * std::sqrt(bb)) break;   // converged (or NaN)
+        if (!tried && check_every % 2 == 0 && max_iter - it >= 2 * check_every) {
+            tried = true;
+            cudaStream_t cap = nullptr;
+            cudaGraph_t g = nullptr;
+            if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess) {
+                if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                    int e = RGCSR_OK;
+                    for (int i = 0; i < check_every && e == RGCSR_OK; ++i) e = iteration(cap, (cur + i) & 1);
+                    if (cudaStreamEndCapture(cap, &g) == cudaSuccess && g && e == RGCSR_OK &&
+                        cudaGraphInstantiate(&round, g, 0) != cudaSuccess)
+                        round = nullptr;
+                    if (g) cudaGraphDestroy(g);
+                }
+                cudaStreamDestroy(cap);
+            }
+            cudaGetLastError();                      // a failed recording leaves no sticky error
         }
     }
+    if (round) cudaGraphExecDestroy(round);
     *iterations = it;
     *rel_residual = std::sqrt(rr / bb);
     return (rr == rr) ? RGCSR_OK : RGCSR_ERR_INVALID_ARG;

@@ -511,28 +511,39 @@ RGCSR_API int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
     if (!y || (M->n_cols > 0 && !x)) return RGCSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     int kernel = launch ? launch->kernel : RGCSR_KERNEL_AUTO;
+    int variant = launch ? launch->variant : 0;
     if (kernel == RGCSR_KERNEL_AUTO) {
         // Dense groups (padding <= 25% of the stored slots): the TMA-staged
-        // kernel for FP32 and for short FP64 rows, the full-occupancy
+        // kernel for FP32 and for short FP64 rows, the vector-load kernel
+        // for short BF16/FP16 rows (G = 32), the full-occupancy
         // thread-per-row kernel otherwise; uneven or long rows take the
         // warp-split kernel.
         // "dense": little padding and no row far longer than the average
         const bool dense = M->n_stored * 4 <= M->nnz * 5 &&
                            !(M->max_row_len > 64 && M->max_row_len * M->n_rows > 8 * M->nnz);
         const bool short_rows = M->nnz <= 8 * M->n_rows;
-        if (dense && tma_eligible(M) && (M->value_type == RGCSR_F32 || short_rows))
+        const bool reduced = M->value_type == RGCSR_BF16 || M->value_type == RGCSR_F16;
+        auto aligned = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+        variant = 0;
+        if (dense && tma_eligible(M) && (M->value_type == RGCSR_F32 || short_rows)) {
             kernel = RGCSR_KERNEL_TMA;
-        else if (dense)
+        } else if (dense && reduced && short_rows && M->group_size == 32 && aligned(M->values) &&
+                   aligned(M->columns)) {
             kernel = RGCSR_KERNEL_LEAN;
-        else
+            variant = 1;
+        } else if (dense) {
+            kernel = RGCSR_KERNEL_LEAN;
+        } else {
             kernel = RGCSR_KERNEL_SPLIT;
+        }
     }
     if (kernel == RGCSR_KERNEL_TMA) {
         if (!tma_eligible(M)) return RGCSR_ERR_INVALID_ARG;
-        return launch_spmv_tma(M, x, y, launch ? launch->variant : 0, s);
+        return launch_spmv_tma(M, x, y, variant, s);
     }
     rgcsr_launch resolved = launch ? *launch : rgcsr_launch{};
     resolved.kernel = kernel;
+    resolved.variant = variant;
     switch (M->value_type) {
         case RGCSR_F64:
             return launch_spmv<double>(M, static_cast<const double *>(x), static_cast<double *>(y), &resolved, s);
