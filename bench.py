@@ -702,6 +702,29 @@ def measure_forms(mats, cases, detail, dev, stream):
     forms["jacobi_grad_96_f32"] = res
     del opj
 
+    # -- conversion CSR -> RgCSR on the device (plan + convert; FP32 values,
+    # CSR already in HBM): bytes = CSR read + RgCSR written ----------------
+    conv = {}
+    for name, A, x in mats:
+        rp = torch.from_numpy(A.rowptr).to(dev)
+        cl = torch.from_numpy(A.col).to(dev)
+        vl = torch.from_numpy(A.val.astype(np.float32)).to(dev)
+        order = "descending" if name == "b" else None
+        ts = []
+        for rep in range(6):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            M = RgCSRMatrix.from_csr(rp, cl, vl, A.n_cols, group_size=32, dtype=torch.float32, row_order=order)
+            torch.cuda.synchronize()
+            if rep:
+                ts.append(1e6 * (time.perf_counter() - t0))
+        t = statistics.median(ts)
+        nb = A.nnz * 8 + (A.n_rows + 1) * 8 + M.n_stored * 8 + A.n_rows * 4 + (M.s.n_groups + 1) * 8
+        conv[name] = {"us": t, "gbs": nb / t / 1e3, "row_order": order or "natural",
+                      "n_stored": M.n_stored, "note": "host wall time incl. the plan's one stream sync"}
+        del M, rp, cl, vl
+    forms["conversion_f32"] = conv
+
     # -- group-size sweep (the paper's Table 4 on these matrices), x read path
     # on/off (the texture study of Sec. 4.3) and sliced ELLPACK (Sec. 3.4) --
     forms.update(measure_tables(mats, flush, stream))

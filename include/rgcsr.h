@@ -141,7 +141,8 @@ typedef struct {
 /*                      Synchronises `stream`.                              */
 /*   2. rgcsr_convert -- scatters values/columns (and slot_to_csr if non-   */
 /*                      NULL) into caller-allocated n_stored arrays.        */
-/*                      M->value_type must equal A->value_type.  Async.     */
+/*                      M->value_type must equal A->value_type; M is the   */
+/*                      descriptor rgcsr_plan filled for A.  Async.          */
 /* With M->row_perm set, both phases work on the rows in that order (plan   */
 /* returns RGCSR_ERR_BAD_PERM if it is not a permutation of [0, n_rows)).   */
 /* ----------------------------------------------------------------------- */

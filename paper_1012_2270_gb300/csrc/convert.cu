@@ -7,6 +7,8 @@
 // rgcsr_convert: one warp per group streams the group's slab
 //                [group_ptr[g], group_ptr[g+1]) with coalesced writes; slot
 //                e of the slab is (slot j, row t) = (e / R_g, e % R_g).
+//                Slabs over kBigSlab slots (groups holding very long rows)
+//                are written one warp per row instead.
 #include "common.cuh"
 
 namespace rgcsr {
@@ -31,6 +33,10 @@ __global__ void group_sizes_kernel(const int32_t *__restrict__ rl, int64_t n, in
     gp[g] = rows * (int64_t)kmax;
 }
 
+// Slabs larger than this go to scatter_big_kernel (one warp per row), so
+// that a group holding very long rows does not serialise one warp.
+constexpr int64_t kBigSlab = 32 * 256;
+
 // Raw element copy: V = uint64_t (f64) or uint32_t (f32) keeps bits exact.
 template <typename V>
 __global__ void __launch_bounds__(256)
@@ -45,6 +51,7 @@ scatter_kernel(RowPtr rp, const int32_t *__restrict__ col, const V *__restrict__
         const int R = (int)min((int64_t)G, n - first);
         const int64_t base = gp[g];
         const int64_t size = gp[g + 1] - base;
+        if (size > kBigSlab) continue;              // scatter_big_kernel's work
         // (j, t) of slab element e = lane, then advanced by 32 each step
         int64_t j = lane / R;
         int t = lane % R;
@@ -65,6 +72,46 @@ scatter_kernel(RowPtr rp, const int32_t *__restrict__ col, const V *__restrict__
             if (s2c) s2c[base + e] = src;
             t += 32;
             while (t >= R) { t -= R; ++j; }
+        }
+    }
+}
+
+// The slabs of big groups: one warp per stored row writes the row's K_g
+// slots j (lane j mod 32) -- its entries, then padding.
+template <typename V>
+__global__ void __launch_bounds__(256)
+scatter_big_kernel(RowPtr rp, const int32_t *__restrict__ col, const V *__restrict__ val,
+                   int64_t n, int32_t G, const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
+                   const int32_t *__restrict__ perm, V *__restrict__ out_val, int32_t *__restrict__ out_col,
+                   int64_t *__restrict__ s2c) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += warps) {
+        const int64_t g = row / G;
+        const int64_t base = gp[g];
+        const int64_t size = gp[g + 1] - base;
+        if (size <= kBigSlab) continue;
+        const int64_t first = g * G;
+        const int R = (int)min((int64_t)G, n - first);
+        const int64_t K = size / R;
+        const int t = (int)(row - first);
+        const int len = rl[row];
+        const int64_t src_row = perm ? (int64_t)perm[row] : row;   // checked by rgcsr_plan
+        const bool ok = src_row >= 0 && src_row < n;
+        const int64_t r0 = ok ? rp[src_row] : 0;
+        for (int64_t j = lane; j < K; j += 32) {
+            V v = 0;
+            int c = 0;
+            int64_t src = -1;
+            if (j < len && ok) {
+                src = r0 + j;
+                v = val[src];
+                c = col[src];
+            }
+            const int64_t e = base + j * R + t;
+            out_val[e] = v;
+            out_col[e] = c;
+            if (s2c) s2c[e] = src;
         }
     }
 }
@@ -138,16 +185,30 @@ RGCSR_API int rgcsr_convert(const rgcsr_csr *A, const rgcsr_matrix *M, rgcsr_str
     RowPtr rp{A->row_ptr, A->row_ptr_type == RGCSR_I64};
     int64_t blocks = ceil_div(M->n_groups, 8);
     if (blocks > 152 * 64) blocks = 152 * 64;
+    // big groups exist only if some row is longer than kBigSlab / G slots
+    const bool big = M->max_row_len * M->group_size > kBigSlab || M->max_row_len > kBigSlab;
+    int64_t big_blocks = ceil_div(M->n_rows, 8);
+    if (big_blocks > 152 * 64) big_blocks = 152 * 64;
     if (A->value_type == RGCSR_F64) {
         scatter_kernel<uint64_t><<<(unsigned)blocks, 256, 0, s>>>(
             rp, A->col_idx, static_cast<const uint64_t *>(A->values), M->n_rows, M->group_size,
             M->n_groups, M->group_ptr, M->row_lengths, M->row_perm, static_cast<uint64_t *>(M->values),
             M->columns, M->slot_to_csr);
+        if (big)
+            scatter_big_kernel<uint64_t><<<(unsigned)big_blocks, 256, 0, s>>>(
+                rp, A->col_idx, static_cast<const uint64_t *>(A->values), M->n_rows, M->group_size,
+                M->group_ptr, M->row_lengths, M->row_perm, static_cast<uint64_t *>(M->values), M->columns,
+                M->slot_to_csr);
     } else {
         scatter_kernel<uint32_t><<<(unsigned)blocks, 256, 0, s>>>(
             rp, A->col_idx, static_cast<const uint32_t *>(A->values), M->n_rows, M->group_size,
             M->n_groups, M->group_ptr, M->row_lengths, M->row_perm, static_cast<uint32_t *>(M->values),
             M->columns, M->slot_to_csr);
+        if (big)
+            scatter_big_kernel<uint32_t><<<(unsigned)big_blocks, 256, 0, s>>>(
+                rp, A->col_idx, static_cast<const uint32_t *>(A->values), M->n_rows, M->group_size,
+                M->group_ptr, M->row_lengths, M->row_perm, static_cast<uint32_t *>(M->values), M->columns,
+                M->slot_to_csr);
     }
     return launch_status();
 }

@@ -341,3 +341,24 @@ def test_sliced_ellpack_comparator(dtype, G):
     assert (np.abs(y[ok] - y_sell[ok]) <= TAU[dtype] * absy[ok]).all()
     if G > 1:
         assert np.isnan(y_sell).any() and not np.isnan(M.spmv(torch.from_numpy(x.astype(NP[dtype])).cuda()).cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("G,order", [(32, None), (32, "descending"), (8, None), (1, None)])
+def test_layout_with_big_groups(dtype, G, order):
+    # groups whose slab exceeds the per-group scatter's limit (rows of 300 to
+    # 9000 slots) are written one warp per row: still bit-exact
+    rng = np.random.default_rng(G)
+    n, m = 3000, 10000
+    L_ = rng.integers(0, 20, n)
+    L_[[5, 6, 40, 1000, 2999]] = [9000, 300, 4000, 260, 7000]
+    A = synth.random_csr(n, m, L_, seed=G)
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dtype]), A.n_cols, group_size=G, dtype=TT[dtype],
+                             keep_slot_map=True, row_order=order)
+    perm = oracle.descending_order(A.rowptr) if order else None
+    lay = oracle.rgcsr_layout(A.rowptr, A.col, A.val.astype(NP[dtype]), G, row_order=perm)
+    ui = np.uint64 if dtype == "f64" else np.uint32
+    assert np.array_equal(M.values.cpu().numpy().view(ui), lay.values.view(ui))
+    assert np.array_equal(M.columns.cpu().numpy(), lay.columns)
+    assert np.array_equal(M.slot_to_csr.cpu().numpy(), lay.slot_to_csr)
+    check_spmv(M, A, dtype, synth.uniform_vector(m, seed=1))
