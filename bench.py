@@ -623,6 +623,7 @@ def measure_forms(mats, cases, detail, dev, stream):
     # and G = 32 in descending row order with group tiles (the tiled kernels)
     Md = RgCSRMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32,
                               group_size=32, row_order="descending").tile_groups(64)
+    Hb = HybMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32)
     forms["spmm_b_f32"] = {"configs": {"lanes_per_row": "G=1, long-row schedule T=32 S=256",
                                        "tiles": "G=32, descending row order, group tiles C=64",
                                        "thread_per_row": f"G={Gm}"}}
@@ -636,9 +637,10 @@ def measure_forms(mats, cases, detail, dev, stream):
         t = ts[best]
         nb = roofline.spmm_bytes(b.n_rows, b.n_cols, b.nnz, (b.n_rows + GROUP - 1) // GROUP, 4, k)
         forms["spmm_b_f32"][f"k{k}"] = {"gbs": nb / t / 1e3, "gflops": 2 * b.nnz * k / t / 1e3, "us": t,
-                                        "best": best, "us_by_config": ts}
+                                        "best": best, "us_by_config": ts,
+                                        "hyb_us": time_flushed(lambda: Hb.spmm(X, out=Y), 5, flush, stream)}
         del X, Y
-    del Mb, Mt, Md
+    del Mb, Mt, Md, Hb
 
     # -- backward of Y = A X on (b), batch of 8 right-hand sides ---------------
     G = 32

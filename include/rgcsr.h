@@ -492,6 +492,16 @@ int hyb_convert(const rgcsr_csr *A, const hyb_matrix *H, void *workspace,
  * COO entries span several warps' tiles are combined with atomic adds, so
  * their last bits may differ between runs.  Async. */
 int hyb_spmv(const hyb_matrix *H, const void *x, void *y, rgcsr_stream_t stream);
+/* Y = A X for k right-hand sides: X row-major [n_cols x k] with row stride
+ * ldx >= k, Y row-major [n_rows x k] with stride ldy >= k, overwritten.  The
+ * ELL step writes Y (one thread per row, up to 8 columns per pass; 16-byte
+ * X loads when X and ldx are 16-byte aligned), the COO step adds the
+ * overflow with one lane per column (up to 32 per pass) and one atomic add
+ * per row run and column, so the last bits of rows with COO entries in
+ * several runs may differ between calls.  Element types as for hyb_spmv.
+ * Async. */
+int hyb_spmm(const hyb_matrix *H, int32_t k, const void *X, int64_t ldx, void *Y, int64_t ldy,
+             rgcsr_stream_t stream);
 
 /* ----------------------------------------------------------------------- */
 /* Misc                                                                     */

@@ -127,6 +127,7 @@ SIGNATURES = {
     "hyb_plan": (ctypes.c_int, [_PCSR, I32, _PH, P, SZ, P]),
     "hyb_convert": (ctypes.c_int, [_PCSR, _PH, P, SZ, P]),
     "hyb_spmv": (ctypes.c_int, [_PH, P, P, P]),
+    "hyb_spmm": (ctypes.c_int, [_PH, I32, P, I64, P, I64, P]),
     "rgcsr_get_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), P]),
     "rgcsr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rgcsr_version": (ctypes.c_int, []),

@@ -88,6 +88,28 @@ __device__ __forceinline__ int choose_split(int len, int w4) {
     return cand;
 }
 
+// KC consecutive entries of a row of X (read-only path); 16-byte vector
+// loads when VEC (the caller checked the alignment of the row pieces).
+template <typename A, int KC, bool VEC>
+__device__ __forceinline__ void load_xrow(const A *__restrict__ p, A (&o)[KC]) {
+    if constexpr (VEC && sizeof(A) == 4 && KC % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < KC / 4; ++q) {
+            const float4 t = __ldg(reinterpret_cast<const float4 *>(p) + q);
+            o[4 * q] = t.x; o[4 * q + 1] = t.y; o[4 * q + 2] = t.z; o[4 * q + 3] = t.w;
+        }
+    } else if constexpr (VEC && sizeof(A) == 8 && KC % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < KC / 2; ++q) {
+            const double2 t = __ldg(reinterpret_cast<const double2 *>(p) + q);
+            o[2 * q] = t.x; o[2 * q + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int w = 0; w < KC; ++w) o[w] = __ldg(p + w);
+    }
+}
+
 // Output index of stored row `row`: the CSR row it holds under a row order
 // (rgcsr_matrix::row_perm), or the row itself without one.
 __device__ __forceinline__ int64_t out_row(const int32_t *perm, int64_t row) {

@@ -17,26 +17,6 @@ namespace {
 
 constexpr int kThreadsT = 256;
 
-template <typename A, int KC, bool VEC>
-__device__ __forceinline__ void load_row(const A *__restrict__ p, A (&o)[KC]) {
-    if constexpr (VEC && sizeof(A) == 4 && KC % 4 == 0) {
-#pragma unroll
-        for (int q = 0; q < KC / 4; ++q) {
-            const float4 t = __ldg(reinterpret_cast<const float4 *>(p) + q);
-            o[4 * q] = t.x; o[4 * q + 1] = t.y; o[4 * q + 2] = t.z; o[4 * q + 3] = t.w;
-        }
-    } else if constexpr (VEC && sizeof(A) == 8 && KC % 2 == 0) {
-#pragma unroll
-        for (int q = 0; q < KC / 2; ++q) {
-            const double2 t = __ldg(reinterpret_cast<const double2 *>(p) + q);
-            o[2 * q] = t.x; o[2 * q + 1] = t.y;
-        }
-    } else {
-#pragma unroll
-        for (int w = 0; w < KC; ++w) o[w] = __ldg(p + w);
-    }
-}
-
 template <typename V, int KC, bool VEC>
 __global__ void __launch_bounds__(kThreadsT, 4)
 rgcsr_spmm_tiles_kernel(int64_t n, int32_t G, int32_t C, int64_t n_groups, int64_t n_tasks,
@@ -88,7 +68,7 @@ rgcsr_spmm_tiles_kernel(int64_t n, int32_t G, int32_t C, int64_t n_groups, int64
             for (int u = 0; u < U; ++u) {
                 if (j + u < jend) {
                     A xw[KC];
-                    load_row<A, KC, VEC>(X + (int64_t)c[u] * ldx, xw);
+                    load_xrow<A, KC, VEC>(X + (int64_t)c[u] * ldx, xw);
 #pragma unroll
                     for (int w = 0; w < KC; ++w) acc[w] = fma(v[u], xw[w], acc[w]);
                 }

@@ -386,5 +386,17 @@ class HybMatrix:
         L.call("hyb_spmv", ctypes.byref(self.s), _ptr(x), _ptr(y), _stream_ptr(stream))
         return y
 
+    def spmm(self, X: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Y = A X for X of shape [n_cols, k] with unit column stride."""
+        if X.dim() != 2 or X.shape[0] != self.s.n_cols or X.dtype != self.x_dtype or X.stride(1) != 1:
+            raise ValueError(f"X must be [{self.s.n_cols}, k] {self.x_dtype} with unit column stride")
+        k = X.shape[1]
+        Y = out if out is not None else torch.empty(self.s.n_rows, k, dtype=self.x_dtype, device=X.device)
+        if Y.shape != (self.s.n_rows, k) or Y.stride(1) != 1:
+            raise ValueError("out must be [n_rows, k] with unit column stride")
+        L.call("hyb_spmm", ctypes.byref(self.s), k, _ptr(X), max(X.stride(0), k), _ptr(Y), max(Y.stride(0), k),
+               _stream_ptr(stream))
+        return Y
+
     def __matmul__(self, x):
         return self.spmv(x)

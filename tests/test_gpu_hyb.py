@@ -65,3 +65,30 @@ def test_hyb_full_size(name):
         y = H.spmv(torch.from_numpy(x.astype(NP[dtype])).cuda()).cpu().numpy()
         y_ref, absy = oracle.csr_spmv(A.rowptr, A.col, rounded_values(A.val, dtype), rounded_values(x, dtype))
         assert_within_bound(y, y_ref, absy, TAU[dtype], f"hyb {name} {dtype}")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("width", [-1, 0, 3])
+@pytest.mark.parametrize("k", [1, 3, 4, 8, 13, 32, 40])
+def test_hyb_spmm(dtype, width, k):
+    rng = np.random.default_rng(k + width)
+    Ls = rng.integers(0, 30, 1200)
+    Ls[[4, 600]] = [2000, 700]
+    A = synth.random_csr(1200, 2500, Ls, seed=k)
+    H = HybMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dtype]), A.n_cols, ell_width=width, dtype=TT[dtype])
+    X = synth.uniform_matrix(A.n_cols, k, seed=k).astype(NP[dtype])
+    Y = H.spmm(torch.from_numpy(X).cuda()).cpu().numpy()
+    Y_ref, aY = oracle.csr_spmm(A.rowptr, A.col, rounded_values(A.val, dtype), X.astype(np.float64))
+    assert_within_bound(Y.ravel(), Y_ref.ravel(), aY.ravel(), TAU[dtype], f"hyb spmm k={k} K1={H.ell_width}")
+
+
+def test_hyb_spmm_strided_and_full_size_b():
+    A = synth.workload_b()
+    H = HybMatrix.from_csr(A.rowptr, A.col, A.val.astype(np.float32), A.n_cols, dtype=torch.float32)
+    wide = synth.uniform_matrix(A.n_cols, 10, seed=1).astype(np.float32)
+    Xd = torch.from_numpy(wide).cuda()[:, 1:9]                        # k = 8, row stride 10
+    Yw = torch.full((A.n_rows, 10), 2.0, device="cuda")
+    H.spmm(Xd, out=Yw[:, 1:9])
+    assert (Yw[:, 0] == 2.0).all() and (Yw[:, 9] == 2.0).all()
+    Y_ref, aY = oracle.csr_spmm(A.rowptr, A.col, rounded_values(A.val, "f32"), wide[:, 1:9].astype(np.float64))
+    assert_within_bound(Yw[:, 1:9].cpu().numpy().ravel(), Y_ref.ravel(), aY.ravel(), TAU["f32"], "hyb spmm b")
