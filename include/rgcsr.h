@@ -411,6 +411,14 @@ int rgcsr_compose_index(const int64_t *outer, const int64_t *inner, int64_t n, i
 int rgcsr_sampled_dot(int64_t nnz, int32_t k, const int32_t *row_index, const int32_t *col_idx,
                       const void *G, int64_t ldg, const void *X, int64_t ldx, void *out,
                       int32_t value_type, rgcsr_stream_t stream);
+/* The same value gradient read straight from an RgCSR matrix of A:
+ * dval[slot_to_csr[s]] = sum_{b<k} G[r_s*ldg + b] * X[columns[s]*ldx + b]
+ * for every stored slot s that holds an entry (padding, slot_to_csr < 0, is
+ * skipped), r_s being the slot's CSR row (through row_perm if set); dval is
+ * in the CSR's entry order (nnz elements of M's value type, F64 or F32).
+ * Needs M->slot_to_csr.  Async. */
+int rgcsr_spmv_bwd_values(const rgcsr_matrix *M, int32_t k, const void *G, int64_t ldg, const void *X,
+                          int64_t ldx, void *dval, rgcsr_stream_t stream);
 
 /* ----------------------------------------------------------------------- */
 /* Vector kernels and solvers around the SpMV (Sec. 1: a Krylov iteration   */

@@ -111,6 +111,7 @@ SIGNATURES = {
     "rgcsr_gather_values": (ctypes.c_int, [_PM, P, P, P]),
     "rgcsr_compose_index": (ctypes.c_int, [P, P, I64, P, P]),
     "rgcsr_sampled_dot": (ctypes.c_int, [I64, I32, P, P, P, I64, P, I64, P, I32, P]),
+    "rgcsr_spmv_bwd_values": (ctypes.c_int, [_PM, I32, P, I64, P, I64, P, P]),
     "rgcsr_batch_tasks": (ctypes.c_int, [_PBD, I32, P, I64, ctypes.POINTER(I64)]),
     "rgcsr_spmv_batched": (ctypes.c_int, [_PB, P, P, P]),
     "rgcsr_dot_workspace_bytes": (SZ, []),

@@ -209,6 +209,33 @@ __global__ void descending_keys_kernel(RowPtr rp, int64_t n, uint32_t mask, uint
     keys[i] = mask - (uint32_t)len;
 }
 
+// dval[slot_to_csr[e]] = sum_b G[row(e), b] X[col[e], b] over a group's slab
+// (one warp per group, slab elements e = (slot j, row t) as in the layout).
+template <typename T>
+__global__ void bwd_values_kernel(int64_t n, int32_t G, int64_t n_groups, const int64_t *__restrict__ gp,
+                                  const int32_t *__restrict__ col, const int64_t *__restrict__ s2c,
+                                  const int32_t *__restrict__ perm, int k, const T *__restrict__ Gy, int64_t ldg,
+                                  const T *__restrict__ X, int64_t ldx, T *__restrict__ dval) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_groups; g += warps) {
+        const int64_t first = g * G;
+        const int R = (int)min((int64_t)G, n - first);
+        const int64_t base = gp[g];
+        const int64_t size = gp[g + 1] - base;
+        for (int64_t e = lane; e < size; e += 32) {
+            const int64_t p = s2c[base + e];
+            if (p < 0) continue;                              // padding
+            const int64_t row = first + (int)(e % R);
+            const T *gr = Gy + out_row(perm, row) * ldg;
+            const T *xr = X + (int64_t)col[base + e] * ldx;
+            T acc = 0;
+            for (int b = 0; b < k; ++b) acc = fma(__ldg(gr + b), __ldg(xr + b), acc);
+            dval[p] = acc;
+        }
+    }
+}
+
 unsigned grid_for(int64_t n, int threads) {
     int64_t b = ceil_div(n, threads);
     if (b > 152 * 64) b = 152 * 64;
@@ -355,4 +382,26 @@ RGCSR_API int rgcsr_descending_order(const rgcsr_csr *A, int32_t *row_perm, void
     if ((st = radix_sort_indices(keys, n, bits, b, &skeys, &sidx, s)) != RGCSR_OK) return st;
     RGCSR_CUDA_TRY(cudaMemcpyAsync(row_perm, sidx, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     return RGCSR_OK;
+}
+
+RGCSR_API int rgcsr_spmv_bwd_values(const rgcsr_matrix *M, int32_t k, const void *G, int64_t ldg, const void *X,
+                                    int64_t ldx, void *dval, rgcsr_stream_t stream) {
+    if (!M || M->n_rows < 0 || M->group_size < 1 || k < 0 || ldg < k || ldx < k) return RGCSR_ERR_INVALID_ARG;
+    if (M->value_type != RGCSR_F64 && M->value_type != RGCSR_F32) return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    if (M->n_groups != ceil_div(M->n_rows, M->group_size)) return RGCSR_ERR_INVALID_ARG;
+    if (M->n_stored == 0 || M->nnz == 0) return RGCSR_OK;
+    if (!M->group_ptr || !M->columns || !M->slot_to_csr || !dval || (k > 0 && (!G || !X)))
+        return RGCSR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned g = grid_for(M->n_groups * 32, 256);
+    if (M->value_type == RGCSR_F64)
+        bwd_values_kernel<double><<<g, 256, 0, s>>>(M->n_rows, M->group_size, M->n_groups, M->group_ptr, M->columns,
+                                                    M->slot_to_csr, M->row_perm, k, static_cast<const double *>(G),
+                                                    ldg, static_cast<const double *>(X), ldx,
+                                                    static_cast<double *>(dval));
+    else
+        bwd_values_kernel<float><<<g, 256, 0, s>>>(M->n_rows, M->group_size, M->n_groups, M->group_ptr, M->columns,
+                                                   M->slot_to_csr, M->row_perm, k, static_cast<const float *>(G),
+                                                   ldg, static_cast<const float *>(X), ldx, static_cast<float *>(dval));
+    return launch_status();
 }

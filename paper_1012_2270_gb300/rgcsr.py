@@ -309,6 +309,23 @@ class RgCSRMatrix:
                0 if part is None else part.numel(), _stream_ptr(stream))
         return Y
 
+    def value_grad(self, Gy: torch.Tensor, X: torch.Tensor, stream=None) -> torch.Tensor:
+        """d/d(values) of sum(Gy * (A X)), in the CSR's entry order:
+        dval_p = sum_b Gy[row_p, b] X[col_p, b] (rgcsr_spmv_bwd_values).
+        Gy [n_rows, k] and X [n_cols, k] (or vectors); needs keep_slot_map."""
+        if self.slot_to_csr is None:
+            raise ValueError("value_grad needs the slot map (from_csr(..., keep_slot_map=True))")
+        G2, X2 = Gy.reshape(self.s.n_rows, -1), X.reshape(self.s.n_cols, -1)
+        if G2.dtype != self.x_dtype or X2.dtype != self.x_dtype or G2.shape[1] != X2.shape[1]:
+            raise ValueError("Gy and X must share the matrix's vector type and column count")
+        if G2.stride(-1) != 1 or X2.stride(-1) != 1:
+            raise ValueError("Gy and X need unit column stride")
+        k = G2.shape[1]
+        out = torch.empty(self.s.nnz, dtype=self.x_dtype, device=X.device)
+        L.call("rgcsr_spmv_bwd_values", ctypes.byref(self.s), k, _ptr(G2), max(G2.stride(0), k), _ptr(X2),
+               max(X2.stride(0), k), _ptr(out), _stream_ptr(stream))
+        return out
+
     def spmv_host(self, x_host: torch.Tensor, y_host: torch.Tensor, x_dev: torch.Tensor,
                   y_dev: torch.Tensor, kernel: int = L.KERNEL_AUTO, variant: int = 0, stream=None) -> None:
         """Host-to-host SpMV through caller-provided device staging buffers

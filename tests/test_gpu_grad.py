@@ -14,7 +14,7 @@ from helpers import TAU, assert_within_bound, rounded_values
 from paper_1012_2270_gb300 import synth
 from paper_1012_2270_gb300 import _lib as L
 from paper_1012_2270_gb300.autograd import SparseOperator, spmm
-from paper_1012_2270_gb300.rgcsr import _ptr, csr_struct, _stream_ptr
+from paper_1012_2270_gb300.rgcsr import RgCSRMatrix, _ptr, csr_struct, _stream_ptr
 
 pytestmark = pytest.mark.gpu
 
@@ -165,3 +165,23 @@ def test_grads_full_size_b_batch8():
     A = synth.workload_b()
     check_grads(A, "f32", 8)
     check_grads(A, "f32", 8, row_order="descending", tiles=64)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("G,order,k", [(32, None, 1), (32, "descending", 5), (7, None, 8), (1, None, 3)])
+def test_bwd_values_from_rgcsr(dtype, G, order, k):
+    # rgcsr_spmv_bwd_values: the value gradient straight from the RgCSR slabs
+    rng = np.random.default_rng(k + G)
+    Ls = rng.integers(0, 25, 900)
+    Ls[[3, 500]] = [700, 260]
+    A = synth.random_csr(900, 1100, Ls, seed=k)
+    vals = rounded_values(A.val, dtype)
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dtype]), A.n_cols, group_size=G, dtype=TT[dtype],
+                             keep_slot_map=True, row_order=order)
+    X = synth.uniform_matrix(A.n_cols, k, seed=1).astype(NP[dtype]).astype(np.float64)
+    Gy = synth.uniform_matrix(A.n_rows, k, seed=2).astype(NP[dtype]).astype(np.float64)
+    dval = M.value_grad(torch.tensor(Gy, dtype=TT[dtype], device="cuda"),
+                        torch.tensor(X, dtype=TT[dtype], device="cuda")).double().cpu().numpy()
+    _, dval_ref = oracle.spmm_grads(A.rowptr, A.col, vals, X, Gy, A.n_cols)
+    _, dval_abs = abs_bounds(A, vals, X, Gy)
+    assert_within_bound(dval, dval_ref, dval_abs, TAU[dtype], f"bwd values G={G} {order}")
