@@ -51,3 +51,14 @@ def test_batch_tasks_host_function():
     small = np.empty(2, np.int32)
     assert lib.rgcsr_batch_tasks(descs, len(sizes), small.ctypes.data_as(ctypes.c_void_p), 1,
                                  ctypes.byref(cnt)) == L.RGCSR_ERR_WORKSPACE
+
+
+def test_heuristic_configuration():
+    import torch
+    from paper_1012_2270_gb300 import autotune
+    lap = synth.laplacian_3d(12)
+    assert autotune.heuristic(lap.rowptr) == {"group_size": 32, "kernel": 0}
+    pl = synth.power_law(20_000, seed=1)
+    cfg = autotune.heuristic(pl.rowptr, torch.float64)
+    assert cfg["row_order"] == "descending" and cfg["tiles"] == [64, 2]
+    assert autotune.heuristic(pl.rowptr, torch.float32)["tiles"] == [64, 3]
