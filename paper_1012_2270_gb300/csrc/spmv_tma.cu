@@ -256,8 +256,10 @@ int launch_tma_t(const rgcsr_matrix *M, const T *x, T *y, int variant, cudaStrea
 
 bool tma_eligible(const rgcsr_matrix *M) {
     auto aligned = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    // (the ring's stage records hold group indices as int)
     return M->group_size == 32 && (M->value_type == RGCSR_F32 || M->value_type == RGCSR_F64) &&
-           M->n_rows >= 32 && aligned(M->values) && aligned(M->columns) && aligned(M->row_lengths);
+           M->n_rows >= 32 && M->n_groups <= (int64_t)INT32_MAX && aligned(M->values) &&
+           aligned(M->columns) && aligned(M->row_lengths);
 }
 
 int launch_spmv_tma(const rgcsr_matrix *M, const void *x, void *y, int variant, cudaStream_t s) {
