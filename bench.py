@@ -383,6 +383,19 @@ def run_ours(args):
                             "artificial_zero_pct": c["pad_pct"], "kernel": c["kernel"],
                             "config": {k: v for k, v in c["config"].items() if k != "us"}}
 
+    # ---- the same bytes as one plain device read (torch.sum over a buffer
+    # of the case's algorithmic bytes, L2 flushed): what a streaming kernel
+    # of this size reaches, launch ramp and tail included ----
+    flush_r = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    for c in cases:
+        buf = torch.ones(c["bytes"] // 4, dtype=torch.float32, device=dev)
+        r_us = time_flushed(lambda: buf.sum(), 10, flush_r, stream)
+        d = detail[c["key"]]
+        d["same_size_read_us"] = r_us
+        d["frac_of_same_size_read"] = r_us / d["us"]
+        del buf
+    del flush_r
+
     # ---- roofline of the dominant kernel ----
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(peaks_path):
