@@ -384,9 +384,9 @@ def run_ours(args):
                             "config": {k: v for k, v in c["config"].items() if k != "us"}}
 
     # ---- the same bytes as one plain device read (torch.sum over a buffer
-    # of the case's algorithmic bytes, L2 flushed): what a streaming kernel
-    # of this size reaches, launch ramp and tail included ----
-    flush_r = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    # of the case's algorithmic bytes, L2 flushed by a read): what a
+    # streaming kernel of this size reaches, launch ramp and tail included ----
+    flush_r = torch.ones(64 << 20, dtype=torch.float32, device=dev)
     for c in cases:
         buf = torch.ones(c["bytes"] // 4, dtype=torch.float32, device=dev)
         r_us = time_flushed(lambda: buf.sum(), 10, flush_r, stream)
@@ -537,13 +537,15 @@ def time_rotating(fns, reps, stream):
 
 
 def time_flushed(fn, reps, flush, stream):
-    """Median microseconds of fn with L2 flushed (a 256 MB write) before each call."""
+    """Median microseconds of fn with L2 flushed (a 256 MB read, which leaves
+    no dirty lines behind) before each call."""
     import torch
+    from paper_1012_2270_gb300 import autotune
     fn()
     torch.cuda.synchronize()
     ts = []
     for _ in range(reps):
-        flush.zero_()
+        autotune.flush_l2(flush)
         e0, e1 = _ev()
         e0.record(stream)
         fn()
@@ -572,7 +574,7 @@ def measure_forms(mats, cases, detail, dev, stream):
     from paper_1012_2270_gb300.rgcsr import HybMatrix, RgCSRMatrix
 
     forms = {}
-    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    flush = torch.ones(64 << 20, dtype=torch.float32, device=dev)
     by = {c["key"]: c for c in cases}
     TT = {"f32": torch.float32, "f64": torch.float64}
 
