@@ -383,13 +383,15 @@ def run_ours(args):
                             "artificial_zero_pct": c["pad_pct"], "kernel": c["kernel"],
                             "config": {k: v for k, v in c["config"].items() if k != "us"}}
 
-    # ---- the same bytes as one plain device read (torch.sum over a buffer
-    # of the case's algorithmic bytes, L2 flushed by a read): what a
-    # streaming kernel of this size reaches, launch ramp and tail included ----
+    # ---- the same bytes as one plain device read (the library's streaming
+    # read of a buffer of the case's algorithmic bytes, L2 flushed by a
+    # read): what a streaming kernel of this size reaches, launch ramp and
+    # tail included ----
+    from paper_1012_2270_gb300.rgcsr import stream_read
     flush_r = torch.ones(64 << 20, dtype=torch.float32, device=dev)
     for c in cases:
-        buf = torch.ones(c["bytes"] // 4, dtype=torch.float32, device=dev)
-        r_us = time_flushed(lambda: buf.sum(), 10, flush_r, stream)
+        buf = torch.ones(c["bytes"] // 16 * 4, dtype=torch.float32, device=dev)
+        r_us = time_flushed(lambda: stream_read(buf, stream), 10, flush_r, stream)
         d = detail[c["key"]]
         d["same_size_read_us"] = r_us
         d["frac_of_same_size_read"] = r_us / d["us"]

@@ -443,6 +443,14 @@ int rgcsr_diag_scale(int64_t n, double alpha, const void *d, const void *x, void
 /* dst = src converted between RGCSR_F64 and RGCSR_F32 (round to nearest). */
 int rgcsr_convert_vector(int64_t n, const void *src, int32_t src_type, void *dst, int32_t dst_type,
                          rgcsr_stream_t stream);
+/* Reads `bytes` bytes at data (device, 16-byte aligned, bytes a multiple of
+ * 16) with 16-byte streaming loads on 8 CTAs of 256 threads per SM, and
+ * writes nothing (sink, one device float, is written only if the float sum
+ * of the data is exactly -1234567).  Not part of the method: it measures
+ * what a plain read of a given size reaches on this GPU, the reference for
+ * a memory-bound kernel that moves the same bytes.  RGCSR_ERR_INVALID_ARG
+ * for an unaligned pointer or size. */
+int rgcsr_stream_read(const void *data, int64_t bytes, void *sink, rgcsr_stream_t stream);
 
 /* Conjugate gradients for a symmetric positive definite square A, from
  * x = 0, stopping when ||r|| <= rel_tol ||b|| (the recurrence residual,

@@ -76,6 +76,21 @@ unsigned vec_grid(int64_t n) {
     return (unsigned)(b > 0 ? b : 1);
 }
 
+// A plain streaming read (16-byte loads, evict-first, grid-stride): the
+// bandwidth reference for a kernel that moves the same bytes.  The sum is
+// stored only if it equals a value the caller's data will not produce, so
+// the loads cannot be dropped.
+__global__ void __launch_bounds__(256)
+stream_read_kernel(const float4 *__restrict__ p, int64_t n16, float *__restrict__ sink) {
+    float s = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+        const float4 v = __ldcs(p + i);
+        s += (v.x + v.y) + (v.z + v.w);
+    }
+    if (s == -1234567.0f) *sink = s;
+}
+
 }  // namespace
 
 int dot_device(int64_t n, const void *x, const void *y, double *out, double *partials, int value_type,
@@ -176,4 +191,18 @@ RGCSR_API int rgcsr_convert_vector(int64_t n, const void *src, int32_t src_type,
                                    rgcsr_stream_t stream) {
     if (n < 0 || (n > 0 && (!src || !dst))) return RGCSR_ERR_INVALID_ARG;
     return convert_device(n, src, src_type, dst, dst_type, (cudaStream_t)stream);
+}
+
+RGCSR_API int rgcsr_stream_read(const void *data, int64_t bytes, void *sink, rgcsr_stream_t stream) {
+    if (bytes < 0 || bytes % 16 != 0 || (bytes > 0 && (!data || !sink)) || ((uintptr_t)data & 15) != 0)
+        return RGCSR_ERR_INVALID_ARG;
+    if (bytes == 0) return RGCSR_OK;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t n16 = bytes / 16;
+    int64_t grid = (int64_t)sms * 8;                     // 8 CTAs of 256 threads per SM
+    if (ceil_div(n16, (int64_t)256) < grid) grid = ceil_div(n16, (int64_t)256);
+    stream_read_kernel<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(static_cast<const float4 *>(data), n16,
+                                                                         static_cast<float *>(sink));
+    return launch_status();
 }

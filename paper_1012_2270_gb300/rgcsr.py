@@ -26,6 +26,21 @@ def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr() if t is not None and t.numel() > 0 else 0)
 
 
+def stream_read(buf: torch.Tensor, stream=None) -> None:
+    """Reads the bytes of `buf` (contiguous, CUDA, a multiple of 16 bytes)
+    with the library's plain streaming-read kernel: the bandwidth reference
+    for a memory-bound kernel that moves as many bytes."""
+    if not (buf.is_cuda and buf.is_contiguous()):
+        raise ValueError("stream_read needs a contiguous CUDA tensor")
+    sink = _READ_SINKS.get(buf.device)
+    if sink is None:                 # allocated once, so a timed call launches only the read
+        sink = _READ_SINKS[buf.device] = torch.zeros(1, dtype=torch.float32, device=buf.device)
+    L.call("rgcsr_stream_read", _ptr(buf), buf.numel() * buf.element_size(), _ptr(sink), _stream_ptr(stream))
+
+
+_READ_SINKS: dict = {}
+
+
 def _dev(a, dtype=None, device="cuda") -> torch.Tensor:
     t = torch.as_tensor(np.ascontiguousarray(a)) if isinstance(a, np.ndarray) else a
     if dtype is not None and t.dtype != dtype:

@@ -57,6 +57,23 @@ def test_vector_kernels():
     assert np.array_equal(f.cpu().numpy(), x.astype(np.float32))
 
 
+def test_stream_read_probe():
+    # the bandwidth probe reads and writes nothing; its host checks reject
+    # unaligned pointers and sizes before any launch
+    from paper_1012_2270_gb300.rgcsr import stream_read
+    buf = torch.arange(1 << 20, dtype=torch.float32, device="cuda")
+    sink = torch.full((1,), 7.0, device="cuda")
+    for nbytes in (0, 16, 4096, 4 << 20):
+        L.call("rgcsr_stream_read", _ptr(buf), nbytes, _ptr(sink), _stream_ptr())
+    stream_read(buf)
+    torch.cuda.synchronize()
+    assert float(sink) == 7.0
+    assert torch.equal(buf, torch.arange(1 << 20, dtype=torch.float32, device="cuda"))
+    lib = L.lib()
+    for args in ((_ptr(buf), 20), (ctypes.c_void_p(buf.data_ptr() + 4), 16), (_ptr(buf), -16)):
+        assert lib.rgcsr_stream_read(*args, _ptr(sink), _stream_ptr()) == L.RGCSR_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_cg_against_oracle(dtype):
     A = synth.laplacian_3d(20)
