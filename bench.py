@@ -116,7 +116,7 @@ def kernel_name(cfg, M, A, dt):
     if "long_rows" in cfg:
         return f"rgcsr_spmv_split+segments<{t}>"
     k = cfg.get("kernel", 0)
-    if k == 4 and cfg.get("variant", 0) in (1, 2):
+    if k == 4 and cfg.get("variant", 0) in (1, 2, 4):
         return f"rgcsr_spmv_vec<{t}>"
     if k == 0:
         n = A.n_rows
@@ -617,7 +617,7 @@ def measure_forms(mats, cases, detail, dev, stream):
             # kernel: the default, or (G = 32, no schedule) 16-byte loads, whichever is faster here
             kws = [{}]
             if Q.group_size == 32 and Q._tiles is None and Q._long is None:
-                kws += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2)]
+                kws += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4)]
             kw = min(kws, key=lambda k: autotune._time(lambda: Q.spmv(c32["x"], out=yq, **k), 8, flush))
             quant.append((name, fmt, Q, c32["x"], yq, A, kw))
     us = time_rotating([lambda q=q: q[2].spmv(q[3], out=q[4], **q[6]) for q in quant], 30, stream)

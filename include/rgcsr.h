@@ -125,11 +125,13 @@ typedef struct {
                                    relative to one thread-per-row step, x 4        */
     int32_t variant;            /* configuration of the chosen kernel, 0 = default:
                                    TMA: 0..3 = (slot-rows per chunk, ring stages)
-                                   (8,2), (8,4), (16,2), (4,4); LEAN: 1, 2 = G =
-                                   32 with vector loads: a lane owns 4 rows (F64:
-                                   2) of a group, 2 slot-rows in flight (1), or
-                                   2 rows, 4 slot-rows in flight (2); 16-byte
-                                   aligned values and columns; other kernels: 0 */
+                                   (8,2), (8,4), (16,2), (4,4); LEAN: 1, 2, 4 =
+                                   G = 32 with vector loads: a lane owns 4 rows
+                                   (F64: 2) of a group, 2 slot-rows in flight
+                                   (1), or 2 rows, 4 slot-rows in flight (2), or
+                                   4 rows (F64: 2), 4 slot-rows in flight (4);
+                                   16-byte aligned values and columns; other
+                                   kernels: 0                                     */
 } rgcsr_launch;
 
 /* ----------------------------------------------------------------------- */

@@ -306,20 +306,24 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
     const int32_t G = M->group_size;
     const float *scale = M->row_scale;
     if (VT<V>::scaled && !scale) return RGCSR_ERR_INVALID_ARG;
-    if (kernel == RGCSR_KERNEL_LEAN && L && (L->variant == 1 || L->variant == 2)) {
+    if (kernel == RGCSR_KERNEL_LEAN && L && (L->variant == 1 || L->variant == 2 || L->variant == 4)) {
         auto aligned = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
         if (G != 32 || !aligned(val) || !aligned(M->columns)) return RGCSR_ERR_INVALID_ARG;
         // variant 1: 4 rows per lane (FP64: 2), 2 slot-rows in flight;
-        // variant 2: 2 rows per lane, 4 slot-rows in flight
+        // variant 2: 2 rows per lane, 4 slot-rows in flight;
+        // variant 4: 4 rows per lane (FP64: 2), 4 slot-rows in flight
         constexpr int rpl1 = sizeof(V) == 8 ? 2 : 4;
-        const int lpg = L->variant == 1 ? 32 / rpl1 : 16;
+        const int lpg = L->variant == 2 ? 16 : 32 / rpl1;
         const int64_t blocks = ceil_div(M->n_groups * lpg, (int64_t)kDefaultThreads);
         if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
         if (L->variant == 1)
             rgcsr_spmv_vec<V, rpl1, 2, 5><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
                 n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
-        else
+        else if (L->variant == 2)
             rgcsr_spmv_vec<V, 2, 4, 5><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
+                n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
+        else
+            rgcsr_spmv_vec<V, rpl1, 4, 4><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
                 n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
         return launch_status();
     }

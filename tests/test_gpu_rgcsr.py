@@ -19,7 +19,7 @@ TT = {"f32": torch.float32, "f64": torch.float64}
 VARIANTS = [dict(), dict(kernel=L.KERNEL_PAPER), dict(kernel=L.KERNEL_SPLIT, x_load=L.XLOAD_PLAIN),
             dict(kernel=L.KERNEL_SPLIT, block_threads=64, split_weight=4), dict(kernel=L.KERNEL_LEAN)]
 VARIANTS += [dict(kernel=L.KERNEL_TMA, variant=v) for v in range(0, 4)]
-VARIANTS += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2)]   # vector loads, G = 32
+VARIANTS += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4)]   # vector loads, G = 32
 
 
 def variants(M):
@@ -28,7 +28,7 @@ def variants(M):
     for kw in VARIANTS:
         if kw.get("kernel") == L.KERNEL_TMA and (M.group_size != 32 or M.shape[0] < 32):
             continue
-        if kw.get("kernel") == L.KERNEL_LEAN and kw.get("variant") in (1, 2) and M.group_size != 32:
+        if kw.get("kernel") == L.KERNEL_LEAN and kw.get("variant") in (1, 2, 4) and M.group_size != 32:
             continue
         if kw.get("kernel") == L.KERNEL_PAPER and M.group_size > 1024:
             continue
@@ -221,7 +221,7 @@ def test_full_size_spmv(name, dtype):
     if name != "b":
         check_spmv(M, A, dtype, x, kernel=L.KERNEL_SPLIT)
         check_spmv(M, A, dtype, x, kernel=L.KERNEL_LEAN)
-        for v in (1, 2):                                    # vector loads
+        for v in (1, 2, 4):                                 # vector loads
             check_spmv(M, A, dtype, x, kernel=L.KERNEL_LEAN, variant=v)
         for v in range(4):
             check_spmv(M, A, dtype, x, kernel=L.KERNEL_TMA, variant=v)
@@ -313,7 +313,8 @@ def test_unknown_kernel_variants_rejected():
     A = ragged(300, 200, seed=2)
     M = to_gpu_matrix(A, "f32", 32)
     x = torch.zeros(A.n_cols, dtype=torch.float32, device="cuda")
-    for kw in (dict(kernel=L.KERNEL_LEAN, variant=3), dict(kernel=L.KERNEL_TMA, variant=4),
+    for kw in (dict(kernel=L.KERNEL_LEAN, variant=3), dict(kernel=L.KERNEL_LEAN, variant=5),
+               dict(kernel=L.KERNEL_TMA, variant=4),
                dict(kernel=L.KERNEL_LEAN, variant=-1)):
         with pytest.raises(L.RgCSRError) as e:
             M.spmv(x, **kw)
