@@ -419,6 +419,11 @@ def run_ours(args):
             "peak_source": peak_src,
             "bytes_per_launch": d["bytes"] / d["launches"], "avg_launch_us": 1e3 * d["ms"] / d["launches"]}
     dom_cases = [(c, ms) for c, ms in zip(cases, per_case_ms) if c["kernel"] == dom]
+    # the same bytes as plain reads (launch ramp and tail included): the
+    # ceiling a memory-bound kernel of this size can reach on this GPU
+    read_us = sum(detail[c["key"]]["same_size_read_us"] for c, _ in dom_cases)
+    read_gbs = sum(c["bytes"] for c, _ in dom_cases) / (read_us * 1e-6) / 1e9
+    roof["same_size_read"] = {"gbs": read_gbs, "frac": achieved / read_gbs, "frac_of_peak": read_gbs / peak_hbm}
     if all(c["name"] == "b" for c, _ in dom_cases):
         # random columns: every x gather is its own L2 request (1.15-1.26
         # requests per non-zero measured with ncu, the streamed lines
