@@ -397,6 +397,22 @@ def run_ours(args):
         d["frac_of_same_size_read"] = r_us / d["us"]
         del buf
     del flush_r
+    # ---- FP64 FMA rate (the library's probe): an FP64 SpMV does one FMA per
+    # non-zero, and on this GPU that rate is low enough to be a second floor ----
+    from paper_1012_2270_gb300.rgcsr import fp64_fma_probe
+    fp64_fma_probe(64, stream)
+    fma_t = []
+    for _ in range(3):
+        e0, e1 = _ev()
+        e0.record(stream)
+        n_fma = fp64_fma_probe(1024, stream)
+        e1.record(stream)
+        e1.synchronize()
+        fma_t.append(e0.elapsed_time(e1) * 1e-3)
+    fma_rate = n_fma / statistics.median(fma_t)                      # FMA/s
+    for c in cases:
+        if c["dt"] == "f64":
+            detail[c["key"]]["fp64_fma_floor_us"] = 1e6 * c["nnz"] / fma_rate
 
     # ---- roofline of the dominant kernel ----
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -424,6 +440,15 @@ def run_ours(args):
     read_us = sum(detail[c["key"]]["same_size_read_us"] for c, _ in dom_cases)
     read_gbs = sum(c["bytes"] for c, _ in dom_cases) / (read_us * 1e-6) / 1e9
     roof["same_size_read"] = {"gbs": read_gbs, "frac": achieved / read_gbs, "frac_of_peak": read_gbs / peak_hbm}
+    if all(c["dt"] == "f64" for c, _ in dom_cases):
+        # one FP64 FMA per non-zero: its floor next to the HBM floor
+        nnz = sum(c["nnz"] for c, _ in dom_cases)
+        t_us = 1e3 * sum(ms for _, ms in dom_cases)
+        roof["fp64_fma"] = {
+            "probe_tflops": 2 * fma_rate / 1e12, "nominal_tflops": roofline.NOMINAL_FP64_TFLOPS,
+            "achieved_tflops": 2 * nnz / (t_us * 1e-6) / 1e12,
+            "floor_us": 1e6 * nnz / fma_rate, "hbm_floor_us": 1e6 * sum(c["bytes"] for c, _ in dom_cases) / (peak_hbm * 1e9),
+            "kernel_us": t_us, "frac_of_probe": (1e6 * nnz / fma_rate) / t_us}
     if all(c["name"] == "b" for c, _ in dom_cases):
         # random columns: every x gather is its own L2 request (1.15-1.26
         # requests per non-zero measured with ncu, the streamed lines

@@ -453,6 +453,13 @@ int rgcsr_convert_vector(int64_t n, const void *src, int32_t src_type, void *dst
  * a memory-bound kernel that moves the same bytes.  RGCSR_ERR_INVALID_ARG
  * for an unaligned pointer or size. */
 int rgcsr_stream_read(const void *data, int64_t bytes, void *sink, rgcsr_stream_t stream);
+/* Runs *fmas (host int64, written before the launch) = SMs x 2048 threads x
+ * 8 independent chains x iters double-precision FMAs, and writes nothing
+ * (sink, one device double, is written only if the chains end at exactly
+ * -1234567).  Not part of the method: it measures the FP64 FMA rate, the
+ * arithmetic ceiling of an FP64 SpMV (one FMA per non-zero).
+ * RGCSR_ERR_INVALID_ARG if iters < 1 or a pointer is NULL. */
+int rgcsr_fp64_fma_probe(int32_t iters, void *sink, int64_t *fmas, rgcsr_stream_t stream);
 
 /* Conjugate gradients for a symmetric positive definite square A, from
  * x = 0, stopping when ||r|| <= rel_tol ||b|| (the recurrence residual,

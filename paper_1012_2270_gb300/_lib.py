@@ -121,6 +121,7 @@ SIGNATURES = {
     "rgcsr_diag_scale": (ctypes.c_int, [I64, D, P, P, P, I32, P]),
     "rgcsr_convert_vector": (ctypes.c_int, [I64, P, I32, P, I32, P]),
     "rgcsr_stream_read": (ctypes.c_int, [P, I64, P, P]),
+    "rgcsr_fp64_fma_probe": (ctypes.c_int, [I32, P, ctypes.POINTER(I64), P]),
     "rgcsr_cg_workspace_bytes": (SZ, [I64, I32]),
     "rgcsr_cg": (ctypes.c_int, [_PM, P, P, D, I32, I32, P, SZ, PI32, PD, P]),
     "rgcsr_ir_cg_workspace_bytes": (SZ, [I64]),

@@ -91,6 +91,24 @@ stream_read_kernel(const float4 *__restrict__ p, int64_t n16, float *__restrict_
     if (s == -1234567.0f) *sink = s;
 }
 
+// FP64 FMA throughput: eight independent chains a = a * m + c per thread,
+// `iters` steps each.  m < 1 keeps every chain bounded; the sums are stored
+// only if they equal a value the chains never reach, so no FMA is dropped.
+__global__ void __launch_bounds__(256)
+fp64_fma_kernel(int32_t iters, double m, double c, double *__restrict__ sink) {
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (double)(threadIdx.x + k);
+    for (int32_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == -1234567.0) *sink = s;
+}
+
 }  // namespace
 
 int dot_device(int64_t n, const void *x, const void *y, double *out, double *partials, int value_type,
@@ -204,5 +222,15 @@ RGCSR_API int rgcsr_stream_read(const void *data, int64_t bytes, void *sink, rgc
     if (ceil_div(n16, (int64_t)256) < grid) grid = ceil_div(n16, (int64_t)256);
     stream_read_kernel<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(static_cast<const float4 *>(data), n16,
                                                                          static_cast<float *>(sink));
+    return launch_status();
+}
+
+RGCSR_API int rgcsr_fp64_fma_probe(int32_t iters, void *sink, int64_t *fmas, rgcsr_stream_t stream) {
+    if (iters < 1 || !sink || !fmas) return RGCSR_ERR_INVALID_ARG;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = sms * 8;                            // 8 CTAs of 256 threads per SM
+    *fmas = (int64_t)grid * 256 * 8 * iters;
+    fp64_fma_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(iters, 0.9999999, 1e-7, static_cast<double *>(sink));
     return launch_status();
 }

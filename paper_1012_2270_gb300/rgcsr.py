@@ -41,6 +41,21 @@ def stream_read(buf: torch.Tensor, stream=None) -> None:
 _READ_SINKS: dict = {}
 
 
+def fp64_fma_probe(iters: int = 1024, stream=None) -> int:
+    """Launches the library's FP64 FMA throughput kernel (independent FMA
+    chains on every SM) and returns how many FMAs it runs."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sink = _FMA_SINKS.get(dev)
+    if sink is None:
+        sink = _FMA_SINKS[dev] = torch.zeros(1, dtype=torch.float64, device=dev)
+    n = ctypes.c_int64(0)
+    L.call("rgcsr_fp64_fma_probe", int(iters), _ptr(sink), ctypes.byref(n), _stream_ptr(stream))
+    return n.value
+
+
+_FMA_SINKS: dict = {}
+
+
 def _dev(a, dtype=None, device="cuda") -> torch.Tensor:
     t = torch.as_tensor(np.ascontiguousarray(a)) if isinstance(a, np.ndarray) else a
     if dtype is not None and t.dtype != dtype:

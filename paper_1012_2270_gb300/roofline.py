@@ -12,6 +12,10 @@ INDEX_BYTES = 4
 # nominal HBM3e bandwidth used for the "% of 8 TB/s" figure
 NOMINAL_HBM_GBS = 8000.0
 
+# nominal FP64 rate of a GB300 (vector and tensor alike): an FP64 SpMV does
+# one FMA (2 flops) per non-zero, so this is its arithmetic ceiling
+NOMINAL_FP64_TFLOPS = 1.25
+
 
 def rgcsr_spmv_bytes(n_rows: int, n_cols: int, nnz: int, n_groups: int, value_bytes: int,
                      x_bytes: int | None = None, row_scale: bool = False) -> int:

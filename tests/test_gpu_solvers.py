@@ -74,6 +74,19 @@ def test_stream_read_probe():
         assert lib.rgcsr_stream_read(*args, _ptr(sink), _stream_ptr()) == L.RGCSR_ERR_INVALID_ARG
 
 
+def test_fp64_fma_probe():
+    # the FP64 rate probe reports its FMA count and writes nothing
+    from paper_1012_2270_gb300.rgcsr import fp64_fma_probe
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert fp64_fma_probe(3) == sms * 2048 * 8 * 3
+    sink = torch.full((1,), 5.0, dtype=torch.float64, device="cuda")
+    n = ctypes.c_int64(0)
+    L.call("rgcsr_fp64_fma_probe", 16, _ptr(sink), ctypes.byref(n), _stream_ptr())
+    torch.cuda.synchronize()
+    assert float(sink) == 5.0 and n.value == sms * 2048 * 8 * 16
+    assert L.lib().rgcsr_fp64_fma_probe(0, _ptr(sink), ctypes.byref(n), _stream_ptr()) == L.RGCSR_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_cg_against_oracle(dtype):
     A = synth.laplacian_3d(20)
