@@ -429,8 +429,10 @@ int rgcsr_spmv_bwd_values(const rgcsr_matrix *M, int32_t k, const void *G, int64
 /* ----------------------------------------------------------------------- */
 /* Scratch of rgcsr_dot, in bytes. */
 size_t rgcsr_dot_workspace_bytes(void);
-/* *result (a DEVICE double) = sum_i x_i y_i, accumulated in double in a
- * fixed order (deterministic). */
+/* *result (a DEVICE double) = sum_i x_i y_i in a fixed order
+ * (deterministic): double vectors accumulate in double; float vectors use
+ * the compensated dot product Dot2 of Ogita, Rump and Oishi (2005) in float
+ * per thread, as accurate as twice float precision, then sum in double. */
 int rgcsr_dot(int64_t n, const void *x, const void *y, double *result, void *workspace,
               size_t workspace_bytes, int32_t value_type, rgcsr_stream_t stream);
 /* y = alpha x + beta y. */

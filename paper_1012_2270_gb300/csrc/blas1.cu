@@ -24,14 +24,41 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return t;
 }
 
-template <typename T>
+// Double vectors: one FP64 FMA per element.
 __global__ void __launch_bounds__(kDotThreads)
-dot_partial(int64_t n, const T *__restrict__ x, const T *__restrict__ y, double *__restrict__ part) {
+dot_partial(int64_t n, const double *__restrict__ x, const double *__restrict__ y, double *__restrict__ part) {
     __shared__ double sh[32];
     double s = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        s = fma((double)x[i], (double)y[i], s);
-    const double t = block_sum<T>(s, sh);
+        s = fma(x[i], y[i], s);
+    const double t = block_sum<double>(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// Float vectors: the compensated dot product "Dot2" of Ogita, Rump and Oishi
+// (Accurate sum and dot product, SIAM J. Sci. Comput. 26, 2005) in float,
+// so that no FP64 instruction runs per element (GB300's FP64 pipe is
+// narrow).  Each product is split exactly into p + e (TwoProduct: a rounded
+// product and its FMA residual), the running sum s absorbs p with its exact
+// rounding error q (TwoSum), and c collects q + e.  A thread's s + c is as
+// accurate as a dot product in twice the working precision; it is widened to
+// double and the block sums it in double.  The _rn intrinsics keep the
+// compiler from contracting or reordering these steps.
+__global__ void __launch_bounds__(kDotThreads)
+dot_partial(int64_t n, const float *__restrict__ x, const float *__restrict__ y, double *__restrict__ part) {
+    __shared__ double sh[32];
+    float s = 0.0f, c = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float a = x[i], b = y[i];
+        const float p = __fmul_rn(a, b);
+        const float e = fmaf(a, b, -p);                        // a b = p + e exactly
+        const float t = __fadd_rn(s, p);
+        const float z = __fsub_rn(t, s);
+        const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));   // s + p = t + q exactly
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(q, e));
+    }
+    const double t = block_sum<double>((double)s + (double)c, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -115,11 +142,11 @@ int dot_device(int64_t n, const void *x, const void *y, double *out, double *par
                cudaStream_t s) {
     const unsigned g = (unsigned)kDotParts;
     if (value_type == RGCSR_F64)
-        dot_partial<double><<<g, kDotThreads, 0, s>>>(n, static_cast<const double *>(x),
-                                                      static_cast<const double *>(y), partials);
+        dot_partial<<<g, kDotThreads, 0, s>>>(n, static_cast<const double *>(x), static_cast<const double *>(y),
+                                              partials);
     else
-        dot_partial<float><<<g, kDotThreads, 0, s>>>(n, static_cast<const float *>(x),
-                                                     static_cast<const float *>(y), partials);
+        dot_partial<<<g, kDotThreads, 0, s>>>(n, static_cast<const float *>(x), static_cast<const float *>(y),
+                                              partials);
     dot_final<<<1, kDotThreads, 0, s>>>((int)g, partials, out);
     return launch_status();
 }

@@ -169,7 +169,8 @@ int launch_row_lengths(const rgcsr_csr *A, const int32_t *perm, int32_t *row_len
 int launch_check_perm(const int32_t *perm, int64_t n, int32_t *seen, int *flags, cudaStream_t s);
 
 // Vector kernels (blas1.cu).  dot_device writes the dot product of x and y
-// (accumulated in double, deterministic) to the device scalar *out, using
+// (deterministic; double vectors in double, float vectors by a compensated
+// float dot per thread summed in double) to the device scalar *out, using
 // kDotParts doubles of scratch.
 constexpr int kDotParts = 304;
 int dot_device(int64_t n, const void *x, const void *y, double *out, double *partials, int value_type,

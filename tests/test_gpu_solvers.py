@@ -39,6 +39,24 @@ def test_dot_deterministic_and_exact_on_integers():
         assert gpu_dot(xa.float(), xb.float()) == d1
 
 
+def test_float_dot_compensated_accuracy():
+    # float vectors: per-thread compensated sums (Dot2) then double.  The
+    # second half of the data cancels the first, so the dot product is tiny
+    # against sum |x_i y_i|; the result stays within 1e-10 of that sum of the
+    # exact dot product of the float inputs (plain float summation: ~1e-7)
+    rng = np.random.default_rng(7)
+    for n in (1, 777, 2_000_003):
+        a = rng.standard_normal(n).astype(np.float32)
+        b = rng.standard_normal(n).astype(np.float32)
+        h = n // 2
+        a[h:2 * h] = a[:h]
+        b[h:2 * h] = -b[:h]
+        prod = a.astype(np.float64) * b.astype(np.float64)        # exact in double
+        exact, scale = float(np.sum(prod)), float(np.sum(np.abs(prod)))
+        got = gpu_dot(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda())
+        assert abs(got - exact) <= 1e-10 * scale, (n, got, exact, scale)
+
+
 def test_vector_kernels():
     rng = np.random.default_rng(1)
     n = 10007
