@@ -24,15 +24,21 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return t;
 }
 
+// One thread's share of x . y over its grid-stride packs of W elements (in
+// element order within a pack), then the last n mod W elements.
 // Double vectors: one FP64 FMA per element.
-__global__ void __launch_bounds__(kDotThreads)
-dot_partial(int64_t n, const double *__restrict__ x, const double *__restrict__ y, double *__restrict__ part) {
-    __shared__ double sh[32];
+template <int W>
+__device__ __forceinline__ double dot_share(int64_t n, const double *__restrict__ x, const double *__restrict__ y) {
+    const int64_t S = (int64_t)gridDim.x * blockDim.x, tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nw = n / W;
     double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        s = fma(x[i], y[i], s);
-    const double t = block_sum<double>(s, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    for (int64_t i = tid; i < nw; i += S) {
+        const Pack<double, W> a = ld_pack<double, W>(x + i * W), b = ld_pack<double, W>(y + i * W);
+#pragma unroll
+        for (int k = 0; k < W; ++k) s = fma(a.v[k], b.v[k], s);
+    }
+    for (int64_t i = nw * W + tid; i < n; i += S) s = fma(x[i], y[i], s);
+    return s;
 }
 
 // Float vectors: the compensated dot product "Dot2" of Ogita, Rump and Oishi
@@ -44,22 +50,63 @@ dot_partial(int64_t n, const double *__restrict__ x, const double *__restrict__ 
 // accurate as a dot product in twice the working precision; it is widened to
 // double and the block sums it in double.  The _rn intrinsics keep the
 // compiler from contracting or reordering these steps.
-__global__ void __launch_bounds__(kDotThreads)
-dot_partial(int64_t n, const float *__restrict__ x, const float *__restrict__ y, double *__restrict__ part) {
-    __shared__ double sh[32];
+__device__ __forceinline__ void dot2_step(float a, float b, float &s, float &c) {
+    const float p = __fmul_rn(a, b);
+    const float e = fmaf(a, b, -p);                            // a b = p + e exactly
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));   // s + p = t + q exactly
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(q, e));
+}
+
+template <int W>
+__device__ __forceinline__ double dot_share(int64_t n, const float *__restrict__ x, const float *__restrict__ y) {
+    const int64_t S = (int64_t)gridDim.x * blockDim.x, tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nw = n / W;
     float s = 0.0f, c = 0.0f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float a = x[i], b = y[i];
-        const float p = __fmul_rn(a, b);
-        const float e = fmaf(a, b, -p);                        // a b = p + e exactly
-        const float t = __fadd_rn(s, p);
-        const float z = __fsub_rn(t, s);
-        const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));   // s + p = t + q exactly
-        s = t;
-        c = __fadd_rn(c, __fadd_rn(q, e));
+    for (int64_t i = tid; i < nw; i += S) {
+        const Pack<float, W> a = ld_pack<float, W>(x + i * W), b = ld_pack<float, W>(y + i * W);
+#pragma unroll
+        for (int k = 0; k < W; ++k) dot2_step(a.v[k], b.v[k], s, c);
     }
-    const double t = block_sum<double>((double)s + (double)c, sh);
+    for (int64_t i = nw * W + tid; i < n; i += S) dot2_step(x[i], y[i], s, c);
+    return (double)s + (double)c;
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(kDotThreads)
+dot_partial(int64_t n, const T *__restrict__ x, const T *__restrict__ y, double *__restrict__ part) {
+    __shared__ double sh[32];
+    const double t = block_sum<double>(dot_share<W>(n, x, y), sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// The same partials, and the last block to finish (a ticket on *count after
+// a fence) adds them in block order -- the sum dot_final forms -- and resets
+// *count for the next call: one launch instead of two.
+template <typename T, int W>
+__global__ void __launch_bounds__(kDotThreads)
+dot_onepass(int64_t n, const T *__restrict__ x, const T *__restrict__ y, double *__restrict__ part,
+            unsigned *__restrict__ count, double *__restrict__ out) {
+    __shared__ double sh[32];
+    __shared__ bool last;
+    const double t = block_sum<double>(dot_share<W>(n, x, y), sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = t;
+        __threadfence();
+        last = atomicAdd(count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(part + i);
+    const double total = block_sum<double>(s, sh);
+    if (threadIdx.x == 0) {
+        *out = total;
+        *count = 0u;
+    }
 }
 
 __global__ void __launch_bounds__(kDotThreads)
@@ -71,30 +118,64 @@ dot_final(int nparts, const double *__restrict__ part, double *__restrict__ out)
     if (threadIdx.x == 0) *out = t;
 }
 
-template <typename T>
+template <typename T, int W>
 __global__ void axpby_kernel(int64_t n, double a, const T *__restrict__ x, double b, T *__restrict__ y) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = (T)(a * (double)x[i] + b * (double)y[i]);
+    const int64_t S = (int64_t)gridDim.x * blockDim.x, tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nw = n / W;
+    for (int64_t i = tid; i < nw; i += S) {
+        const Pack<T, W> xv = ld_pack<T, W>(x + i * W);
+        Pack<T, W> yv = ld_pack<T, W>(y + i * W);
+#pragma unroll
+        for (int k = 0; k < W; ++k) yv.v[k] = (T)(a * (double)xv.v[k] + b * (double)yv.v[k]);
+        st_pack<T, W>(y + i * W, yv);
+    }
+    for (int64_t i = nw * W + tid; i < n; i += S) y[i] = (T)(a * (double)x[i] + b * (double)y[i]);
 }
 
-template <typename T>
+template <typename T, int W>
 __global__ void jacobi_kernel(int64_t n, T omega, const T *__restrict__ dinv, const T *__restrict__ b,
                               const T *__restrict__ ax, const T *__restrict__ x, T *__restrict__ out) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = x[i] + omega * dinv[i] * (b[i] - ax[i]);
+    const int64_t S = (int64_t)gridDim.x * blockDim.x, tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nw = n / W;
+    for (int64_t i = tid; i < nw; i += S) {
+        const Pack<T, W> dv = ld_pack<T, W>(dinv + i * W), bv = ld_pack<T, W>(b + i * W),
+                         av = ld_pack<T, W>(ax + i * W), xv = ld_pack<T, W>(x + i * W);
+        Pack<T, W> o;
+#pragma unroll
+        for (int k = 0; k < W; ++k) o.v[k] = xv.v[k] + omega * dv.v[k] * (bv.v[k] - av.v[k]);
+        st_pack<T, W>(out + i * W, o);
+    }
+    for (int64_t i = nw * W + tid; i < n; i += S) out[i] = x[i] + omega * dinv[i] * (b[i] - ax[i]);
 }
 
-template <typename T>
+template <typename T, int W>
 __global__ void diag_scale_kernel(int64_t n, T alpha, const T *__restrict__ d, const T *__restrict__ x,
                                   T *__restrict__ out) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = alpha * d[i] * x[i];
+    const int64_t S = (int64_t)gridDim.x * blockDim.x, tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nw = n / W;
+    for (int64_t i = tid; i < nw; i += S) {
+        const Pack<T, W> dv = ld_pack<T, W>(d + i * W), xv = ld_pack<T, W>(x + i * W);
+        Pack<T, W> o;
+#pragma unroll
+        for (int k = 0; k < W; ++k) o.v[k] = alpha * dv.v[k] * xv.v[k];
+        st_pack<T, W>(out + i * W, o);
+    }
+    for (int64_t i = nw * W + tid; i < n; i += S) out[i] = alpha * d[i] * x[i];
 }
 
-template <typename S, typename D>
-__global__ void convert_kernel(int64_t n, const S *__restrict__ src, D *__restrict__ dst) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = (D)src[i];
+// W = 2: 16 bytes on the double side, 8 on the float side.
+template <typename S_, typename D, int W>
+__global__ void convert_kernel(int64_t n, const S_ *__restrict__ src, D *__restrict__ dst) {
+    const int64_t S = (int64_t)gridDim.x * blockDim.x, tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nw = n / W;
+    for (int64_t i = tid; i < nw; i += S) {
+        const Pack<S_, W> a = ld_pack<S_, W>(src + i * W);
+        Pack<D, W> o;
+#pragma unroll
+        for (int k = 0; k < W; ++k) o.v[k] = (D)a.v[k];
+        st_pack<D, W>(dst + i * W, o);
+    }
+    for (int64_t i = nw * W + tid; i < n; i += S) dst[i] = (D)src[i];
 }
 
 unsigned vec_grid(int64_t n) {
@@ -139,39 +220,63 @@ fp64_fma_kernel(int32_t iters, double m, double c, double *__restrict__ sink) {
 }  // namespace
 
 int dot_device(int64_t n, const void *x, const void *y, double *out, double *partials, int value_type,
-               cudaStream_t s) {
+               cudaStream_t s, unsigned *count) {
     const unsigned g = (unsigned)kDotParts;
+    const bool v = all_aligned16(x, y);
+    const double *xd = static_cast<const double *>(x), *yd = static_cast<const double *>(y);
+    const float *xf = static_cast<const float *>(x), *yf = static_cast<const float *>(y);
+    if (count) {
+        if (value_type == RGCSR_F64)
+            v ? dot_onepass<double, 2><<<g, kDotThreads, 0, s>>>(n, xd, yd, partials, count, out)
+              : dot_onepass<double, 1><<<g, kDotThreads, 0, s>>>(n, xd, yd, partials, count, out);
+        else
+            v ? dot_onepass<float, 4><<<g, kDotThreads, 0, s>>>(n, xf, yf, partials, count, out)
+              : dot_onepass<float, 1><<<g, kDotThreads, 0, s>>>(n, xf, yf, partials, count, out);
+        return launch_status();
+    }
     if (value_type == RGCSR_F64)
-        dot_partial<<<g, kDotThreads, 0, s>>>(n, static_cast<const double *>(x), static_cast<const double *>(y),
-                                              partials);
+        v ? dot_partial<double, 2><<<g, kDotThreads, 0, s>>>(n, xd, yd, partials)
+          : dot_partial<double, 1><<<g, kDotThreads, 0, s>>>(n, xd, yd, partials);
     else
-        dot_partial<<<g, kDotThreads, 0, s>>>(n, static_cast<const float *>(x), static_cast<const float *>(y),
-                                              partials);
+        v ? dot_partial<float, 4><<<g, kDotThreads, 0, s>>>(n, xf, yf, partials)
+          : dot_partial<float, 1><<<g, kDotThreads, 0, s>>>(n, xf, yf, partials);
     dot_final<<<1, kDotThreads, 0, s>>>((int)g, partials, out);
     return launch_status();
 }
 
 int axpby_device(int64_t n, double a, const void *x, double b, void *y, int value_type, cudaStream_t s) {
     if (n <= 0) return RGCSR_OK;
-    if (value_type == RGCSR_F64)
-        axpby_kernel<double><<<vec_grid(n), 256, 0, s>>>(n, a, static_cast<const double *>(x), b,
-                                                          static_cast<double *>(y));
-    else
-        axpby_kernel<float><<<vec_grid(n), 256, 0, s>>>(n, a, static_cast<const float *>(x), b,
-                                                         static_cast<float *>(y));
+    const bool v = all_aligned16(x, y);
+    if (value_type == RGCSR_F64) {
+        const double *xd = static_cast<const double *>(x);
+        double *yd = static_cast<double *>(y);
+        v ? axpby_kernel<double, 2><<<vec_grid(ceil_div(n, 2)), 256, 0, s>>>(n, a, xd, b, yd)
+          : axpby_kernel<double, 1><<<vec_grid(n), 256, 0, s>>>(n, a, xd, b, yd);
+    } else {
+        const float *xf = static_cast<const float *>(x);
+        float *yf = static_cast<float *>(y);
+        v ? axpby_kernel<float, 4><<<vec_grid(ceil_div(n, 4)), 256, 0, s>>>(n, a, xf, b, yf)
+          : axpby_kernel<float, 1><<<vec_grid(n), 256, 0, s>>>(n, a, xf, b, yf);
+    }
     return launch_status();
 }
 
 int convert_device(int64_t n, const void *src, int src_type, void *dst, int dst_type, cudaStream_t s) {
     if (n <= 0) return RGCSR_OK;
-    if (src_type == RGCSR_F64 && dst_type == RGCSR_F32)
-        convert_kernel<double, float><<<vec_grid(n), 256, 0, s>>>(n, static_cast<const double *>(src),
-                                                                 static_cast<float *>(dst));
-    else if (src_type == RGCSR_F32 && dst_type == RGCSR_F64)
-        convert_kernel<float, double><<<vec_grid(n), 256, 0, s>>>(n, static_cast<const float *>(src),
-                                                                 static_cast<double *>(dst));
-    else
+    const bool v = all_aligned16(src, dst);
+    if (src_type == RGCSR_F64 && dst_type == RGCSR_F32) {
+        const double *a = static_cast<const double *>(src);
+        float *o = static_cast<float *>(dst);
+        v ? convert_kernel<double, float, 2><<<vec_grid(ceil_div(n, 2)), 256, 0, s>>>(n, a, o)
+          : convert_kernel<double, float, 1><<<vec_grid(n), 256, 0, s>>>(n, a, o);
+    } else if (src_type == RGCSR_F32 && dst_type == RGCSR_F64) {
+        const float *a = static_cast<const float *>(src);
+        double *o = static_cast<double *>(dst);
+        v ? convert_kernel<float, double, 2><<<vec_grid(ceil_div(n, 2)), 256, 0, s>>>(n, a, o)
+          : convert_kernel<float, double, 1><<<vec_grid(n), 256, 0, s>>>(n, a, o);
+    } else {
         return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    }
     return launch_status();
 }
 
@@ -201,18 +306,21 @@ RGCSR_API int rgcsr_jacobi_step(int64_t n, double omega, const void *dinv, const
     if (n < 0 || (n > 0 && (!dinv || !b || !Ax || !x || !x_out))) return RGCSR_ERR_INVALID_ARG;
     if (n == 0) return RGCSR_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if (value_type == RGCSR_F64)
-        jacobi_kernel<double><<<vec_grid(n), 256, 0, s>>>(n, omega, static_cast<const double *>(dinv),
-                                                          static_cast<const double *>(b),
-                                                          static_cast<const double *>(Ax),
-                                                          static_cast<const double *>(x), static_cast<double *>(x_out));
-    else if (value_type == RGCSR_F32)
-        jacobi_kernel<float><<<vec_grid(n), 256, 0, s>>>(n, (float)omega, static_cast<const float *>(dinv),
-                                                         static_cast<const float *>(b),
-                                                         static_cast<const float *>(Ax),
-                                                         static_cast<const float *>(x), static_cast<float *>(x_out));
-    else
+    const bool v = all_aligned16(dinv, b, Ax, x, x_out);
+    if (value_type == RGCSR_F64) {
+        auto p = [](const void *q) { return static_cast<const double *>(q); };
+        double *o = static_cast<double *>(x_out);
+        v ? jacobi_kernel<double, 2><<<vec_grid(ceil_div(n, 2)), 256, 0, s>>>(n, omega, p(dinv), p(b), p(Ax), p(x), o)
+          : jacobi_kernel<double, 1><<<vec_grid(n), 256, 0, s>>>(n, omega, p(dinv), p(b), p(Ax), p(x), o);
+    } else if (value_type == RGCSR_F32) {
+        auto p = [](const void *q) { return static_cast<const float *>(q); };
+        float *o = static_cast<float *>(x_out);
+        const float w = (float)omega;
+        v ? jacobi_kernel<float, 4><<<vec_grid(ceil_div(n, 4)), 256, 0, s>>>(n, w, p(dinv), p(b), p(Ax), p(x), o)
+          : jacobi_kernel<float, 1><<<vec_grid(n), 256, 0, s>>>(n, w, p(dinv), p(b), p(Ax), p(x), o);
+    } else {
         return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    }
     return launch_status();
 }
 
@@ -221,14 +329,20 @@ RGCSR_API int rgcsr_diag_scale(int64_t n, double alpha, const void *d, const voi
     if (n < 0 || (n > 0 && (!d || !x || !out))) return RGCSR_ERR_INVALID_ARG;
     if (n == 0) return RGCSR_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if (value_type == RGCSR_F64)
-        diag_scale_kernel<double><<<vec_grid(n), 256, 0, s>>>(n, alpha, static_cast<const double *>(d),
-                                                              static_cast<const double *>(x), static_cast<double *>(out));
-    else if (value_type == RGCSR_F32)
-        diag_scale_kernel<float><<<vec_grid(n), 256, 0, s>>>(n, (float)alpha, static_cast<const float *>(d),
-                                                             static_cast<const float *>(x), static_cast<float *>(out));
-    else
+    const bool v = all_aligned16(d, x, out);
+    if (value_type == RGCSR_F64) {
+        const double *dd = static_cast<const double *>(d), *xd = static_cast<const double *>(x);
+        double *o = static_cast<double *>(out);
+        v ? diag_scale_kernel<double, 2><<<vec_grid(ceil_div(n, 2)), 256, 0, s>>>(n, alpha, dd, xd, o)
+          : diag_scale_kernel<double, 1><<<vec_grid(n), 256, 0, s>>>(n, alpha, dd, xd, o);
+    } else if (value_type == RGCSR_F32) {
+        const float *df = static_cast<const float *>(d), *xf = static_cast<const float *>(x);
+        float *o = static_cast<float *>(out);
+        v ? diag_scale_kernel<float, 4><<<vec_grid(ceil_div(n, 4)), 256, 0, s>>>(n, (float)alpha, df, xf, o)
+          : diag_scale_kernel<float, 1><<<vec_grid(n), 256, 0, s>>>(n, (float)alpha, df, xf, o);
+    } else {
         return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    }
     return launch_status();
 }
 

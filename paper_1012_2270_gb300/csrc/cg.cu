@@ -25,30 +25,52 @@ unsigned grid(int64_t n) {
     return (unsigned)(b > 0 ? b : 1);
 }
 
-// alpha = rr / dq;  x += alpha d;  r -= alpha q
-template <typename T>
+// alpha = rr / dq;  x += alpha d;  r -= alpha q   (W elements per access)
+template <typename T, int W>
 __global__ void cg_xr_kernel(int64_t n, const double *__restrict__ rr, const double *__restrict__ dq,
                              T *__restrict__ x, T *__restrict__ r, const T *__restrict__ d,
                              const T *__restrict__ q) {
     const T alpha = (T)(*rr / *dq);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t S = (int64_t)gridDim.x * blockDim.x, tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nw = n / W;
+    for (int64_t i = tid; i < nw; i += S) {
+        Pack<T, W> xv = ld_pack<T, W>(x + i * W), rv = ld_pack<T, W>(r + i * W);
+        const Pack<T, W> dv = ld_pack<T, W>(d + i * W), qv = ld_pack<T, W>(q + i * W);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            xv.v[k] = fma(alpha, dv.v[k], xv.v[k]);
+            rv.v[k] = fma(-alpha, qv.v[k], rv.v[k]);
+        }
+        st_pack<T, W>(x + i * W, xv);
+        st_pack<T, W>(r + i * W, rv);
+    }
+    for (int64_t i = nw * W + tid; i < n; i += S) {
         x[i] = fma(alpha, d[i], x[i]);
         r[i] = fma(-alpha, q[i], r[i]);
     }
 }
 
 // beta = rr_new / rr_old;  d = r + beta d
-template <typename T>
+template <typename T, int W>
 __global__ void cg_d_kernel(int64_t n, const double *__restrict__ rr_new, const double *__restrict__ rr_old,
                             const T *__restrict__ r, T *__restrict__ d) {
     const T beta = (T)(*rr_new / *rr_old);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        d[i] = fma(beta, d[i], r[i]);
+    const int64_t S = (int64_t)gridDim.x * blockDim.x, tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nw = n / W;
+    for (int64_t i = tid; i < nw; i += S) {
+        const Pack<T, W> rv = ld_pack<T, W>(r + i * W);
+        Pack<T, W> dv = ld_pack<T, W>(d + i * W);
+#pragma unroll
+        for (int k = 0; k < W; ++k) dv.v[k] = fma(beta, dv.v[k], rv.v[k]);
+        st_pack<T, W>(d + i * W, dv);
+    }
+    for (int64_t i = nw * W + tid; i < n; i += S) d[i] = fma(beta, d[i], r[i]);
 }
 
 struct CgScratch {
     void *r, *d, *q;
     double *scal;       // [rr0, rr1, dq, spare]
+    unsigned *count;    // the one-pass dot's block ticket (in the scalar block)
     double *partials;
 };
 
@@ -65,7 +87,9 @@ CgScratch carve_cg(void *ws, int64_t n, int vt) {
     c.r = p; p += a;
     c.d = p; p += a;
     c.q = p; p += a;
-    c.scal = reinterpret_cast<double *>(p); p += 256;
+    c.scal = reinterpret_cast<double *>(p);
+    c.count = reinterpret_cast<unsigned *>(p + 64);
+    p += 256;
     c.partials = reinterpret_cast<double *>(p);
     return c;
 }
@@ -82,7 +106,8 @@ int cg_run(const rgcsr_matrix *A, const void *b, void *x, double rel_tol, int ma
     RGCSR_CUDA_TRY(cudaMemsetAsync(x, 0, bytes, s));
     RGCSR_CUDA_TRY(cudaMemcpyAsync(c.r, b, bytes, cudaMemcpyDeviceToDevice, s));
     RGCSR_CUDA_TRY(cudaMemcpyAsync(c.d, b, bytes, cudaMemcpyDeviceToDevice, s));
-    if ((st = dot_device(n, c.r, c.r, &c.scal[0], c.partials, vt, s)) != RGCSR_OK) return st;
+    RGCSR_CUDA_TRY(cudaMemsetAsync(c.count, 0, sizeof(unsigned), s));
+    if ((st = dot_device(n, c.r, c.r, &c.scal[0], c.partials, vt, s, c.count)) != RGCSR_OK) return st;
     double bb = 0.0;
     RGCSR_CUDA_TRY(cudaMemcpyAsync(&bb, &c.scal[0], sizeof(double), cudaMemcpyDeviceToHost, s));
     RGCSR_CUDA_TRY(cudaStreamSynchronize(s));
@@ -93,16 +118,25 @@ int cg_run(const rgcsr_matrix *A, const void *b, void *x, double rel_tol, int ma
     int cur = 0, it = 0;
     // One CG iteration: q = A d; alpha = rr / (d.q); x += alpha d; r -= alpha q;
     // rr' = r.r; d = r + (rr' / rr) d.  `cur` selects which scalar slot holds rr.
+    constexpr int kW = 16 / (int)sizeof(T);                 // 16-byte accesses when x is aligned
+    const bool vec = all_aligned16(x, c.r, c.d, c.q);
     auto iteration = [&](cudaStream_t st_, int cur_) -> int {
         int e;
         if ((e = rgcsr_spmv(A, c.d, c.q, (rgcsr_stream_t)st_)) != RGCSR_OK) return e;
-        if ((e = dot_device(n, c.d, c.q, &c.scal[2], c.partials, vt, st_)) != RGCSR_OK) return e;
-        cg_xr_kernel<T><<<grid(n), kThreads, 0, st_>>>(n, &c.scal[cur_], &c.scal[2], static_cast<T *>(x),
-                                                       static_cast<T *>(c.r), static_cast<const T *>(c.d),
-                                                       static_cast<const T *>(c.q));
-        if ((e = dot_device(n, c.r, c.r, &c.scal[1 - cur_], c.partials, vt, st_)) != RGCSR_OK) return e;
-        cg_d_kernel<T><<<grid(n), kThreads, 0, st_>>>(n, &c.scal[1 - cur_], &c.scal[cur_],
-                                                      static_cast<const T *>(c.r), static_cast<T *>(c.d));
+        if ((e = dot_device(n, c.d, c.q, &c.scal[2], c.partials, vt, st_, c.count)) != RGCSR_OK) return e;
+        T *xt = static_cast<T *>(x), *rt = static_cast<T *>(c.r), *dt = static_cast<T *>(c.d);
+        const T *qt = static_cast<const T *>(c.q);
+        if (vec)
+            cg_xr_kernel<T, kW><<<grid(ceil_div(n, kW)), kThreads, 0, st_>>>(n, &c.scal[cur_], &c.scal[2], xt, rt,
+                                                                            dt, qt);
+        else
+            cg_xr_kernel<T, 1><<<grid(n), kThreads, 0, st_>>>(n, &c.scal[cur_], &c.scal[2], xt, rt, dt, qt);
+        if ((e = dot_device(n, c.r, c.r, &c.scal[1 - cur_], c.partials, vt, st_, c.count)) != RGCSR_OK) return e;
+        if (vec)
+            cg_d_kernel<T, kW><<<grid(ceil_div(n, kW)), kThreads, 0, st_>>>(n, &c.scal[1 - cur_], &c.scal[cur_],
+                                                                           rt, dt);
+        else
+            cg_d_kernel<T, 1><<<grid(n), kThreads, 0, st_>>>(n, &c.scal[1 - cur_], &c.scal[cur_], rt, dt);
         return launch_status();
     };
     // After the first round of iterations (which also runs any one-off kernel

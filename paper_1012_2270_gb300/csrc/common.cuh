@@ -38,6 +38,23 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// W consecutive elements moved as one access: 16 bytes for W = 16 / sizeof(T)
+// (a vector load or store), or one element for W = 1.  The vector kernels
+// use W > 1 when every pointer is 16-byte aligned, so that each thread keeps
+// 16 bytes per operand in flight, and finish the last n mod W elements one
+// by one.
+template <typename T, int W>
+struct alignas(sizeof(T) * W) Pack {
+    T v[W];
+};
+template <typename T, int W>
+__device__ __forceinline__ Pack<T, W> ld_pack(const T *p) { return *reinterpret_cast<const Pack<T, W> *>(p); }
+template <typename T, int W>
+__device__ __forceinline__ void st_pack(T *p, const Pack<T, W> &v) { *reinterpret_cast<Pack<T, W> *>(p) = v; }
+inline bool all_aligned16() { return true; }
+template <typename P, typename... R>
+inline bool all_aligned16(P p, R... r) { return ((uintptr_t)p & 15) == 0 && all_aligned16(r...); }
+
 __device__ __forceinline__ int warp_max_i(int v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
@@ -171,10 +188,12 @@ int launch_check_perm(const int32_t *perm, int64_t n, int32_t *seen, int *flags,
 // Vector kernels (blas1.cu).  dot_device writes the dot product of x and y
 // (deterministic; double vectors in double, float vectors by a compensated
 // float dot per thread summed in double) to the device scalar *out, using
-// kDotParts doubles of scratch.
+// kDotParts doubles of scratch.  With `count` (a device counter that is 0
+// before the first call; each call leaves it at 0) the block partials are
+// added by the last block to finish: one launch, the same result.
 constexpr int kDotParts = 304;
 int dot_device(int64_t n, const void *x, const void *y, double *out, double *partials, int value_type,
-               cudaStream_t s);
+               cudaStream_t s, unsigned *count = nullptr);
 int axpby_device(int64_t n, double a, const void *x, double b, void *y, int value_type, cudaStream_t s);
 int convert_device(int64_t n, const void *src, int src_type, void *dst, int dst_type, cudaStream_t s);
 

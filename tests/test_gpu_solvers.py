@@ -57,22 +57,40 @@ def test_float_dot_compensated_accuracy():
         assert abs(got - exact) <= 1e-10 * scale, (n, got, exact, scale)
 
 
-def test_vector_kernels():
+@pytest.mark.parametrize("offset", [0, 1])
+def test_vector_kernels(offset):
+    # offset 0: 16-byte accesses with a tail of n mod W elements; offset 1:
+    # vectors that start one element past an aligned address take the
+    # scalar path.  FP64 and FP32, n odd.
     rng = np.random.default_rng(1)
     n = 10007
+
+    def dev(v, dt):                         # a CUDA vector starting `offset` elements into its buffer
+        buf = torch.zeros(n + 1, dtype=dt, device="cuda")
+        t = buf[offset:offset + n]
+        t.copy_(torch.from_numpy(v).to(dt))
+        return t
+
     x, y, d, b, ax = (rng.standard_normal(n) for _ in range(5))
-    X, Y = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
-    L.call("rgcsr_axpby", n, 2.0, _ptr(X), -0.5, _ptr(Y), L.F64, _stream_ptr())
-    assert np.allclose(Y.cpu().numpy(), 2.0 * x - 0.5 * y, rtol=1e-15, atol=1e-15)
-    out = torch.empty(n, dtype=torch.float64, device="cuda")
-    D, B, AX = (torch.from_numpy(v).cuda() for v in (d, b, ax))
-    L.call("rgcsr_jacobi_step", n, 0.7, _ptr(D), _ptr(B), _ptr(AX), _ptr(X), _ptr(out), L.F64, _stream_ptr())
-    assert np.allclose(out.cpu().numpy(), x + 0.7 * d * (b - ax), rtol=1e-14, atol=1e-14)
-    L.call("rgcsr_diag_scale", n, -3.0, _ptr(D), _ptr(X), _ptr(out), L.F64, _stream_ptr())
-    assert np.allclose(out.cpu().numpy(), -3.0 * d * x, rtol=1e-15, atol=1e-15)
-    f = torch.empty(n, dtype=torch.float32, device="cuda")
+    for dt, vt, tol in ((torch.float64, L.F64, 1e-14), (torch.float32, L.F32, 2e-6)):
+        xs, ys, ds, bs, axs = (v.astype(np.float64 if dt == torch.float64 else np.float32).astype(np.float64)
+                               for v in (x, y, d, b, ax))
+        X, Y, D, B, AX = (dev(v, dt) for v in (xs, ys, ds, bs, axs))
+        L.call("rgcsr_axpby", n, 2.0, _ptr(X), -0.5, _ptr(Y), vt, _stream_ptr())
+        assert np.allclose(Y.double().cpu().numpy(), 2.0 * xs - 0.5 * ys, rtol=tol, atol=tol)
+        out = dev(np.zeros(n), dt)
+        L.call("rgcsr_jacobi_step", n, 0.7, _ptr(D), _ptr(B), _ptr(AX), _ptr(X), _ptr(out), vt, _stream_ptr())
+        assert np.allclose(out.double().cpu().numpy(), xs + 0.7 * ds * (bs - axs), rtol=tol, atol=tol)
+        L.call("rgcsr_diag_scale", n, -3.0, _ptr(D), _ptr(X), _ptr(out), vt, _stream_ptr())
+        assert np.allclose(out.double().cpu().numpy(), -3.0 * ds * xs, rtol=tol, atol=tol)
+        ref = float(np.dot(xs, ds))
+        assert abs(gpu_dot(X, D) - ref) <= 1e-12 * float(np.dot(np.abs(xs), np.abs(ds)))
+    X = dev(x, torch.float64)
+    f = dev(np.zeros(n), torch.float32)
     L.call("rgcsr_convert_vector", n, _ptr(X), L.F64, _ptr(f), L.F32, _stream_ptr())
     assert np.array_equal(f.cpu().numpy(), x.astype(np.float32))
+    L.call("rgcsr_convert_vector", n, _ptr(f), L.F32, _ptr(X), L.F64, _stream_ptr())
+    assert np.array_equal(X.cpu().numpy(), x.astype(np.float32).astype(np.float64))
 
 
 def test_stream_read_probe():
