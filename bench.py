@@ -122,7 +122,9 @@ def kernel_name(cfg, M, A, dt):
         n = A.n_rows
         dense = (M.n_stored * 4 <= M.nnz * 5 and
                  not (M.max_row_len > 64 and M.max_row_len * n > 8 * M.nnz))
-        if dense and M.group_size == 32 and n >= 32 and (dt == "f32" or A.nnz <= 8 * n):
+        if dense and M.group_size == 32 and A.nnz <= 8 * n:       # (device allocations are aligned)
+            return f"rgcsr_spmv_vec<{t}>"
+        if dense and M.group_size == 32 and n >= 32 and dt == "f32":
             k = 3
         else:
             k = 4 if dense else 2

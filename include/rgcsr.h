@@ -98,11 +98,12 @@ typedef struct {
 /* Kernel selection for rgcsr_spmv_ex (autotuning and ablations). */
 #define RGCSR_KERNEL_AUTO   0    /* default: when the groups are dense (padding <=
                                     25% of the stored slots, no row longer than 64
-                                    and 8x the mean) the TMA kernel (FP32, or FP64
-                                    with <= 8 entries per row on average), the LEAN
-                                    vector-load variant 1 (BF16/FP16, G = 32, <= 8
-                                    entries per row), or else the LEAN kernel;
-                                    otherwise the warp-split kernel                 */
+                                    and 8x the mean) and rows are short (<= 8 per
+                                    row on average) at G = 32, the LEAN vector-load
+                                    variant 1 (FP64: 4); dense FP32 with longer
+                                    rows, the TMA kernel, variant 2; other dense
+                                    matrices, the LEAN kernel; otherwise the
+                                    warp-split kernel                               */
 #define RGCSR_KERNEL_PAPER  1    /* one block per group, one thread per row (Sec. 3.4 listing) */
 #define RGCSR_KERNEL_SPLIT  2    /* one thread per row; long rows of a warp finished
                                     by the whole warp with a shuffle reduction      */

@@ -517,24 +517,24 @@ RGCSR_API int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
     int kernel = launch ? launch->kernel : RGCSR_KERNEL_AUTO;
     int variant = launch ? launch->variant : 0;
     if (kernel == RGCSR_KERNEL_AUTO) {
-        // Dense groups (padding <= 25% of the stored slots): the TMA-staged
-        // kernel for FP32 and for short FP64 rows, the vector-load kernel
-        // for short BF16/FP16 rows (G = 32), the full-occupancy
-        // thread-per-row kernel otherwise; uneven or long rows take the
-        // warp-split kernel.
+        // Dense groups (padding <= 25% of the stored slots), as timed on
+        // GB300: short rows (<= 8 per row) at G = 32 take the vector-load
+        // kernel (4 rows per lane with 2 slot-rows per step; FP64: 2 rows
+        // with 4); longer FP32 rows the TMA-staged kernel (16 slot-rows per
+        // stage); the rest the full-occupancy thread-per-row kernel.  Uneven
+        // or long rows take the warp-split kernel.
         // "dense": little padding and no row far longer than the average
         const bool dense = M->n_stored * 4 <= M->nnz * 5 &&
                            !(M->max_row_len > 64 && M->max_row_len * M->n_rows > 8 * M->nnz);
         const bool short_rows = M->nnz <= 8 * M->n_rows;
-        const bool reduced = M->value_type == RGCSR_BF16 || M->value_type == RGCSR_F16;
         auto aligned = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
         variant = 0;
-        if (dense && tma_eligible(M) && (M->value_type == RGCSR_F32 || short_rows)) {
-            kernel = RGCSR_KERNEL_TMA;
-        } else if (dense && reduced && short_rows && M->group_size == 32 && aligned(M->values) &&
-                   aligned(M->columns)) {
+        if (dense && short_rows && M->group_size == 32 && aligned(M->values) && aligned(M->columns)) {
             kernel = RGCSR_KERNEL_LEAN;
-            variant = 1;
+            variant = M->value_type == RGCSR_F64 ? 4 : 1;
+        } else if (dense && M->value_type == RGCSR_F32 && tma_eligible(M)) {
+            kernel = RGCSR_KERNEL_TMA;
+            variant = 2;
         } else if (dense) {
             kernel = RGCSR_KERNEL_LEAN;
         } else {
