@@ -37,10 +37,6 @@ class CSRMatrix:
     def row_lengths(self) -> np.ndarray:
         return np.diff(self.rowptr)
 
-    def with_values(self, val: np.ndarray, name: str | None = None) -> "CSRMatrix":
-        return CSRMatrix(self.n_rows, self.n_cols, self.rowptr, self.col,
-                         np.ascontiguousarray(val), name or self.name, dict(self.meta))
-
 
 def _from_offsets(shape_rows: int, offsets_cols: np.ndarray, valid: np.ndarray,
                   n_cols: int, name: str) -> CSRMatrix:
