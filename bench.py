@@ -513,7 +513,7 @@ def run_ours(args):
     # ---- forms beside plain ----
     forms = {}
     if not args.no_forms and rank == 0:
-        forms = measure_forms(mats, cases, detail, dev, stream)
+        forms = measure_forms(mats, cases, detail, dev, stream, tune_cache=bool(args.tune_cache))
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -597,7 +597,7 @@ def max_scaled_error(y, y_ref, absy):
     return float((err[ok] / den[ok]).max()) if bool(ok.any()) else 0.0
 
 
-def measure_forms(mats, cases, detail, dev, stream):
+def measure_forms(mats, cases, detail, dev, stream, tune_cache=False):
     import torch
     from paper_1012_2270_gb300 import solvers
     from paper_1012_2270_gb300.autograd import SparseOperator, spmm
@@ -795,6 +795,9 @@ def measure_forms(mats, cases, detail, dev, stream):
     # on/off (the texture study of Sec. 4.3) and sliced ELLPACK (Sec. 3.4) --
     forms.update(measure_tables(mats, flush, stream))
 
+    # -- the four matrix shapes of Sec. 4.4.2 (Table 6), FP64 ----------------
+    forms["table6_fp64"] = measure_table6(flush, stream, tune_cache)
+
     # -- batched: the 512-member uneven batch in one launch vs 512 launches ---
     members = synth.workload_batch(512)
     Bt = BatchedRgCSR.from_csr_list(members, dtype=torch.float32, group_sizes="model")
@@ -839,6 +842,46 @@ def measure_forms(mats, cases, detail, dev, stream):
         "plain_512_launches_us": t_p, "plain_gbs": nb_batch / t_p / 1e3, "speedup_vs_plain": t_p / min(t_b, t_d)}
     del Bt, members
     return forms
+
+
+def measure_table6(flush, stream, tune_cache):
+    """Stand-ins for Hohn/fd18, AMD/G2_circuit, IBM_EDA/trans4 and Rajat/Raj1
+    (their rows and longest / mean / shortest row length), FP64 like the
+    paper's Table 6: GFLOP/s of the paper's kernel at G = 128 (read-only x,
+    the paper's setting), of HYB, and of the autotuned RgCSR configuration,
+    with the artificial-zero share of each RgCSR layout."""
+    import torch
+    from paper_1012_2270_gb300 import _lib as L
+    from paper_1012_2270_gb300 import autotune
+    from paper_1012_2270_gb300.rgcsr import HybMatrix, RgCSRMatrix
+    out = {}
+    for name in synth.TABLE6_ROWS:
+        A = synth.table6_standin(name)
+        x = torch.from_numpy(synth.uniform_vector(A.n_cols, seed=0)).cuda()
+        y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        gf = lambda us: 2 * A.nnz / us / 1e3
+        M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val, A.n_cols, group_size=128, dtype=torch.float64)
+        t_paper = time_flushed(lambda: M.spmv(x, out=y, kernel=L.KERNEL_PAPER), 3, flush, stream)
+        pad_paper = M.artificial_zero_percent()
+        del M
+        H = HybMatrix.from_csr(A.rowptr, A.col, A.val, A.n_cols, dtype=torch.float64)
+        t_hyb = time_flushed(lambda: H.spmv(x, out=y), 10, flush, stream)
+        del H
+        cfg = autotune.tune(A.rowptr, A.col, A.val, A.n_cols, dtype=torch.float64, reps=8,
+                            use_cache=tune_cache)
+        T, kw = autotune.build(A.rowptr, A.col, A.val, A.n_cols, cfg, torch.float64)
+        t_tuned = time_flushed(lambda: T.spmv(x, out=y, **kw), 10, flush, stream)
+        L_ = A.row_lengths()
+        out[name] = {"rows": A.n_rows, "max": int(L_.max()), "mean": float(L_.mean()), "min": int(L_.min()),
+                     "nnz": A.nnz,
+                     "paper_kernel_G128": {"us": t_paper, "gflops": gf(t_paper), "artificial_zero_pct": pad_paper},
+                     "hyb": {"us": t_hyb, "gflops": gf(t_hyb)},
+                     "tuned": {"us": t_tuned, "gflops": gf(t_tuned), "artificial_zero_pct": T.artificial_zero_percent(),
+                               "config": {k: v for k, v in cfg.items() if k != "us"}},
+                     "paper_over_hyb": t_hyb / t_paper, "tuned_over_hyb": t_hyb / t_tuned}
+        del T
+        torch.cuda.empty_cache()
+    return out
 
 
 def measure_tables(mats, flush, stream):

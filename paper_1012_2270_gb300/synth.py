@@ -221,6 +221,69 @@ def uniform_matrix(n: int, k: int, seed: int = 0) -> np.ndarray:
     return np.random.default_rng(seed).uniform(-1.0, 1.0, (n, k))
 
 
+# Row statistics of the four matrices that Sec. 4.4.2 (Table 6) analyses:
+# rows, longest, mean and shortest row length.  The matrices themselves
+# (Hohn/fd18, AMD/G2_circuit, IBM_EDA/trans4 and Rajat/Raj1 of the UF
+# collection) are not available here; the stand-ins match these numbers.
+TABLE6_ROWS = {
+    "fd18": (16_248, 6, 3.860, 1),
+    "G2_circuit": (150_102, 6, 4.841, 2),
+    "trans4": (116_835, 114_190, 6.600, 1),
+    "Raj1": (263_743, 40_468, 4.938, 1),
+}
+
+
+def row_statistics_lengths(n: int, lmax: int, mean: float, lmin: int, rng) -> np.ndarray:
+    """n row lengths with longest lmax, shortest lmin and total round(mean n):
+    one row of lmax at a random position; the others lmin + Geometric - 1
+    with the mean the total needs, clipped to [lmin, min(lmax, 64)] and then
+    moved one entry at a time (random rows) until the total is met."""
+    total = int(round(mean * n))
+    cap = min(lmax, 64)
+    rest = total - lmax
+    if not (lmin * (n - 1) <= rest <= cap * (n - 1)):
+        raise ValueError("statistics not reachable")
+    target = rest / (n - 1)
+    L = np.clip(lmin - 1 + rng.geometric(1.0 / (target - lmin + 1.0), n - 1), lmin, cap).astype(np.int64)
+    diff = rest - int(L.sum())
+    while diff:
+        cand = np.flatnonzero(L < cap) if diff > 0 else np.flatnonzero(L > lmin)
+        pick = rng.choice(cand, min(abs(diff), cand.size), replace=False)
+        L[pick] += 1 if diff > 0 else -1
+        diff = rest - int(L.sum())
+    if L.min() > lmin:                       # keep one shortest row (moving its entries elsewhere)
+        i = int(np.argmin(L))
+        extra = int(L[i]) - lmin
+        L[i] = lmin
+        room = np.flatnonzero(L < cap)
+        L[rng.choice(room, extra, replace=False)] += 1
+    return np.insert(L, int(rng.integers(0, n)), lmax)
+
+
+def table6_standin(name: str, seed: int = 0, window: int = 65) -> CSRMatrix:
+    """Square stand-in for a Table 6 matrix.  Rows of at most 64 entries take
+    distinct sorted columns from a window of `window` columns around the
+    diagonal (local coupling, as in these PDE and circuit matrices); the
+    longest row takes distinct columns over the whole range.  Values
+    U[-1, 1]."""
+    n, lmax, mean, lmin = TABLE6_ROWS[name]
+    rng = np.random.default_rng(seed)
+    L = row_statistics_lengths(n, lmax, mean, lmin, rng)
+    rowptr = np.zeros(n + 1, np.int64)
+    np.cumsum(L, out=rowptr[1:])
+    col = np.empty(int(rowptr[-1]), np.int32)
+    short = L <= min(64, window)
+    rows = np.flatnonzero(short)
+    local = _distinct_sorted_columns(rng, L[short], window).astype(np.int64)
+    start = np.clip(rows - window // 2, 0, max(0, n - window))
+    dst = np.concatenate([np.arange(rowptr[i], rowptr[i + 1]) for i in rows]) if rows.size else np.zeros(0, np.int64)
+    col[dst] = (np.repeat(start, L[short]) + local).astype(np.int32)
+    for i in np.flatnonzero(~short):
+        col[rowptr[i]:rowptr[i + 1]] = np.sort(rng.choice(n, int(L[i]), replace=False))
+    val = rng.uniform(-1.0, 1.0, int(rowptr[-1]))
+    return CSRMatrix(n, n, rowptr, col, val, f"table6_{name}_s{seed}")
+
+
 # ---------------------------------------------------------------------------
 # Named workloads
 # ---------------------------------------------------------------------------

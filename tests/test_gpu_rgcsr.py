@@ -10,7 +10,7 @@ import oracle
 from helpers import TAU, assert_within_bound, rounded_values
 from paper_1012_2270_gb300 import synth
 from paper_1012_2270_gb300 import _lib as L
-from paper_1012_2270_gb300.rgcsr import RgCSRMatrix
+from paper_1012_2270_gb300.rgcsr import HybMatrix, RgCSRMatrix
 
 pytestmark = pytest.mark.gpu
 
@@ -363,3 +363,26 @@ def test_layout_with_big_groups(dtype, G, order):
     assert np.array_equal(M.columns.cpu().numpy(), lay.columns)
     assert np.array_equal(M.slot_to_csr.cpu().numpy(), lay.slot_to_csr)
     check_spmv(M, A, dtype, synth.uniform_vector(m, seed=1))
+
+
+@pytest.mark.parametrize("name", list(synth.TABLE6_ROWS))
+def test_table6_standins(name):
+    # the four matrix shapes of Sec. 4.4.2 (Table 6), FP64 as in the paper:
+    # layout at G = 128 (the paper's setting) against the oracle, and the SpMV
+    # of the paper's kernel at G = 128, the default at G = 32, the warp split,
+    # descending order with group tiles, and HYB, within tau |A||x|
+    A = synth.table6_standin(name)
+    x = synth.uniform_vector(A.n_cols, seed=11)
+    M = to_gpu_matrix(A, "f64", 128, slot_map=False)
+    rl, gp = oracle_sizes(A, 128)
+    assert np.array_equal(M.group_ptr.cpu().numpy(), gp) and np.array_equal(M.row_lengths.cpu().numpy(), rl)
+    check_spmv(M, A, "f64", x, kernel=L.KERNEL_PAPER)
+    M32 = to_gpu_matrix(A, "f64", 32, slot_map=False)
+    check_spmv(M32, A, "f64", x)
+    check_spmv(M32, A, "f64", x, kernel=L.KERNEL_SPLIT)
+    D = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val, A.n_cols, group_size=32, dtype=torch.float64,
+                             row_order="descending").tile_groups(64)
+    check_spmv(D, A, "f64", x)
+    H = HybMatrix.from_csr(A.rowptr, A.col, A.val, A.n_cols, dtype=torch.float64)
+    check_spmv(H, A, "f64", x)
+    assert device_status() == 0

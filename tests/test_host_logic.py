@@ -62,3 +62,23 @@ def test_heuristic_configuration():
     cfg = autotune.heuristic(pl.rowptr, torch.float64)
     assert cfg["row_order"] == "descending" and cfg["tiles"] == [64, 2]
     assert autotune.heuristic(pl.rowptr, torch.float32)["tiles"] == [64, 3]
+
+
+@pytest.mark.parametrize("name", list(synth.TABLE6_ROWS))
+def test_table6_standins_match_the_table(name):
+    # Sec. 4.4.2, Table 6: rows and longest / mean / shortest row length of
+    # Hohn/fd18, AMD/G2_circuit, IBM_EDA/trans4 and Rajat/Raj1 (the table
+    # prints the mean to three decimals)
+    printed = {"fd18": (16_248, 6, "3.860", 1), "G2_circuit": (150_102, 6, "4.841", 2),
+               "trans4": (116_835, 114_190, "6.600", 1), "Raj1": (263_743, 40_468, "4.938", 1)}[name]
+    A = synth.table6_standin(name)
+    L = np.diff(A.rowptr)
+    assert (A.n_rows, int(L.max()), f"{L.mean():.3f}", int(L.min())) == printed
+    assert A.n_cols == A.n_rows and A.col.dtype == np.int32
+    assert A.col.min() >= 0 and A.col.max() < A.n_cols
+    d = np.diff(A.col.astype(np.int64))
+    same_row = np.ones(A.nnz - 1, bool)
+    same_row[A.rowptr[1:-1] - 1] = False                               # pairs that straddle a row end
+    assert (d[same_row] > 0).all()                                     # distinct, ascending within each row
+    B2 = synth.table6_standin(name)
+    assert np.array_equal(A.col, B2.col) and np.array_equal(A.val, B2.val)   # seeded
