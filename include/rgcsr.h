@@ -236,8 +236,9 @@ int rgcsr_spmv_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *S, const 
  * coalesced).  A group whose longest row K_g exceeds `tile` slot-rows is cut
  * into ceil(K_g / tile) tasks of at most `tile` slot-rows each; tasks of
  * one group write per-row partial sums, and the last of them to finish
- * (an arrival counter per group, no waiting) adds the partials in task
- * order and writes y, so the result does not depend on scheduling.  With
+ * (an arrival counter per group, no waiting) adds the partials in a fixed
+ * order (task q into the (q mod 8)-th of eight sums, then a fixed tree) and
+ * writes y, so the result does not depend on scheduling.  With
  * rows in descending length order (row_perm, Sec. 4.4.2) the groups are
  * dense and every warp's work is bounded by `tile` slot-rows, which removes
  * the long-row imbalance that the paper names as the format's weak point.

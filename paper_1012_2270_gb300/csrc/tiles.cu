@@ -8,7 +8,8 @@
 // consecutive words (the format's column-major slab), so each load of the
 // warp is one coalesced segment.  A group longer than one tile is cut into
 // several tasks; they write per-row partial sums and the last task of the
-// group to arrive (an atomic counter, no waiting) sums them in task order.
+// group to arrive (an atomic counter, no waiting) sums them in a fixed order
+// (eight interleaved sums over the tasks, then a fixed tree).
 //
 // Task numbering: task g < n_groups is the first tile of group g (no lookup
 // needed); task n_groups + e is extra tile e, of group extra_group[e], and
@@ -43,6 +44,23 @@ __global__ void tile_fill_kernel(int64_t n_groups, const int64_t *__restrict__ f
 
 template <typename A>
 __device__ __forceinline__ A ld_coherent(const A *p) { return __ldcg(p); }
+
+// Sum of a row's nt tile partials (stride 32 between consecutive tiles):
+// eight interleaved sums -- tile q goes to sum q mod 8, so eight loads are
+// in flight at once -- added in a fixed tree.  Deterministic for a given nt.
+template <typename A>
+__device__ __forceinline__ A sum_partials(const A *p, int64_t nt) {
+    A s[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] = 0;
+    int64_t q = 0;
+    for (; q + 8 <= nt; q += 8) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s[k] += ld_coherent(p + (q + k) * 32);
+    }
+    for (int k = 0; q < nt; ++q, ++k) s[k] += ld_coherent(p + q * 32);
+    return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+}
 
 template <typename V, int U, int MIN_BLOCKS>
 __global__ void __launch_bounds__(kTileThreads, MIN_BLOCKS)
@@ -101,7 +119,7 @@ rgcsr_spmv_tiles_kernel(int64_t n, int32_t G, int32_t C, int64_t n_groups, int64
             continue;
         }
         // split group: publish this tile's partials; the last tile to
-        // arrive adds them in tile order (deterministic) and resets the
+        // arrive adds them in a fixed order (deterministic) and resets the
         // group's counter for the next launch.
         const int64_t pb = __ldg(part_base + g);
         if (active) partials[(pb + k) * 32 + lane] = acc;
@@ -116,8 +134,7 @@ rgcsr_spmv_tiles_kernel(int64_t n, int32_t G, int32_t C, int64_t n_groups, int64
         if (!last) continue;
         __threadfence();
         if (active) {
-            A s = 0;
-            for (int64_t q = 0; q < nt; ++q) s += ld_coherent(partials + (pb + q) * 32 + lane);
+            const A s = sum_partials(partials + pb * 32 + lane, nt);
             y[orow] = VT<V>::scaled ? s * sc : s;
         }
         if (lane == 0) arrivals[g] = 0;
@@ -246,8 +263,7 @@ rgcsr_spmv_tiles_pipe_kernel(int64_t n, int32_t G, int32_t C, int64_t n_groups, 
             if (last) {
                 __threadfence();
                 if (active) {
-                    A s = 0;
-                    for (int q = 0; q < cur.nt; ++q) s += ld_coherent(partials + (cur.pb + q) * 32 + lane);
+                    const A s = sum_partials(partials + cur.pb * 32 + lane, (int64_t)cur.nt);
                     y[cur.orow] = VT<V>::scaled ? s * cur.sc : s;
                 }
                 if (lane == 0) arrivals[cur.g] = 0;
