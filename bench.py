@@ -65,6 +65,7 @@ def parse():
                    help="CPU work of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip HYB and the other forms")
+    p.add_argument("--forms", default="", help="comma-separated subset of the forms to run (default: all)")
     p.add_argument("--tune-cache", default=None,
                    help="JSON file for the tuned configurations: read if present, else written "
                         "(lets a profiled run use the configurations of an unprofiled one)")
@@ -513,7 +514,8 @@ def run_ours(args):
     # ---- forms beside plain ----
     forms = {}
     if not args.no_forms and rank == 0:
-        forms = measure_forms(mats, cases, detail, dev, stream, tune_cache=bool(args.tune_cache))
+        forms = measure_forms(mats, cases, detail, dev, stream, tune_cache=bool(args.tune_cache),
+                              only=set(args.forms.split(",")) if args.forms else None)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -597,7 +599,10 @@ def max_scaled_error(y, y_ref, absy):
     return float((err[ok] / den[ok]).max()) if bool(ok.any()) else 0.0
 
 
-def measure_forms(mats, cases, detail, dev, stream, tune_cache=False):
+def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None):
+    """The forms beside the plain SpMV; `only` (a set of names: hyb,
+    quantized, spmm, backward, ir_cg, jacobi, conversion, group_size_sweep,
+    table6, batched) limits them, None runs all."""
     import torch
     from paper_1012_2270_gb300 import solvers
     from paper_1012_2270_gb300.autograd import SparseOperator, spmm
@@ -610,237 +615,255 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False):
     forms = {}
     flush = torch.ones(64 << 20, dtype=torch.float32, device=dev)
     by = {c["key"]: c for c in cases}
+    b = [m for m in mats if m[0] == "b"][0][1]
+
+    def want(name):
+        return only is None or name in only
+
     TT = {"f32": torch.float32, "f64": torch.float64}
 
-    # -- HYB (ELL + COO), the paper's comparison format -----------------------
-    hyb = []
-    for name, A, x in mats:
-        for dt in DTYPES:
-            H = HybMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dt]), A.n_cols, dtype=TT[dt])
-            c = by[f"{name}_{dt}"]
-            hyb.append((c, H, torch.empty_like(c["y"])))
-    us = time_rotating([lambda h=h: h[1].spmv(h[0]["x"], out=h[2]) for h in hyb], 30, stream)
-    forms["hyb"] = {}
-    for (c, H, _), t in zip(hyb, us):
-        A = c["A"]
-        nb = roofline.hyb_spmv_bytes(A.n_rows, A.n_cols, A.nnz, H.nnz_coo, VB[c["dt"]])
-        forms["hyb"][c["key"]] = {"gbs": nb / t / 1e3, "gflops": 2 * A.nnz / t / 1e3, "us": t,
-                                  "ell_width": H.ell_width, "nnz_coo": H.nnz_coo,
-                                  "rgcsr_speedup": t / detail[c["key"]]["us"]}
-    del hyb
+    if want("hyb"):
+        # -- HYB (ELL + COO), the paper's comparison format -----------------------
+        hyb = []
+        for name, A, x in mats:
+            for dt in DTYPES:
+                H = HybMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dt]), A.n_cols, dtype=TT[dt])
+                c = by[f"{name}_{dt}"]
+                hyb.append((c, H, torch.empty_like(c["y"])))
+        us = time_rotating([lambda h=h: h[1].spmv(h[0]["x"], out=h[2]) for h in hyb], 30, stream)
+        forms["hyb"] = {}
+        for (c, H, _), t in zip(hyb, us):
+            A = c["A"]
+            nb = roofline.hyb_spmv_bytes(A.n_rows, A.n_cols, A.nnz, H.nnz_coo, VB[c["dt"]])
+            forms["hyb"][c["key"]] = {"gbs": nb / t / 1e3, "gflops": 2 * A.nnz / t / 1e3, "us": t,
+                                      "ell_width": H.ell_width, "nnz_coo": H.nnz_coo,
+                                      "rgcsr_speedup": t / detail[c["key"]]["us"]}
+        del hyb
 
-    # -- reduced-precision values (bf16 / fp16 + per-row scale) ----------------
-    # The error is taken against the library's FP64 product (itself within
-    # 1e-12 |A||x| of the CPU oracle in the parity tests), scaled by |A||x|.
-    quant, ref = [], {}
-    for name in ("a", "b", "c"):
-        c64, c32 = by[f"{name}_f64"], by[f"{name}_f32"]
-        A = c32["A"]
-        absA = RgCSRMatrix.from_csr(A.rowptr, A.col, np.abs(A.val), A.n_cols, dtype=torch.float64)
-        ref[name] = (c64["M"].spmv(c64["x"]), absA.spmv(c64["x"].abs()))
-        del absA
-        for fmt in ("bf16", "f16"):
-            Q = c64["M"].quantized(fmt)
-            # Q has c64's layout; take the FP32 case's schedule when the two
-            # layouts agree (Q computes in float), else c64's
-            same = all(c32["config"].get(k) == c64["config"].get(k) for k in ("group_size", "row_order"))
-            Q.copy_schedule(c32["M"] if same else c64["M"])
-            yq = torch.empty(A.n_rows, dtype=torch.float32, device=dev)
-            # kernel: the default, or (G = 32, no schedule) 16-byte loads, whichever is faster here
-            kws = [{}]
-            if Q.group_size == 32 and Q._tiles is None and Q._long is None:
-                kws += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4)]
-            kw = min(kws, key=lambda k: autotune._time(lambda: Q.spmv(c32["x"], out=yq, **k), 8, flush))
-            quant.append((name, fmt, Q, c32["x"], yq, A, kw))
-    us = time_rotating([lambda q=q: q[2].spmv(q[3], out=q[4], **q[6]) for q in quant], 30, stream)
-    forms["quantized"] = {}
-    for (name, fmt, Q, x32, y, A, kw), t in zip(quant, us):
-        nb = roofline.rgcsr_spmv_bytes(A.n_rows, A.n_cols, A.nnz, Q.s.n_groups, 2, x_bytes=4, row_scale=True)
-        y64, absy = ref[name]
-        forms["quantized"][f"{name}_{fmt}"] = {
-            "gbs": nb / t / 1e3, "gflops": 2 * A.nnz / t / 1e3, "us": t,
-            "speedup_vs_f32": detail[f"{name}_f32"]["us"] / t, "kernel": kw or "default",
-            "max_err_over_absAx_vs_f64": max_scaled_error(y, y64, absy)}
-    del quant, ref
+    if want("quantized"):
+        # -- reduced-precision values (bf16 / fp16 + per-row scale) ----------------
+        # The error is taken against the library's FP64 product (itself within
+        # 1e-12 |A||x| of the CPU oracle in the parity tests), scaled by |A||x|.
+        quant, ref = [], {}
+        for name in ("a", "b", "c"):
+            c64, c32 = by[f"{name}_f64"], by[f"{name}_f32"]
+            A = c32["A"]
+            absA = RgCSRMatrix.from_csr(A.rowptr, A.col, np.abs(A.val), A.n_cols, dtype=torch.float64)
+            ref[name] = (c64["M"].spmv(c64["x"]), absA.spmv(c64["x"].abs()))
+            del absA
+            for fmt in ("bf16", "f16"):
+                Q = c64["M"].quantized(fmt)
+                # Q has c64's layout; take the FP32 case's schedule when the two
+                # layouts agree (Q computes in float), else c64's
+                same = all(c32["config"].get(k) == c64["config"].get(k) for k in ("group_size", "row_order"))
+                Q.copy_schedule(c32["M"] if same else c64["M"])
+                yq = torch.empty(A.n_rows, dtype=torch.float32, device=dev)
+                # kernel: the default, or (G = 32, no schedule) 16-byte loads, whichever is faster here
+                kws = [{}]
+                if Q.group_size == 32 and Q._tiles is None and Q._long is None:
+                    kws += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4)]
+                kw = min(kws, key=lambda k: autotune._time(lambda: Q.spmv(c32["x"], out=yq, **k), 8, flush))
+                quant.append((name, fmt, Q, c32["x"], yq, A, kw))
+        us = time_rotating([lambda q=q: q[2].spmv(q[3], out=q[4], **q[6]) for q in quant], 30, stream)
+        forms["quantized"] = {}
+        for (name, fmt, Q, x32, y, A, kw), t in zip(quant, us):
+            nb = roofline.rgcsr_spmv_bytes(A.n_rows, A.n_cols, A.nnz, Q.s.n_groups, 2, x_bytes=4, row_scale=True)
+            y64, absy = ref[name]
+            forms["quantized"][f"{name}_{fmt}"] = {
+                "gbs": nb / t / 1e3, "gflops": 2 * A.nnz / t / 1e3, "us": t,
+                "speedup_vs_f32": detail[f"{name}_f32"]["us"] / t, "kernel": kw or "default",
+                "max_err_over_absAx_vs_f64": max_scaled_error(y, y64, absy)}
+        del quant, ref
 
-    # -- multi-RHS SpMM on (b) ------------------------------------------------
-    # natural row order, G = 1 with the long-row schedule (T = 32, 256-slot
-    # segments): the lanes-per-row kernels; the thread-per-row kernel at the
-    # byte model's group size beside it
-    b = [m for m in mats if m[0] == "b"][0][1]
-    Mb = RgCSRMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32,
-                              group_size=1).split_long_rows(32, 256)
-    Gm = model_group_size(b.rowptr, 4)
-    Mt = RgCSRMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32,
-                              group_size=Gm)
-    # and G = 32 in descending row order with group tiles (the tiled kernels)
-    Md = RgCSRMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32,
-                              group_size=32, row_order="descending").tile_groups(64)
-    Hb = HybMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32)
-    forms["spmm_b_f32"] = {"configs": {"lanes_per_row": "G=1, long-row schedule T=32 S=256",
-                                       "tiles": "G=32, descending row order, group tiles C=64",
-                                       "thread_per_row": f"G={Gm}"}}
-    for k in (1, 4, 8, 16, 32):
-        X = torch.rand(b.n_cols, k, device=dev)
-        Y = torch.empty(b.n_rows, k, device=dev)
-        ts = {"lanes_per_row": time_flushed(lambda: Mb.spmm(X, out=Y), 10, flush, stream),
-              "tiles": time_flushed(lambda: Md.spmm(X, out=Y), 10, flush, stream),
-              "thread_per_row": time_flushed(lambda: Mt.spmm(X, out=Y), 5, flush, stream)}
-        best = min(ts, key=ts.get)
-        t = ts[best]
-        nb = roofline.spmm_bytes(b.n_rows, b.n_cols, b.nnz, (b.n_rows + GROUP - 1) // GROUP, 4, k)
-        forms["spmm_b_f32"][f"k{k}"] = {"gbs": nb / t / 1e3, "gflops": 2 * b.nnz * k / t / 1e3, "us": t,
-                                        "best": best, "us_by_config": ts,
-                                        "hyb_us": time_flushed(lambda: Hb.spmm(X, out=Y), 5, flush, stream)}
-        del X, Y
-    del Mb, Mt, Md, Hb
+    if want("spmm"):
+        # -- multi-RHS SpMM on (b) ------------------------------------------------
+        # natural row order, G = 1 with the long-row schedule (T = 32, 256-slot
+        # segments): the lanes-per-row kernels; the thread-per-row kernel at the
+        # byte model's group size beside it
+        b = [m for m in mats if m[0] == "b"][0][1]
+        Mb = RgCSRMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32,
+                                  group_size=1).split_long_rows(32, 256)
+        Gm = model_group_size(b.rowptr, 4)
+        Mt = RgCSRMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32,
+                                  group_size=Gm)
+        # and G = 32 in descending row order with group tiles (the tiled kernels)
+        Md = RgCSRMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32,
+                                  group_size=32, row_order="descending").tile_groups(64)
+        Hb = HybMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32)
+        forms["spmm_b_f32"] = {"configs": {"lanes_per_row": "G=1, long-row schedule T=32 S=256",
+                                           "tiles": "G=32, descending row order, group tiles C=64",
+                                           "thread_per_row": f"G={Gm}"}}
+        for k in (1, 4, 8, 16, 32):
+            X = torch.rand(b.n_cols, k, device=dev)
+            Y = torch.empty(b.n_rows, k, device=dev)
+            ts = {}
+            for cfg_name, Mx, reps in (("lanes_per_row", Mb, 10), ("tiles", Md, 10), ("thread_per_row", Mt, 5)):
+                torch.cuda.nvtx.range_push(f"spmm_k{k}_{cfg_name}")         # a profiler can pick one out
+                ts[cfg_name] = time_flushed(lambda: Mx.spmm(X, out=Y), reps, flush, stream)
+                torch.cuda.nvtx.range_pop()
+            best = min(ts, key=ts.get)
+            t = ts[best]
+            nb = roofline.spmm_bytes(b.n_rows, b.n_cols, b.nnz, (b.n_rows + GROUP - 1) // GROUP, 4, k)
+            forms["spmm_b_f32"][f"k{k}"] = {"gbs": nb / t / 1e3, "gflops": 2 * b.nnz * k / t / 1e3, "us": t,
+                                            "best": best, "us_by_config": ts,
+                                            "hyb_us": time_flushed(lambda: Hb.spmm(X, out=Y), 5, flush, stream)}
+            del X, Y
+        del Mb, Mt, Md, Hb
 
-    # -- backward of Y = A X on (b), batch of 8 right-hand sides ---------------
-    G = 32
-    op = SparseOperator(b.rowptr, b.col, b.n_cols, dtype=torch.float32, group_size=G, row_order="descending",
-                        tiles=64)
-    vals = torch.from_numpy(b.val.astype(np.float32)).to(dev).requires_grad_(True)
-    X = torch.rand(b.n_cols, 8, device=dev, requires_grad=True)
+    if want("backward"):
+        # -- backward of Y = A X on (b), batch of 8 right-hand sides ---------------
+        G = 32
+        op = SparseOperator(b.rowptr, b.col, b.n_cols, dtype=torch.float32, group_size=G, row_order="descending",
+                            tiles=64)
+        vals = torch.from_numpy(b.val.astype(np.float32)).to(dev).requires_grad_(True)
+        X = torch.rand(b.n_cols, 8, device=dev, requires_grad=True)
 
-    def fwd():
-        with torch.no_grad():
-            return spmm(op, vals, X)
+        def fwd():
+            with torch.no_grad():
+                return spmm(op, vals, X)
 
-    def fwd_bwd():
-        vals.grad = None
-        X.grad = None
-        Y = spmm(op, vals, X)
-        (Y * Y).sum().backward()
-    t_f = time_flushed(fwd, 10, flush, stream)
-    t_fb = time_flushed(fwd_bwd, 10, flush, stream)
-    forms["backward_b_k8_f32"] = {"group_size": G, "schedule": "descending row order, group tiles C=64", "forward_us": t_f, "forward_backward_us": t_fb,
-                                  "backward_over_forward": (t_fb - t_f) / t_f}
-    del op, vals, X
+        def fwd_bwd():
+            vals.grad = None
+            X.grad = None
+            Y = spmm(op, vals, X)
+            (Y * Y).sum().backward()
+        t_f = time_flushed(fwd, 10, flush, stream)
+        t_fb = time_flushed(fwd_bwd, 10, flush, stream)
+        forms["backward_b_k8_f32"] = {"group_size": G, "schedule": "descending row order, group tiles C=64", "forward_us": t_f, "forward_backward_us": t_fb,
+                                      "backward_over_forward": (t_fb - t_f) / t_f}
+        del op, vals, X
 
-    # -- mixed-precision iterative refinement CG, Poisson 128^3 ---------------
-    a = [m for m in mats if m[0] == "a"][0][1]
-    M64 = by["a_f64"]["M"]
-    rhs = torch.from_numpy(synth.uniform_vector(a.n_rows, seed=0)).to(dev)
-    lo = M64.quantized("bf16")
-    e0, e1 = _ev()
-    e0.record(stream)
-    x_ir, outer, inner, rel = solvers.ir_cg(M64, lo, rhs, outer_tol=1e-10, max_outer=50, inner_tol=1e-4,
-                                             max_inner=500)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_ir = e0.elapsed_time(e1)
-    e0, e1 = _ev()
-    e0.record(stream)
-    x64, its64, rel64 = solvers.cg(M64, rhs, rel_tol=1e-10, max_iter=5000)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    forms["ir_cg_poisson128"] = {
-        "ms": t_ir, "corrections": outer, "inner_iterations": inner, "final_rel_residual": rel,
-        "fp64_cg_ms": e0.elapsed_time(e1), "fp64_cg_iterations": its64,
-        "rel_diff_vs_fp64_cg": float((x_ir - x64).norm() / x64.norm())}
-    del lo, x_ir, x64
-
-    # -- gradient through 100 damped-Jacobi steps, 96^3, checkpoint every 10 --
-    J = synth.laplacian_3d(96)
-    opj = SparseOperator(J.rowptr, J.col, J.n_cols, dtype=torch.float32)
-    vj = torch.from_numpy(J.val.astype(np.float32)).to(dev).requires_grad_(True)
-    bj = torch.from_numpy(synth.uniform_vector(J.n_rows, seed=0).astype(np.float32)).to(dev).requires_grad_(True)
-    dinv = torch.full((J.n_rows,), 1.0 / 6.0, device=dev)
-    res = {}
-    for ck in (0, 10):
-        def run():
-            vj.grad = None
-            bj.grad = None
-            xj = solvers.jacobi(opj, vj, bj, dinv, 2.0 / 3.0, 100, checkpoint_every=ck)
-            (xj * xj).sum().backward()
-        run()                                   # warm-up
-        torch.cuda.synchronize()
-        torch.cuda.reset_peak_memory_stats()
-        base = torch.cuda.memory_allocated()
+    if want("ir_cg"):
+        # -- mixed-precision iterative refinement CG, Poisson 128^3 ---------------
+        a = [m for m in mats if m[0] == "a"][0][1]
+        M64 = by["a_f64"]["M"]
+        rhs = torch.from_numpy(synth.uniform_vector(a.n_rows, seed=0)).to(dev)
+        lo = M64.quantized("bf16")
         e0, e1 = _ev()
         e0.record(stream)
-        run()
+        x_ir, outer, inner, rel = solvers.ir_cg(M64, lo, rhs, outer_tol=1e-10, max_outer=50, inner_tol=1e-4,
+                                                 max_inner=500)
         e1.record(stream)
         torch.cuda.synchronize()
-        res["checkpoint_every_10" if ck else "no_checkpoint"] = {
-            "ms": e0.elapsed_time(e1),
-            "peak_extra_mem_mb": (torch.cuda.max_memory_allocated() - base) / 2**20}
-    forms["jacobi_grad_96_f32"] = res
-    del opj
+        t_ir = e0.elapsed_time(e1)
+        e0, e1 = _ev()
+        e0.record(stream)
+        x64, its64, rel64 = solvers.cg(M64, rhs, rel_tol=1e-10, max_iter=5000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        forms["ir_cg_poisson128"] = {
+            "ms": t_ir, "corrections": outer, "inner_iterations": inner, "final_rel_residual": rel,
+            "fp64_cg_ms": e0.elapsed_time(e1), "fp64_cg_iterations": its64,
+            "rel_diff_vs_fp64_cg": float((x_ir - x64).norm() / x64.norm())}
+        del lo, x_ir, x64
 
-    # -- conversion CSR -> RgCSR on the device (plan + convert; FP32 values,
-    # CSR already in HBM): bytes = CSR read + RgCSR written ----------------
-    conv = {}
-    for name, A, x in mats:
-        rp = torch.from_numpy(A.rowptr).to(dev)
-        cl = torch.from_numpy(A.col).to(dev)
-        vl = torch.from_numpy(A.val.astype(np.float32)).to(dev)
-        order = "descending" if name == "b" else None
-        ts = []
-        for rep in range(6):
+    if want("jacobi"):
+        # -- gradient through 100 damped-Jacobi steps, 96^3, checkpoint every 10 --
+        J = synth.laplacian_3d(96)
+        opj = SparseOperator(J.rowptr, J.col, J.n_cols, dtype=torch.float32)
+        vj = torch.from_numpy(J.val.astype(np.float32)).to(dev).requires_grad_(True)
+        bj = torch.from_numpy(synth.uniform_vector(J.n_rows, seed=0).astype(np.float32)).to(dev).requires_grad_(True)
+        dinv = torch.full((J.n_rows,), 1.0 / 6.0, device=dev)
+        res = {}
+        for ck in (0, 10):
+            def run():
+                vj.grad = None
+                bj.grad = None
+                xj = solvers.jacobi(opj, vj, bj, dinv, 2.0 / 3.0, 100, checkpoint_every=ck)
+                (xj * xj).sum().backward()
+            run()                                   # warm-up
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            M = RgCSRMatrix.from_csr(rp, cl, vl, A.n_cols, group_size=32, dtype=torch.float32, row_order=order)
+            torch.cuda.reset_peak_memory_stats()
+            base = torch.cuda.memory_allocated()
+            e0, e1 = _ev()
+            e0.record(stream)
+            run()
+            e1.record(stream)
             torch.cuda.synchronize()
-            if rep:
-                ts.append(1e6 * (time.perf_counter() - t0))
-        t = statistics.median(ts)
-        nb = A.nnz * 8 + (A.n_rows + 1) * 8 + M.n_stored * 8 + A.n_rows * 4 + (M.s.n_groups + 1) * 8
-        conv[name] = {"us": t, "gbs": nb / t / 1e3, "row_order": order or "natural",
-                      "n_stored": M.n_stored, "note": "host wall time incl. the plan's one stream sync"}
-        del M, rp, cl, vl
-    forms["conversion_f32"] = conv
+            res["checkpoint_every_10" if ck else "no_checkpoint"] = {
+                "ms": e0.elapsed_time(e1),
+                "peak_extra_mem_mb": (torch.cuda.max_memory_allocated() - base) / 2**20}
+        forms["jacobi_grad_96_f32"] = res
+        del opj
 
-    # -- group-size sweep (the paper's Table 4 on these matrices), x read path
-    # on/off (the texture study of Sec. 4.3) and sliced ELLPACK (Sec. 3.4) --
-    forms.update(measure_tables(mats, flush, stream))
+    if want("conversion"):
+        # -- conversion CSR -> RgCSR on the device (plan + convert; FP32 values,
+        # CSR already in HBM): bytes = CSR read + RgCSR written ----------------
+        conv = {}
+        for name, A, x in mats:
+            rp = torch.from_numpy(A.rowptr).to(dev)
+            cl = torch.from_numpy(A.col).to(dev)
+            vl = torch.from_numpy(A.val.astype(np.float32)).to(dev)
+            order = "descending" if name == "b" else None
+            ts = []
+            for rep in range(6):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                M = RgCSRMatrix.from_csr(rp, cl, vl, A.n_cols, group_size=32, dtype=torch.float32, row_order=order)
+                torch.cuda.synchronize()
+                if rep:
+                    ts.append(1e6 * (time.perf_counter() - t0))
+            t = statistics.median(ts)
+            nb = A.nnz * 8 + (A.n_rows + 1) * 8 + M.n_stored * 8 + A.n_rows * 4 + (M.s.n_groups + 1) * 8
+            conv[name] = {"us": t, "gbs": nb / t / 1e3, "row_order": order or "natural",
+                          "n_stored": M.n_stored, "note": "host wall time incl. the plan's one stream sync"}
+            del M, rp, cl, vl
+        forms["conversion_f32"] = conv
 
-    # -- the four matrix shapes of Sec. 4.4.2 (Table 6), FP64 ----------------
-    forms["table6_fp64"] = measure_table6(flush, stream, tune_cache)
+    if want("group_size_sweep"):
+        # -- group-size sweep (the paper's Table 4 on these matrices), x read path
+        # on/off (the texture study of Sec. 4.3) and sliced ELLPACK (Sec. 3.4) --
+        forms.update(measure_tables(mats, flush, stream))
 
-    # -- batched: the 512-member uneven batch in one launch vs 512 launches ---
-    members = synth.workload_batch(512)
-    Bt = BatchedRgCSR.from_csr_list(members, dtype=torch.float32, group_sizes="model")
-    xb = torch.rand(Bt.n_cols_total, device=dev)
-    yb = torch.empty(Bt.n_rows_total, device=dev)
-    g = Bt.capture(xb, yb, repeats=1)
-    nb_batch = sum(roofline.rgcsr_spmv_bytes(m.n_rows, m.n_cols, m.nnz, (m.n_rows + GROUP - 1) // GROUP, 4)
-                   for m in members)
-    t_b = time_flushed(lambda: g.replay(), 10, flush, stream)
-    plain = [RgCSRMatrix.from_csr(m.rowptr, m.col, m.val, m.n_cols, group_size=Gm, dtype=torch.float32)
-             for m, Gm in zip(members, Bt.group_sizes)]
-    xs = [xb[Bt.member_slices(i)[0]] for i in range(len(members))]
-    ys = [yb[Bt.member_slices(i)[1]] for i in range(len(members))]
-    gp = torch.cuda.CUDAGraph()
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        for M, xi, yi in zip(plain, xs, ys):
-            M.spmv(xi, out=yi)
-        side.synchronize()
-        with torch.cuda.graph(gp, stream=side):
+    if want("table6"):
+        # -- the four matrix shapes of Sec. 4.4.2 (Table 6), FP64 ----------------
+        forms["table6_fp64"] = measure_table6(flush, stream, tune_cache)
+
+    if want("batched"):
+        # -- batched: the 512-member uneven batch in one launch vs 512 launches ---
+        members = synth.workload_batch(512)
+        Bt = BatchedRgCSR.from_csr_list(members, dtype=torch.float32, group_sizes="model")
+        xb = torch.rand(Bt.n_cols_total, device=dev)
+        yb = torch.empty(Bt.n_rows_total, device=dev)
+        g = Bt.capture(xb, yb, repeats=1)
+        nb_batch = sum(roofline.rgcsr_spmv_bytes(m.n_rows, m.n_cols, m.nnz, (m.n_rows + GROUP - 1) // GROUP, 4)
+                       for m in members)
+        t_b = time_flushed(lambda: g.replay(), 10, flush, stream)
+        plain = [RgCSRMatrix.from_csr(m.rowptr, m.col, m.val, m.n_cols, group_size=Gm, dtype=torch.float32)
+                 for m, Gm in zip(members, Bt.group_sizes)]
+        xs = [xb[Bt.member_slices(i)[0]] for i in range(len(members))]
+        ys = [yb[Bt.member_slices(i)[1]] for i in range(len(members))]
+        gp = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
             for M, xi, yi in zip(plain, xs, ys):
-                M.spmv(xi, out=yi, stream=side)
-    torch.cuda.current_stream().wait_stream(side)
-    t_p = time_flushed(lambda: gp.replay(), 10, flush, stream)
-    del plain, gp
-    # the same batch as one block-diagonal matrix, rows in descending length
-    # order over the whole batch, group tiles
-    bd = {}
-    for tile, var in ((64, 0), (64, 1), (32, 1)):
-        Bd = BlockDiagonalBatch.from_csr_list(members, dtype=torch.float32, tile=tile, variant=var)
-        gd = Bd.capture(xb, yb, repeats=1)
-        bd[f"tiles_{tile}_v{var}"] = time_flushed(lambda: gd.replay(), 10, flush, stream)
-        del Bd, gd
-        torch.cuda.empty_cache()
-    best = min(bd, key=bd.get)
-    t_d = bd[best]
-    forms["batched_512_f32"] = {
-        "members": len(members), "rows": Bt.n_rows_total, "nnz": Bt.nnz,
-        "gbs": nb_batch / min(t_b, t_d) / 1e3, "gflops": 2 * Bt.nnz / min(t_b, t_d) / 1e3, "us": min(t_b, t_d),
-        "per_member_kernel_us": t_b, "block_diagonal_us": bd, "block_diagonal_best": best,
-        "plain_512_launches_us": t_p, "plain_gbs": nb_batch / t_p / 1e3, "speedup_vs_plain": t_p / min(t_b, t_d)}
-    del Bt, members
+                M.spmv(xi, out=yi)
+            side.synchronize()
+            with torch.cuda.graph(gp, stream=side):
+                for M, xi, yi in zip(plain, xs, ys):
+                    M.spmv(xi, out=yi, stream=side)
+        torch.cuda.current_stream().wait_stream(side)
+        t_p = time_flushed(lambda: gp.replay(), 10, flush, stream)
+        del plain, gp
+        # the same batch as one block-diagonal matrix, rows in descending length
+        # order over the whole batch, group tiles
+        bd = {}
+        for tile, var in ((64, 0), (64, 1), (32, 1)):
+            Bd = BlockDiagonalBatch.from_csr_list(members, dtype=torch.float32, tile=tile, variant=var)
+            gd = Bd.capture(xb, yb, repeats=1)
+            bd[f"tiles_{tile}_v{var}"] = time_flushed(lambda: gd.replay(), 10, flush, stream)
+            del Bd, gd
+            torch.cuda.empty_cache()
+        best = min(bd, key=bd.get)
+        t_d = bd[best]
+        forms["batched_512_f32"] = {
+            "members": len(members), "rows": Bt.n_rows_total, "nnz": Bt.nnz,
+            "gbs": nb_batch / min(t_b, t_d) / 1e3, "gflops": 2 * Bt.nnz / min(t_b, t_d) / 1e3, "us": min(t_b, t_d),
+            "per_member_kernel_us": t_b, "block_diagonal_us": bd, "block_diagonal_best": best,
+            "plain_512_launches_us": t_p, "plain_gbs": nb_batch / t_p / 1e3, "speedup_vs_plain": t_p / min(t_b, t_d)}
+        del Bt, members
+
     return forms
 
 
