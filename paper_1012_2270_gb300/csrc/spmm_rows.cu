@@ -190,8 +190,8 @@ int spmm_rows_t(const rgcsr_matrix *M, const rgcsr_long_rows *L, int k, const ty
         A *Yc = Y + c0;
         int st, w;
         if (left >= 32) {
-            st = vec ? launch_chunk_rows<V, 8, 4, 1, true>(M, L, Xc, ldx, Yc, ldy, part, s)
-                     : launch_chunk_rows<V, 8, 4, 1, false>(M, L, Xc, ldx, Yc, ldy, part, s);
+            st = vec ? launch_chunk_rows<V, 8, 4, 2, true>(M, L, Xc, ldx, Yc, ldy, part, s)
+                     : launch_chunk_rows<V, 8, 4, 2, false>(M, L, Xc, ldx, Yc, ldy, part, s);
             w = 32;
         } else if (left >= 16) {
             st = vec ? launch_chunk_rows<V, 4, 4, 2, true>(M, L, Xc, ldx, Yc, ldy, part, s)
