@@ -134,8 +134,9 @@ def kernel_name(cfg, M, A, dt):
 
 def measured_traffic(kernel, cases):
     """DRAM bytes per launch of `kernel` (mean over the cases that ran it)
-    from the committed ncu summary, or None if a case is missing, ran
-    another kernel, or the kernel's source changed since the capture."""
+    from the committed ncu summary (case -> kernel -> bytes), or None if a
+    case has no entry for that kernel or the kernel's source changed since
+    the capture."""
     import hashlib
     try:
         table = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
@@ -145,8 +146,8 @@ def measured_traffic(kernel, cases):
     for c in cases:
         if c["kernel"] != kernel:
             continue
-        e = table.get(c["key"])
-        if not e or e.get("kernel") != kernel:
+        e = (table.get(c["key"]) or {}).get(kernel)
+        if not e:
             return None
         try:
             sha = hashlib.sha1(open(os.path.join(ROOT, e["source"]), "rb").read()).hexdigest()
