@@ -9,7 +9,8 @@
 // warp is one coalesced segment.  A group longer than one tile is cut into
 // several tasks; they write per-row partial sums and the last task of the
 // group to arrive (an atomic counter, no waiting) sums them in a fixed order
-// (eight interleaved sums over the tasks, then a fixed tree).
+// (eight interleaved sums over the tasks for FP32 storage, four otherwise,
+// then a fixed tree).
 //
 // Task numbering: task g < n_groups is the first tile of group g (no lookup
 // needed); task n_groups + e is extra tile e, of group extra_group[e], and
@@ -46,20 +47,30 @@ template <typename A>
 __device__ __forceinline__ A ld_coherent(const A *p) { return __ldcg(p); }
 
 // Sum of a row's nt tile partials (stride 32 between consecutive tiles):
-// eight interleaved sums -- tile q goes to sum q mod 8, so eight loads are
-// in flight at once -- added in a fixed tree.  Deterministic for a given nt.
-template <typename A>
+// NS interleaved sums -- tile q goes to sum q mod NS, so NS loads are in
+// flight at once -- added in a fixed tree.  Deterministic for a given nt.
+// Every index is static, so the sums stay in registers.  NS = 8 for FP32
+// storage, 4 otherwise (more would spill in the tighter FP64 and BF16/FP16
+// variants).
+template <typename V, typename A>
 __device__ __forceinline__ A sum_partials(const A *p, int64_t nt) {
-    A s[8];
+    constexpr int NS = (sizeof(A) == 8 || VT<V>::scaled) ? 4 : 8;
+    A s[NS];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) s[k] = 0;
+    for (int k = 0; k < NS; ++k) s[k] = 0;
     int64_t q = 0;
-    for (; q + 8 <= nt; q += 8) {
+    for (; q + NS <= nt; q += NS) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) s[k] += ld_coherent(p + (q + k) * 32);
+        for (int k = 0; k < NS; ++k) s[k] += ld_coherent(p + (q + k) * 32);
     }
-    for (int k = 0; q < nt; ++q, ++k) s[k] += ld_coherent(p + q * 32);
-    return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+#pragma unroll
+    for (int k = 0; k < NS - 1; ++k)
+        if (q + k < nt) s[k] += ld_coherent(p + (q + k) * 32);
+#pragma unroll
+    for (int w = NS / 2; w > 0; w /= 2)                 // pairwise tree: (s0+s1)+(s2+s3)...
+#pragma unroll
+        for (int k = 0; k < w; ++k) s[k] = s[2 * k] + s[2 * k + 1];
+    return s[0];
 }
 
 template <typename V, int U, int MIN_BLOCKS>
@@ -134,7 +145,7 @@ rgcsr_spmv_tiles_kernel(int64_t n, int32_t G, int32_t C, int64_t n_groups, int64
         if (!last) continue;
         __threadfence();
         if (active) {
-            const A s = sum_partials(partials + pb * 32 + lane, nt);
+            const A s = sum_partials<V>(partials + pb * 32 + lane, nt);
             y[orow] = VT<V>::scaled ? s * sc : s;
         }
         if (lane == 0) arrivals[g] = 0;
@@ -263,7 +274,7 @@ rgcsr_spmv_tiles_pipe_kernel(int64_t n, int32_t G, int32_t C, int64_t n_groups, 
             if (last) {
                 __threadfence();
                 if (active) {
-                    const A s = sum_partials(partials + cur.pb * 32 + lane, (int64_t)cur.nt);
+                    const A s = sum_partials<V>(partials + cur.pb * 32 + lane, (int64_t)cur.nt);
                     y[cur.orow] = VT<V>::scaled ? s * cur.sc : s;
                 }
                 if (lane == 0) arrivals[cur.g] = 0;
