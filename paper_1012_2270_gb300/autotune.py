@@ -3,12 +3,13 @@
 * ``model_group_size``: the group size G from a byte model -- the slots one
   SpMV streams, n_stored(G) * (value + index bytes), plus 8 bytes of group
   pointer per group -- preferring G = 32 (full 128-byte slot-rows, the
-  TMA-staged kernel) when it is within 5% of the best.  The paper fixed G
+  vector-load and TMA-staged kernels) when it is within 5% of the best.  The paper fixed G
   per GPU by experiment (Sec. 4.3: 128 was best on a GTX 280); here the
   choice follows the matrix.
 * ``tune``: times candidate (group size, kernel, variant) configurations
-  with CUDA events, flushing L2 between launches, and caches the fastest
-  per (matrix pattern, value type, GPU name) in a JSON file.
+  with CUDA events, flushing L2 (by a read) between launches, and caches
+  the fastest per (matrix pattern, value type, GPU name) in a JSON file;
+  the default configuration stays unless another is more than 2% faster.
 * ``tune_hyb_width``: the same for the ELL width of the HYB format around
   the library's byte-cost rule.
 * ``heuristic``: a configuration from the row lengths alone, without timing.
