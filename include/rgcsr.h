@@ -203,17 +203,23 @@ int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
 /* Long-row segments, for matrices whose row lengths vary wildly (the
  * paper's weak point, Sec. 4.4.2: one very long row makes its whole group
  * wait).  The slots j >= threshold of every longer row are cut into
- * segments of `segment` slots; one warp sums each segment (deterministic
- * per-segment partials), a final pass adds a row's partials in order, and
- * the remaining slots of every row go through the warp-split kernel.  The
+ * segments of `segment` slots; one warp sums each segment, and the last
+ * segment of a row to finish (a counter in `arrivals`, no waiting) adds the
+ * row's partials in a fixed order (lane l of its warp takes partials l,
+ * l + 32, ..., then a fixed shuffle tree), so the result does not depend on
+ * scheduling; the remaining slots of every row go through the warp-split
+ * kernel, one launch earlier.  The
  * RgCSR format itself is unchanged; the segment lists are a launch schedule.
  *   1. set threshold and segment, call rgcsr_long_rows_plan (sets
  *      n_segments, n_long_rows; synchronises `stream`);
  *   2. allocate seg_row, seg_start (n_segments int32), long_row,
- *      long_first, long_count (n_long_rows int32) and partials (n_segments
- *      doubles for F64 storage, floats otherwise; scratch of the SpMV);
- *   3. rgcsr_long_rows_build fills the lists (async);
- *   4. rgcsr_spmv_long_rows computes y = A x (three launches, async).   */
+ *      long_first, long_count (n_long_rows int32), arrivals (n_segments
+ *      int32) and partials (n_segments doubles for F64 storage, floats
+ *      otherwise; scratch of the SpMV);
+ *   3. rgcsr_long_rows_build fills the lists and zeroes arrivals (async);
+ *   4. rgcsr_spmv_long_rows computes y = A x (two launches, async).  One
+ *      SpMV per schedule may be in flight at a time: arrivals and partials
+ *      are its scratch, and every counter is back at 0 when it ends.      */
 typedef struct {
     int32_t threshold;          /* T >= 0                                     */
     int32_t segment;            /* S >= 1 slots per segment                   */
@@ -222,6 +228,8 @@ typedef struct {
     int32_t *seg_row, *seg_start;
     int32_t *long_row, *long_first, *long_count;
     void *partials;
+    int32_t *arrivals;          /* n_segments; a row's counter sits at its
+                                   first segment                              */
 } rgcsr_long_rows;
 size_t rgcsr_long_rows_workspace_bytes(int64_t n_rows);
 int rgcsr_long_rows_plan(const rgcsr_matrix *M, rgcsr_long_rows *S, void *workspace,
@@ -237,8 +245,8 @@ int rgcsr_spmv_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *S, const 
  * into ceil(K_g / tile) tasks of at most `tile` slot-rows each; tasks of
  * one group write per-row partial sums, and the last of them to finish
  * (an arrival counter per group, no waiting) adds the partials in a fixed
- * order (task q into the (q mod 8)-th of eight sums, then a fixed tree) and
- * writes y, so the result does not depend on scheduling.  With
+ * order (task q into sum q mod NS, NS = 8 for F32 storage and 4 for the
+ * others, then a fixed tree) and writes y, so the result does not depend on scheduling.  With
  * rows in descending length order (row_perm, Sec. 4.4.2) the groups are
  * dense and every warp's work is bounded by `tile` slot-rows, which removes
  * the long-row imbalance that the paper names as the format's weak point.

@@ -56,7 +56,7 @@ class Hyb(ctypes.Structure):
 class LongRows(ctypes.Structure):
     _fields_ = [("threshold", I32), ("segment", I32), ("n_segments", I64), ("n_long_rows", I64),
                 ("seg_row", P), ("seg_start", P), ("long_row", P), ("long_first", P), ("long_count", P),
-                ("partials", P)]
+                ("partials", P), ("arrivals", P)]
 
 
 class Tiles(ctypes.Structure):

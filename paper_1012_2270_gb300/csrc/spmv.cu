@@ -377,9 +377,12 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
 // ---------------------------------------------------------------------------
 // Long-row segments.  The slots j >= T of every row longer than T are cut
 // into segments of S slots; each segment is one warp's work (its slots are
-// read with the row's group stride), giving one partial sum per segment, and
-// a last pass adds a row's partials in segment order.  The rest of every row
-// (slots < T) goes through the split kernel with its length capped at T.
+// read with the row's group stride), giving one partial sum per segment.
+// The last segment of a row to finish (an arrival counter at the row's first
+// segment, no waiting) adds the row's partials with its whole warp -- lane l
+// sums partials l, l + 32, ..., then a fixed shuffle tree -- and adds that to
+// y.  The rest of every row (slots < T) goes through the split kernel with
+// its length capped at T, one launch earlier.
 // Work per warp is bounded by S slots whatever the row lengths are, so no
 // warp is held up by a very long row; the result is deterministic.
 // ---------------------------------------------------------------------------
@@ -418,8 +421,10 @@ template <typename V>
 __global__ void __launch_bounds__(kDefaultThreads)
 seg_spmv_kernel(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *__restrict__ col,
                 const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
-                const int32_t *__restrict__ seg_row, const int32_t *__restrict__ seg_start, int32_t S,
-                int64_t n_seg, const typename VT<V>::A *__restrict__ x, typename VT<V>::A *__restrict__ partials) {
+                const int32_t *__restrict__ seg_row, const int32_t *__restrict__ seg_start, int32_t T, int32_t S,
+                int64_t n_seg, const typename VT<V>::A *__restrict__ x, typename VT<V>::A *partials,
+                int32_t *__restrict__ arrivals, const float *__restrict__ scale, typename VT<V>::A *__restrict__ y,
+                const int32_t *__restrict__ perm) {
     using A = typename VT<V>::A;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -450,22 +455,27 @@ seg_spmv_kernel(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *
         }
         part = warp_sum(part);
         if (lane == 0) partials[s] = part;
+        // the row's segments are s - q .. s - q + c - 1
+        const int64_t f = s - (ja - T) / S;
+        const int c = (__ldg(rl + row) - T + S - 1) / S;
+        __threadfence();
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            __threadfence();
+            last = atomicAdd(arrivals + f, 1) == c - 1;
+        }
+        last = __shfl_sync(kFull, last, 0);
+        if (!last) continue;
+        __threadfence();
+        A sum = 0;
+        for (int i = lane; i < c; i += 32) sum += __ldcg(partials + f + i);
+        sum = warp_sum(sum);
+        if (lane == 0) {
+            y[out_row(perm, row)] += finish<V>(sum, scale, row);
+            arrivals[f] = 0;
+        }
     }
-}
-
-template <typename V>
-__global__ void seg_combine_kernel(int64_t n_long, const int32_t *__restrict__ long_row,
-                                   const int32_t *__restrict__ long_first, const int32_t *__restrict__ long_count,
-                                   const typename VT<V>::A *__restrict__ partials, const float *__restrict__ scale,
-                                   typename VT<V>::A *__restrict__ y, const int32_t *__restrict__ perm) {
-    using A = typename VT<V>::A;
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n_long) return;
-    const int64_t row = long_row[k];
-    const int64_t f = long_first[k];
-    A s = 0;
-    for (int q = 0; q < long_count[k]; ++q) s += partials[f + q];
-    y[out_row(perm, row)] += finish<V>(s, scale, row);
 }
 
 template <typename V>
@@ -487,9 +497,7 @@ int launch_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *S, const type
     A *part = static_cast<A *>(S->partials);
     seg_spmv_kernel<V><<<(unsigned)sb, kDefaultThreads, 0, s>>>(
         n, M->group_size, val, M->columns, M->group_ptr, M->row_lengths, S->seg_row, S->seg_start,
-        S->segment, S->n_segments, x, part);
-    seg_combine_kernel<V><<<(unsigned)ceil_div(S->n_long_rows, 256), 256, 0, s>>>(
-        S->n_long_rows, S->long_row, S->long_first, S->long_count, part, scale, y, M->row_perm);
+        S->threshold, S->segment, S->n_segments, x, part, S->arrivals, scale, y, M->row_perm);
     return launch_status();
 }
 
@@ -624,12 +632,13 @@ RGCSR_API int rgcsr_long_rows_build(const rgcsr_matrix *M, const rgcsr_long_rows
     if (st != RGCSR_OK) return st;
     if (!S || S->threshold < 0 || S->segment < 1) return RGCSR_ERR_INVALID_ARG;
     if (S->n_segments == 0 || M->n_rows == 0) return RGCSR_OK;
-    if (!S->seg_row || !S->seg_start || !S->long_row || !S->long_first || !S->long_count)
+    if (!S->seg_row || !S->seg_start || !S->long_row || !S->long_first || !S->long_count || !S->arrivals)
         return RGCSR_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < rgcsr_long_rows_workspace_bytes(M->n_rows)) return RGCSR_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     SegScratch c = carve_seg(workspace, M->n_rows);
     if ((st = seg_scan(M, S, c, s)) != RGCSR_OK) return st;
+    RGCSR_CUDA_TRY(cudaMemsetAsync(S->arrivals, 0, (size_t)S->n_segments * sizeof(int32_t), s));
     seg_fill_kernel<<<(unsigned)ceil_div(M->n_rows, 256), 256, 0, s>>>(
         M->n_rows, M->row_lengths, S->threshold, S->segment, c.seg_off, c.long_off, S->seg_row, S->seg_start,
         S->long_row, S->long_first, S->long_count);
@@ -643,7 +652,7 @@ RGCSR_API int rgcsr_spmv_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows 
     if (M->n_rows == 0) return RGCSR_OK;
     if (!S || S->threshold < 0 || S->segment < 1 || !y || (M->n_cols > 0 && !x)) return RGCSR_ERR_INVALID_ARG;
     if (S->n_segments > 0 && (!S->seg_row || !S->seg_start || !S->long_row || !S->long_first ||
-                              !S->long_count || !S->partials))
+                              !S->long_count || !S->partials || !S->arrivals))
         return RGCSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     switch (M->value_type) {

@@ -171,7 +171,7 @@ class RgCSRMatrix:
         i32 = dict(dtype=torch.int32, device=dev)
         bufs = dict(seg_row=torch.empty(S.n_segments, **i32), seg_start=torch.empty(S.n_segments, **i32),
                     long_row=torch.empty(S.n_long_rows, **i32), long_first=torch.empty(S.n_long_rows, **i32),
-                    long_count=torch.empty(S.n_long_rows, **i32),
+                    long_count=torch.empty(S.n_long_rows, **i32), arrivals=torch.empty(S.n_segments, **i32),
                     partials=torch.empty(S.n_segments, dtype=self.x_dtype, device=dev))
         for k, t in bufs.items():
             setattr(S, k, _ptr(t))

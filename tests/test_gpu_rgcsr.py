@@ -287,6 +287,28 @@ def test_long_row_segments(dtype, G, T, S):
     check_spmv(M, A, dtype, synth.uniform_vector(m, seed=8))
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_long_row_segments_repeat_bitwise(dtype):
+    # the last segment of a row to finish adds its partials in a fixed order:
+    # repeated products on one schedule agree bit for bit, and every arrival
+    # counter is back at zero after each product
+    rng = np.random.default_rng(11)
+    n, m = 4000, 50000
+    L_ = rng.integers(0, 12, n)
+    L_[[0, 7, 1234, 3999]] = [40000, 2048, 33 * 64 + 1, 700]
+    A = synth.random_csr(n, m, L_, seed=12)
+    M = to_gpu_matrix(A, dtype, 4, slot_map=False).split_long_rows(threshold=16, segment=64)
+    x = torch.from_numpy(synth.uniform_vector(m, seed=13)).cuda().to(M.x_dtype)
+    arrivals = M._long[1]["arrivals"]
+    first = M.spmv(x)
+    assert int(arrivals.abs().sum()) == 0
+    for _ in range(4):
+        y = M.spmv(x)
+        assert torch.equal(y, first)
+        assert int(arrivals.abs().sum()) == 0
+    check_spmv(M, A, dtype, synth.uniform_vector(m, seed=13))
+
+
 def test_long_row_segments_quantized():
     A = synth.power_law(20000, seed=4)
     M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val, A.n_cols, group_size=8, dtype=torch.float64)
