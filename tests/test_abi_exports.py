@@ -88,3 +88,46 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(L, "_lib", None)
     with pytest.raises(RuntimeError, match="not found"):
         L.lib()
+
+
+# ctypes mirror -> C typedef of include/rgcsr.h
+STRUCTS = {"CSR": "rgcsr_csr", "Matrix": "rgcsr_matrix", "Launch": "rgcsr_launch", "Hyb": "hyb_matrix",
+           "LongRows": "rgcsr_long_rows", "Tiles": "rgcsr_tiles", "BatchDesc": "rgcsr_batch_desc",
+           "Batch": "rgcsr_batch"}
+
+
+def declared_structs():
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return sorted(set(re.findall(r"\}\s*([a-z_][a-z0-9_]*)\s*;", src)))
+
+
+def test_every_header_struct_has_a_binding():
+    assert sorted(STRUCTS.values()) == declared_structs()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Compiles a host program against the header that prints sizeof and
+    offsetof of every field the binding declares; a field added, dropped or
+    reordered on either side changes one of them."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rgcsr.h"', "int main(void) {"]
+    expected = []
+    for py, c in STRUCTS.items():
+        cls = getattr(L, py)
+        lines.append(f'printf("%zu\\n", sizeof({c}));')
+        expected.append(ctypes.sizeof(cls))
+        for name, _ in cls._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({c}, {name}));')
+            expected.append(getattr(cls, name).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c11", "-I", B.INCLUDE, str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == expected
