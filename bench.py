@@ -340,7 +340,7 @@ def run_ours(args):
             cases.append(dict(key=f"{name}_{dt}", name=name, dt=dt, A=A, M=M, kw=kw, x=xd, y=yd, bytes=nb,
                               nnz=A.nnz, kernel=kernel_name(cfg, M, A, dt), config=cfg,
                               pad_pct=M.artificial_zero_percent(),
-                              launches=3 if M._long is not None and M._long[0].n_segments > 0 else 1))
+                              launches=2 if M._long is not None and M._long[0].n_segments > 0 else 1))
     torch.cuda.synchronize()
     step_bytes = sum(c["bytes"] for c in cases)
 
