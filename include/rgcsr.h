@@ -246,10 +246,11 @@ int rgcsr_spmv_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *S, const 
  * one group write per-row partial sums, and the last of them to finish
  * (an arrival counter per group, no waiting) adds the partials in a fixed
  * order (task q into sum q mod NS, NS = 8 for F32 storage and 4 for the
- * others, then a fixed tree) and writes y, so the result does not depend on scheduling.  With
- * rows in descending length order (row_perm, Sec. 4.4.2) the groups are
- * dense and every warp's work is bounded by `tile` slot-rows, which removes
- * the long-row imbalance that the paper names as the format's weak point.
+ * others, then a fixed tree) and writes y, so the result does not depend
+ * on scheduling.  With rows in descending length order (row_perm, Sec.
+ * 4.4.2) the groups are dense and every warp's work is bounded by `tile`
+ * slot-rows, which removes the long-row imbalance that the paper names as
+ * the format's weak point.
  *   1. set tile, call rgcsr_tiles_plan (sets n_extra, n_split, n_partials;
  *      synchronises `stream`);
  *   2. allocate first_extra, part_base (n_groups+1 int64), extra_group
