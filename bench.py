@@ -576,10 +576,10 @@ def time_rotating(fns, reps, stream):
 def time_flushed(fn, reps, flush, stream):
     """Microseconds of fn with L2 flushed (a 256 MB read, which leaves no
     dirty lines behind) before each call: the mean of the middle half of
-    the samples.  The event timer ticks in steps of about 2 us here, so a
-    median of a few samples of a 10-30 us launch lands on a tick; the
-    interquartile mean resolves finer differences when samples straddle
-    ticks."""
+    the samples.  Event times of short launches come in steps of about
+    2 us on GB300, so a median of a few samples of a 10-30 us launch lands
+    on a step; the interquartile mean resolves finer differences when the
+    samples straddle steps."""
     import torch
     from paper_1012_2270_gb300 import autotune
     fn()
