@@ -131,3 +131,33 @@ def test_struct_layouts_match_the_header(tmp_path):
     assert r.returncode == 0, r.stderr
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert got == expected
+
+
+def test_c_program_links_against_the_library(tmp_path, lib):
+    """A plain C program (no C++ runtime, no CUDA headers) compiles against
+    the header, links against librgcsr.so and calls its host-only entry
+    points, with the same answers as the binding gets."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    src = tmp_path / "use.c"
+    src.write_text("\n".join([
+        "#include <stdio.h>",
+        '#include "rgcsr.h"',
+        "int main(void) {",
+        '    printf("%d\\n", rgcsr_version());',
+        '    printf("%zu\\n", rgcsr_plan_workspace_bytes(1000000, 32));',
+        '    printf("%s\\n", rgcsr_status_string(RGCSR_ERR_COL_OOB));',
+        "    return 0;",
+        "}", ""]))
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(B.LIB_PATH)
+    r = subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-I", B.INCLUDE, str(src), "-o", str(exe),
+                        "-L", libdir, "-lrgcsr", f"-Wl,-rpath,{libdir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    assert int(out[0]) == lib.rgcsr_version()
+    assert int(out[1]) == lib.rgcsr_plan_workspace_bytes(1_000_000, 32)
+    assert out[2] == lib.rgcsr_status_string(L.RGCSR_ERR_COL_OOB).decode()
