@@ -60,6 +60,17 @@ def test_brute_force_all_length_patterns(n):
             addr, total = independent_map(L, G)
             assert lay.n_stored == total
             assert lay.row_lengths.tolist() == list(L)
+            # rowLengths and groupPointers alone: group g starts where the
+            # address map puts slot 0 of its first row, or, for a group of
+            # empty rows, where the previous group ends
+            rl, gp = oracle.rgcsr_sizes(A.rowptr, G)
+            assert rl.tolist() == list(L)
+            starts = [addr.get((g0, 0)) for g0 in range(0, n, G)]
+            for g in range(len(starts) - 1, -1, -1):
+                if starts[g] is None:
+                    starts[g] = starts[g + 1] if g + 1 < len(starts) else total
+            assert gp.tolist() == starts + [total]
+            assert np.array_equal(gp, lay.group_ptr)
             seen = np.zeros(lay.n_stored, bool)
             for i in range(n):
                 for j in range(L[i]):
