@@ -160,7 +160,10 @@ class RgCSRMatrix:
 
     def split_long_rows(self, threshold: int = 64, segment: int = 256, stream=None) -> "RgCSRMatrix":
         """Makes spmv() cut the slots >= threshold of longer rows into
-        segments of `segment` slots, one warp each (rgcsr_spmv_long_rows)."""
+        segments of `segment` slots, one warp each (rgcsr_spmv_long_rows).
+        The schedule's partial sums and arrival counters are the product's
+        scratch, so one product per schedule may be in flight at a time:
+        products on several streams need a matrix (or schedule) each."""
         S = L.LongRows()
         S.threshold, S.segment = int(threshold), int(segment)
         dev = self.group_ptr.device
@@ -182,7 +185,8 @@ class RgCSRMatrix:
     def tile_groups(self, tile: int = 64, variant: int = 0, stream=None) -> "RgCSRMatrix":
         """Makes spmv() use the group-tile schedule (rgcsr_spmv_tiles): one
         warp per tile of at most `tile` slot-rows of a group, long groups cut
-        into several tiles.  Needs group_size <= 32."""
+        into several tiles.  Needs group_size <= 32.  As with the long-row
+        schedule, one product per schedule may be in flight at a time."""
         T = L.Tiles()
         T.tile = int(tile)
         T.variant = int(variant)
