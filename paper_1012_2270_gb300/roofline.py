@@ -36,10 +36,14 @@ def hyb_spmv_bytes(n_rows: int, n_cols: int, nnz: int, nnz_coo: int, value_bytes
             + n_cols * value_bytes + n_rows * value_bytes)
 
 
-def spmm_bytes(n_rows: int, n_cols: int, nnz: int, n_groups: int, value_bytes: int, k: int) -> int:
-    """Multiple right-hand sides: matrix once, X [n_cols x k] once, Y once."""
+def spmm_bytes(n_rows: int, n_cols: int, nnz: int, n_groups: int, value_bytes: int, k: int,
+               x_bytes: int | None = None) -> int:
+    """Multiple right-hand sides: matrix once, X [n_cols x k] once, Y once
+    (X and Y elements of the value type, or x_bytes for reduced-precision
+    storage)."""
+    xb = value_bytes if x_bytes is None else x_bytes
     return (nnz * (value_bytes + INDEX_BYTES) + n_rows * 4 + (n_groups + 1) * 8
-            + k * (n_cols + n_rows) * 4)
+            + k * (n_cols + n_rows) * xb)
 
 
 def peak_gflops(bandwidth_gbs: float, value_bytes: int, x_cached: bool = False) -> float:

@@ -1,6 +1,7 @@
 """Host-side logic without a GPU: the autotuner's padding model against the
-oracle's layout sizes, its group-size choice, and the batch task builder
-(a host function of the C ABI)."""
+oracle's layout sizes, its group-size choice and selection rule, the batch
+task builder (a host function of the C ABI), the Table 6 stand-ins, the
+traffic lookup, and the roofline's algorithmic byte counts."""
 import ctypes
 
 import numpy as np
@@ -120,3 +121,30 @@ def test_traffic_lookup_per_case_and_kernel(tmp_path, monkeypatch):
     assert bench.measured_traffic("kB", [{"key": "y_f32", "kernel": "kB"}]) is None      # no entry
     src.write_text("changed")
     assert bench.measured_traffic("kA", cases) is None                                   # stale hash
+
+
+@pytest.mark.parametrize("G", [1, 8, 32])
+def test_algorithmic_bytes_count_the_arrays_read_and_written(G):
+    # the roofline's byte counts equal the sizes of the arrays one product
+    # reads and writes once: the non-zeros' values and columns (padding
+    # excluded), rowLengths, groupPointers, x and y
+    from paper_1012_2270_gb300 import roofline
+    A = synth.random_csr(301, 257, np.random.default_rng(G).integers(0, 30, 301), seed=G)
+    lay = oracle.rgcsr_layout(A.rowptr, A.col, A.val, G)
+    for vdt, xdt in ((np.float64, np.float64), (np.float32, np.float32), (np.uint16, np.float32)):
+        vals = A.val.astype(vdt)
+        x, y = np.zeros(A.n_cols, xdt), np.zeros(A.n_rows, xdt)
+        matrix = vals.nbytes + A.col.astype(np.int32).nbytes + lay.row_lengths.nbytes + lay.group_ptr.nbytes
+        scale = np.zeros(A.n_rows, np.float32).nbytes if vdt == np.uint16 else 0
+        got = roofline.rgcsr_spmv_bytes(A.n_rows, A.n_cols, A.nnz, lay.group_ptr.size - 1, vals.itemsize,
+                                        x_bytes=x.itemsize, row_scale=bool(scale))
+        assert got == matrix + scale + x.nbytes + y.nbytes
+        if vdt != np.uint16:
+            k = 5
+            X, Y = np.zeros((A.n_cols, k), xdt), np.zeros((A.n_rows, k), xdt)
+            got = roofline.spmm_bytes(A.n_rows, A.n_cols, A.nnz, lay.group_ptr.size - 1, vals.itemsize, k)
+            assert got == matrix + X.nbytes + Y.nbytes
+    h = oracle.hyb_layout(A.rowptr, A.col, A.val, 4)
+    nnz_coo = h.coo_row.size
+    got = roofline.hyb_spmv_bytes(A.n_rows, A.n_cols, A.nnz, nnz_coo, 8)
+    assert got == (A.nnz * 12 + h.coo_row.astype(np.int32).nbytes + A.n_cols * 8 + A.n_rows * 8)
