@@ -81,6 +81,17 @@ def test_argument_errors_without_gpu(lib):
     assert lib.rgcsr_spmv(ctypes.byref(M1), None, None, None) == L.RGCSR_ERR_INVALID_ARG
     H = L.Hyb(n_rows=3, n_cols=3, value_type=L.BF16)
     assert lib.hyb_spmv(ctypes.byref(H), None, None, None) == L.RGCSR_ERR_UNSUPPORTED_DTYPE
+    # a long-row schedule with segments needs every list, the arrival
+    # counters included; the check comes before any device work (the
+    # pointers here are never dereferenced)
+    M2 = L.Matrix(n_rows=4, n_cols=4, group_size=32, n_groups=1, value_type=L.F32, group_ptr=8, row_lengths=8)
+    full = dict(threshold=2, segment=4, n_segments=1, n_long_rows=1, seg_row=8, seg_start=8, long_row=8,
+                long_first=8, long_count=8, partials=8, arrivals=8)
+    for missing in ("arrivals", "partials", "seg_row"):
+        S = L.LongRows(**{k: v for k, v in full.items() if k != missing})
+        assert lib.rgcsr_spmv_long_rows(ctypes.byref(M2), ctypes.byref(S), 8, 8, None) == L.RGCSR_ERR_INVALID_ARG
+    S = L.LongRows(**{k: v for k, v in full.items() if k != "arrivals"})
+    assert lib.rgcsr_long_rows_build(ctypes.byref(M2), ctypes.byref(S), None, 0, None) == L.RGCSR_ERR_INVALID_ARG
 
 
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
