@@ -92,6 +92,17 @@ def test_argument_errors_without_gpu(lib):
         assert lib.rgcsr_spmv_long_rows(ctypes.byref(M2), ctypes.byref(S), 8, 8, None) == L.RGCSR_ERR_INVALID_ARG
     S = L.LongRows(**{k: v for k, v in full.items() if k != "arrivals"})
     assert lib.rgcsr_long_rows_build(ctypes.byref(M2), ctypes.byref(S), None, 0, None) == L.RGCSR_ERR_INVALID_ARG
+    # the same for the group-tile schedule, which also needs G <= 32
+    full = dict(tile=64, n_groups=1, n_extra=1, n_split=1, n_partials=2, first_extra=8, part_base=8,
+                extra_group=8, arrivals=8, partials=8)
+    for missing in ("arrivals", "partials", "extra_group"):
+        T = L.Tiles(**{k: v for k, v in full.items() if k != missing})
+        assert lib.rgcsr_spmv_tiles(ctypes.byref(M2), ctypes.byref(T), 8, 8, None) == L.RGCSR_ERR_INVALID_ARG
+    T = L.Tiles(**{k: v for k, v in full.items() if k != "arrivals"})
+    assert lib.rgcsr_tiles_build(ctypes.byref(M2), ctypes.byref(T), None) == L.RGCSR_ERR_INVALID_ARG
+    M64 = L.Matrix(n_rows=4, n_cols=4, group_size=64, n_groups=1, value_type=L.F32, group_ptr=8, row_lengths=8)
+    T = L.Tiles(**full)
+    assert lib.rgcsr_spmv_tiles(ctypes.byref(M64), ctypes.byref(T), 8, 8, None) == L.RGCSR_ERR_INVALID_ARG
 
 
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
