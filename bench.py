@@ -49,10 +49,8 @@ CASES = [("a", synth.workload_a), ("b", synth.workload_b), ("c", synth.workload_
 DTYPES = ["f32", "f64"]
 VB = {"f32": 4, "f64": 8}
 NP = {"f32": np.float32, "f64": np.float64}
-WORKLOAD = ("RgCSR SpMV, autotuned group size/kernel, FP32 and FP64, of (a) 3D 7-point Laplacian 128^3, "
-            "(b) power-law rows n=1e6 (Zipf(2) lengths, max 10,000, rows given in natural order; "
-            "the conversion may reorder them), "
-            "(c) 27-point stencil 96^3")
+WORKLOAD_SHORT = ("RgCSR SpMV, FP32+FP64, tuned config: (a) 7-point 128^3, (b) power-law rows n=1e6 "
+                  "(Zipf(2) lengths <= 10,000), (c) 27-point 96^3")
 
 
 def parse():
@@ -66,6 +64,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip HYB and the other forms")
     p.add_argument("--forms", default="", help="comma-separated subset of the forms to run (default: all)")
+    p.add_argument("--detail-out", default=None,
+                   help="write the full record (per-case detail, forms) to this JSON file; "
+                        "default: print it on one line starting with 'detail: ' before the headline")
     p.add_argument("--tune-cache", default=None,
                    help="JSON file for the tuned configurations: read if present, else written "
                         "(lets a profiled run use the configurations of an unprofiled one)")
@@ -221,8 +222,7 @@ def cpu_baseline(mats, seconds):
             passes += 1
         t = time.perf_counter() - t0
     return {"value": nbytes / t / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{passes} full pass(es) of the six SpMVs (FP64 CSR loop on the FP32/FP64 values), "
-                      f"{t:.1f} s wall on {threads} host threads (rows in {4 * threads} blocks per case)"}
+            "sample": f"{passes} pass(es) of the six SpMVs (FP64 CSR loop), {t:.1f} s on {threads} threads"}
 
 
 def run_reference(args):
@@ -248,7 +248,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD + "; CPU oracle", "group_size": GROUP},
+        "config": {"workload": WORKLOAD_SHORT, "l2": "inputs larger than L2 (~1.3 GB per step)",
+                   "timing": "host wall clock of K steps of the CPU oracle",
+                   "parallelism": f"replicas x{world}"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -300,13 +302,131 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# CUDA-graph timing
+# ---------------------------------------------------------------------------
+COPIES = 3        # rotating copies of each case's matrix, x and y for the per-case graphs
+ROUNDS = 8        # passes over the copies in one per-case graph (COPIES * ROUNDS launches)
+REPLAYS = 15      # timed replays of each per-case graph (median taken)
+
+
+def capture_graph(fns):
+    """A CUDA graph of fns called in order (each enqueues its kernels on the
+    current stream).  The calls run once eagerly on the capture stream
+    first, so one-off set-up (kernel attributes) happens outside capture."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for f in fns:
+            f()
+    side.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        for f in fns:
+            f()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    return g
+
+
+def replay_us(g, replays, stream):
+    """Microseconds of each of `replays` back-to-back replays of graph g,
+    one event pair per replay on the launching stream."""
+    import torch
+    g.replay()
+    torch.cuda.synchronize()
+    ev = [_ev() for _ in range(replays)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return [1e3 * e0.elapsed_time(e1) for e0, e1 in ev]
+
+
+def rotating_us(fns, stream, rounds=ROUNDS, replays=REPLAYS):
+    """Microseconds per call of one operation whose copies (fns: one call
+    per copy, each on its own data) are called in turn, `rounds` times, in
+    one CUDA graph: consecutive calls touch different data, so with three
+    copies of >= 100 MB L2 holds none of a call's inputs when it starts;
+    the graph removes host launch gaps.  Median over replays."""
+    g = capture_graph([f for _ in range(rounds) for f in fns])
+    t = statistics.median(replay_us(g, replays, stream))
+    del g
+    return t / (rounds * len(fns))
+
+
+# ---------------------------------------------------------------------------
+# the JSON line
+# ---------------------------------------------------------------------------
+def _r(v, digits=4):
+    """Floats rounded to `digits` significant digits, recursively (keeps
+    the headline line short)."""
+    if isinstance(v, float):
+        return float(f"{v:.{digits}g}") if v == v and v not in (float("inf"), float("-inf")) else None
+    if isinstance(v, dict):
+        return {k: _r(x, digits) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [_r(x, digits) for x in v]
+    return v
+
+
+HEADLINE_MAX_BYTES = 2048
+
+
+def headline(*, value, world, steps, warmup, ms_per_step, gflops, launches, clocks, roof, e2e, cpu,
+             cases, forms_summary, detail_file):
+    """The one JSON line that ends the run: the metric, the roofline of the
+    dominant kernel, the end-to-end and CPU figures, per-case times and a
+    few numbers of the other forms.  Everything else goes to the detail
+    record, so that this line stays under HEADLINE_MAX_BYTES."""
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32,f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_SHORT, "l2": "inputs larger than L2 (~1.3 GB per step)",
+                   "timing": "graphs: the step x K; per case 3 rotating copies",
+                   "parallelism": f"replicas x{world}"},
+        "gflops": gflops, "pct_of_8tbs": 100 * value / world / roofline.NOMINAL_HBM_GBS,
+        "gpu_launches": launches, "clocks": clocks, "roofline": roof, "e2e": e2e,
+        "cpu_baseline": cpu, "cases": cases, "forms": forms_summary, "detail": detail_file,
+    }
+    return _r(line)
+
+
+def forms_summary(forms):
+    """A few numbers of the other forms for the headline (the full tables
+    are in the detail record)."""
+    s = {}
+    q = forms.get("quantized") or {}
+    if "a_bf16" in q:
+        s["bf16_a_speedup_vs_f32"] = q["a_bf16"]["speedup_vs_f32"]
+        s["bf16_a_err"] = q["a_bf16"]["max_err_over_absAx_vs_f64"]
+    bt = forms.get("batched_512_f32")
+    if bt:
+        s["batched_gbs"] = bt["gbs"]
+        s["batched_speedup_vs_512_launches"] = bt["speedup_vs_plain"]
+    bw = forms.get("backward_b_k8_f32")
+    if bw:
+        s["bwd_over_fwd"] = bw["backward_over_forward"]
+    h = forms.get("hyb")
+    if h:
+        s["rgcsr_over_hyb"] = {k: v["rgcsr_speedup"] for k, v in h.items() if k.startswith("b")}
+    ic = forms.get("ir_cg_poisson128")
+    if ic:
+        s["ir_cg_speedup_vs_fp64_cg"] = ic["fp64_cg_ms"] / ic["ms"]
+    sp = forms.get("spmm_b_f32")
+    if sp and "k8" in sp:
+        s["spmm_b_k8_gflops"] = sp["k8"]["gflops"]
+    return s
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
     import torch
     import torch.distributed as dist
-    from paper_1012_2270_gb300 import _lib as L
-    from paper_1012_2270_gb300.rgcsr import HybMatrix, RgCSRMatrix
 
     rank, world, local = rank_info()
     torch.cuda.set_device(local)
@@ -321,7 +441,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     mats = load_cases()
 
-    # ---- convert (one-off) ----
+    # ---- convert (one-off): each case in its tuned configuration, in
+    # COPIES copies (own matrix, x and y) for the per-case graphs ----
     from paper_1012_2270_gb300 import autotune
     if args.tune_cache:
         autotune.CACHE_PATH = os.path.abspath(args.tune_cache)
@@ -333,74 +454,74 @@ def run_ours(args):
             # group size, kernel and long-row schedule chosen by timing on this GPU
             cfg = autotune.tune(A.rowptr, A.col, vals, A.n_cols, dtype=tdt, reps=12,
                                  use_cache=bool(args.tune_cache))
-            M, kw = autotune.build(A.rowptr, A.col, vals, A.n_cols, cfg, tdt)
-            xd = torch.from_numpy(x.astype(NP[dt])).to(dev)
-            yd = torch.empty(A.n_rows, dtype=xd.dtype, device=dev)
+            copies = []
+            for _ in range(COPIES):
+                M, kw = autotune.build(A.rowptr, A.col, vals, A.n_cols, cfg, tdt)
+                xd = torch.from_numpy(x.astype(NP[dt])).to(dev)
+                copies.append((M, xd, torch.empty(A.n_rows, dtype=xd.dtype, device=dev)))
+            M = copies[0][0]
             nb = case_bytes(A, (A.n_rows + GROUP - 1) // GROUP, dt)
-            cases.append(dict(key=f"{name}_{dt}", name=name, dt=dt, A=A, M=M, kw=kw, x=xd, y=yd, bytes=nb,
-                              nnz=A.nnz, kernel=kernel_name(cfg, M, A, dt), config=cfg,
+            cases.append(dict(key=f"{name}_{dt}", name=name, dt=dt, A=A, M=M, kw=kw, x=copies[0][1],
+                              y=copies[0][2], copies=copies, bytes=nb, nnz=A.nnz,
+                              kernel=kernel_name(cfg, M, A, dt), config=cfg,
                               pad_pct=M.artificial_zero_percent(),
                               launches=2 if M._long is not None and M._long[0].n_segments > 0 else 1))
     torch.cuda.synchronize()
     step_bytes = sum(c["bytes"] for c in cases)
 
-    def launch(c):
-        c["M"].spmv(c["x"], out=c["y"], **c["kw"])
+    def launcher(c, j):
+        M, xd, yd = c["copies"][j]
+        return lambda: M.spmv(xd, out=yd, **c["kw"])
 
-    # ---- warm-up ----
+    # ---- the step as one CUDA graph: the six SpMVs back to back ----
+    step_graph = capture_graph([launcher(c, 0) for c in cases])
     for _ in range(args.warmup):
-        for c in cases:
-            launch(c)
+        step_graph.replay()
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps, per-launch events on the launching stream ----
+    # ---- timed region: K replays of the step graph ----
     K = args.steps
-    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in cases] for _ in range(K)]
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
+    t_start, t_end = _ev()
     barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local) if rank == 0 else None
-    time.sleep(0.3 if clocks else 0)
+    time.sleep(0.2 if clocks else 0)
     torch.cuda.nvtx.range_push("timed_region")    # lets a profiler capture just these launches
     t_start.record(stream)
-    for k in range(K):
-        for i, c in enumerate(cases):
-            ev[k][i][0].record(stream)
-            launch(c)
-            ev[k][i][1].record(stream)
+    for _ in range(K):
+        step_graph.replay()
     t_end.record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
-    clk = clocks.stop() if clocks else None
     ms_total, = max_over_ranks([t_start.elapsed_time(t_end)], dev)
-    per_case_ms = [statistics.fmean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(K))
-                   for i in range(len(cases))]
     value = whole_job_gbs(world, K, step_bytes, ms_total)
 
+    # ---- per case: a graph of its COPIES copies in turn, ROUNDS times ----
+    per_case_us = [rotating_us([launcher(c, j) for j in range(COPIES)], stream) for c in cases]
+    clk = clocks.stop() if clocks else None
+
     detail = {}
-    for c, ms in zip(cases, per_case_ms):
-        detail[c["key"]] = {"gbs": c["bytes"] / (ms * 1e-3) / 1e9, "gflops": 2 * c["nnz"] / (ms * 1e-3) / 1e9,
-                            "us": ms * 1e3, "pct_of_8tbs": 100 * c["bytes"] / (ms * 1e-3) / 1e9 / roofline.NOMINAL_HBM_GBS,
+    for c, us in zip(cases, per_case_us):
+        detail[c["key"]] = {"gbs": c["bytes"] / us / 1e3, "gflops": 2 * c["nnz"] / us / 1e3,
+                            "us": us, "pct_of_8tbs": 100 * c["bytes"] / us / 1e3 / roofline.NOMINAL_HBM_GBS,
                             "artificial_zero_pct": c["pad_pct"], "kernel": c["kernel"],
+                            "launches": c["launches"],
                             "config": {k: v for k, v in c["config"].items() if k != "us"}}
 
     # ---- the same bytes as one plain device read (the library's streaming
-    # read of a buffer of the case's algorithmic bytes, L2 flushed by a
-    # read): what a streaming kernel of this size reaches, launch ramp and
-    # tail included ----
+    # read of a buffer of the case's algorithmic bytes, three rotating
+    # buffers in a graph like the SpMVs): what a streaming kernel of this
+    # size reaches, launch ramp and tail included ----
     from paper_1012_2270_gb300.rgcsr import stream_read
-    flush_r = torch.ones(64 << 20, dtype=torch.float32, device=dev)
     for c in cases:
-        buf = torch.ones(c["bytes"] // 16 * 4, dtype=torch.float32, device=dev)
-        r_us = time_flushed(lambda: stream_read(buf, stream), 10, flush_r, stream)
+        bufs = [torch.ones(c["bytes"] // 16 * 4, dtype=torch.float32, device=dev) for _ in range(COPIES)]
+        r_us = rotating_us([lambda b=b: stream_read(b) for b in bufs], stream)
         d = detail[c["key"]]
         d["same_size_read_us"] = r_us
         d["frac_of_same_size_read"] = r_us / d["us"]
-        del buf
-    del flush_r
+        del bufs
+    torch.cuda.empty_cache()
     # ---- FP64 FMA rate (the library's probe): an FP64 SpMV does one FMA per
     # non-zero, and on this GPU that rate is low enough to be a second floor ----
     from paper_1012_2270_gb300.rgcsr import fp64_fma_probe
@@ -418,7 +539,52 @@ def run_ours(args):
         if c["dt"] == "f64":
             detail[c["key"]]["fp64_fma_floor_us"] = 1e6 * c["nnz"] / fma_rate
 
-    # ---- roofline of the dominant kernel ----
+    roof = roofline_of(cases, per_case_us, detail, fma_rate, clk, dev)
+
+    # ---- end to end: host x in, host y out, through rgcsr_spmv_host ----
+    e2e = measure_e2e(cases, world, step_bytes, K, stream, barrier, dev)
+
+    # ---- forms beside plain ----
+    forms = {}
+    if not args.no_forms and rank == 0:
+        forms = measure_forms(mats, cases, detail, dev, stream, tune_cache=bool(args.tune_cache),
+                              only=set(args.forms.split(",")) if args.forms else None)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(mats, args.cpu_seconds)
+
+    if rank == 0:
+        record = {"cases": detail, "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "forms": forms,
+                  "clocks": clk, "ms_per_step": ms_total / K,
+                  "sum_of_case_us": sum(per_case_us),
+                  "tuned": {c["key"]: {k: v for k, v in c["config"].items() if k != "us"} for c in cases}}
+        if args.detail_out:
+            with open(args.detail_out, "w") as f:
+                json.dump(record, f, indent=1)
+        else:
+            print("detail: " + json.dumps(record), flush=True)
+        line = headline(
+            value=value, world=world, steps=K, warmup=args.warmup, ms_per_step=ms_total / K,
+            gflops=world * K * sum(2 * c["nnz"] for c in cases) / (ms_total * 1e-3) / 1e9,
+            launches=K * sum(c["launches"] for c in cases),
+            clocks={k: v for k, v in clk.items() if k != "samples"} if clk else None,
+            roof={k: v for k, v in roof.items() if k not in ("fp64_fma", "cases")},
+            e2e={k: v for k, v in e2e.items() if k not in ("note", "one_stream_value")}, cpu=cpu,
+            cases={c["key"]: [d["us"], d["gbs"]]
+                   for c, d in ((c, detail[c["key"]]) for c in cases)},
+            forms_summary=forms_summary(forms), detail_file=args.detail_out)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def roofline_of(cases, per_case_us, detail, fma_rate, clk, dev):
+    """Roofline of the dominant kernel (the one with the largest share of
+    the step): algorithmic bytes per launch / its mean time per launch from
+    the per-case graphs, against the measured HBM copy bandwidth."""
+    import torch
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(peaks_path):
         peak_hbm = json.load(open(peaks_path))["hbm_gbs"]
@@ -426,51 +592,55 @@ def run_ours(args):
     else:
         peak_hbm, peak_src = 6800.0, "fallback"
     by_kernel = {}
-    for c, ms in zip(cases, per_case_ms):
-        d = by_kernel.setdefault(c["kernel"], {"ms": 0.0, "bytes": 0, "launches": 0})
-        d["ms"] += ms
+    for c, us in zip(cases, per_case_us):
+        d = by_kernel.setdefault(c["kernel"], {"us": 0.0, "bytes": 0, "launches": 0})
+        d["us"] += us
         d["bytes"] += c["bytes"]
         d["launches"] += 1
-    dom = max(by_kernel, key=lambda k: by_kernel[k]["ms"])
+    dom = max(by_kernel, key=lambda k: by_kernel[k]["us"])
     d = by_kernel[dom]
-    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+    achieved = d["bytes"] / d["us"] / 1e3
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
             "frac": achieved / peak_hbm, "traffic": measured_traffic(dom, cases), "kernel": dom,
-            "peak_source": peak_src,
-            "bytes_per_launch": d["bytes"] / d["launches"], "avg_launch_us": 1e3 * d["ms"] / d["launches"]}
-    dom_cases = [(c, ms) for c, ms in zip(cases, per_case_ms) if c["kernel"] == dom]
+            "cases": [c["key"] for c in cases if c["kernel"] == dom], "peak_source": peak_src,
+            "share_of_step": d["us"] / sum(per_case_us),
+            "bytes_per_launch": d["bytes"] / d["launches"], "avg_launch_us": d["us"] / d["launches"]}
+    dom_cases = [(c, us) for c, us in zip(cases, per_case_us) if c["kernel"] == dom]
     # the same bytes as plain reads (launch ramp and tail included): the
     # ceiling a memory-bound kernel of this size can reach on this GPU
     read_us = sum(detail[c["key"]]["same_size_read_us"] for c, _ in dom_cases)
-    read_gbs = sum(c["bytes"] for c, _ in dom_cases) / (read_us * 1e-6) / 1e9
-    roof["same_size_read"] = {"gbs": read_gbs, "frac": achieved / read_gbs, "frac_of_peak": read_gbs / peak_hbm}
+    read_gbs = sum(c["bytes"] for c, _ in dom_cases) / read_us / 1e3
+    roof["same_size_read"] = {"gbs": read_gbs, "frac": achieved / read_gbs}
     if all(c["dt"] == "f64" for c, _ in dom_cases):
         # one FP64 FMA per non-zero: its floor next to the HBM floor
         nnz = sum(c["nnz"] for c, _ in dom_cases)
-        t_us = 1e3 * sum(ms for _, ms in dom_cases)
+        t_us = sum(us for _, us in dom_cases)
         roof["fp64_fma"] = {
             "probe_tflops": 2 * fma_rate / 1e12, "nominal_tflops": roofline.NOMINAL_FP64_TFLOPS,
             "achieved_tflops": 2 * nnz / (t_us * 1e-6) / 1e12,
-            "floor_us": 1e6 * nnz / fma_rate, "hbm_floor_us": 1e6 * sum(c["bytes"] for c, _ in dom_cases) / (peak_hbm * 1e9),
+            "floor_us": 1e6 * nnz / fma_rate,
+            "hbm_floor_us": 1e6 * sum(c["bytes"] for c, _ in dom_cases) / (peak_hbm * 1e9),
             "kernel_us": t_us, "frac_of_probe": (1e6 * nnz / fma_rate) / t_us}
     if all(c["name"] == "b" for c, _ in dom_cases):
-        # random columns: every x gather is its own L2 request (1.15-1.26
-        # requests per non-zero measured with ncu, the streamed lines
-        # included), and an SM sends at most about one request per clock
-        # (the L1->crossbar request path is the busiest unit) -- a second
-        # ceiling below HBM
+        # random columns: every x gather is its own L2 request, and an SM
+        # sends at most about one request per clock -- a second ceiling below
+        # HBM (one request per non-zero plus one per 128-byte line of the
+        # algorithmic bytes)
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         mhz = (clk or {}).get("sm_mhz") or 1920.0
         reqs = [c["nnz"] + c["bytes"] / 128 for c, _ in dom_cases]
         ceil_us = statistics.fmean(r / (sms * mhz) for r in reqs)
-        t_us = 1e3 * statistics.fmean(ms for _, ms in dom_cases)
-        roof["gather_request_ceiling"] = {
-            "requests_per_launch": statistics.fmean(reqs),
-            "model": "one L2 request per non-zero plus one per 128-byte line of the algorithmic bytes, "
-                     "at one request per SM clock",
-            "sms": sms, "sm_mhz": mhz, "ceiling_us": ceil_us, "frac": ceil_us / t_us}
+        t_us = statistics.fmean(us for _, us in dom_cases)
+        roof["gather_request_ceiling"] = {"us": ceil_us, "frac": ceil_us / t_us, "sm_mhz": mhz}
+    return roof
 
-    # ---- end to end: host x in, host y out, through rgcsr_spmv_host ----
+
+def measure_e2e(cases, world, step_bytes, K, stream, barrier, dev):
+    """The same six SpMVs end to end through rgcsr_spmv_host: per step and
+    case x host->device, SpMV, y device->host (pinned buffers, matrix
+    resident, as in a Krylov solver); the six cases on three streams so that
+    one case's copies overlap another's SpMV."""
+    import torch
     host = []
     for c in cases:
         xh = c["x"].cpu().pin_memory()
@@ -479,12 +649,11 @@ def run_ours(args):
     h2d = sum(h[0].numel() * h[0].element_size() for h in host)
     d2h = sum(h[1].numel() * h[1].element_size() for h in host)
     Ke = max(3, K // 4)
-    # the six cases are independent: case i runs on stream i mod 3, so one
-    # case's copies overlap another's SpMV (each stream keeps its own order)
     streams = [torch.cuda.Stream() for _ in range(3)]
-
+    # each case's SpMVs on one stream at a time: a schedule's scratch allows
+    # one product in flight, so case i always uses stream i mod 3
     def e2e_run(n_steps, overlap):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = _ev()
         e0.record(stream)
         for st in streams:
             st.wait_event(e0)
@@ -506,45 +675,11 @@ def run_ours(args):
     ms_e2e_serial = e2e_run(Ke, False)
     barrier()
     ms_e2e, ms_e2e_serial = max_over_ranks([ms_e2e, ms_e2e_serial], dev)
-    e2e = {"value": whole_job_gbs(world, Ke, step_bytes, ms_e2e), "unit": UNIT,
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "one_stream_value": whole_job_gbs(world, Ke, step_bytes, ms_e2e_serial),
-           "note": "per step and case: x host->device, SpMV, y device->host through rgcsr_spmv_host (pinned "
-                   "buffers, matrix resident); the six cases on three streams so copies overlap SpMVs"}
-
-    # ---- forms beside plain ----
-    forms = {}
-    if not args.no_forms and rank == 0:
-        forms = measure_forms(mats, cases, detail, dev, stream, tune_cache=bool(args.tune_cache),
-                              only=set(args.forms.split(",")) if args.forms else None)
-
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(mats, args.cpu_seconds)
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-            "warmup": args.warmup, "ms_per_step": ms_total / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32,f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD,
-                       "tuned": {c["key"]: {k: v for k, v in c["config"].items() if k != "us"} for c in cases},
-                       "l2": "inputs larger than L2: each step streams the six matrices (~1.3 GB algorithmic)",
-                       "parallelism": f"replicas x{world}"},
-            "gflops": world * K * sum(2 * c["nnz"] for c in cases) / (ms_total * 1e-3) / 1e9,
-            "pct_of_8tbs": 100 * value / world / roofline.NOMINAL_HBM_GBS,
-            "gpu_launches": K * sum(c["launches"] for c in cases),
-            "clocks": clk,
-            "roofline": roof,
-            "e2e": e2e,
-            "cpu_baseline": cpu,
-            "detail": detail,
-            "forms": forms,
-        }
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
-    return 0
+    return {"value": whole_job_gbs(world, Ke, step_bytes, ms_e2e), "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "one_stream_value": whole_job_gbs(world, Ke, step_bytes, ms_e2e_serial),
+            "note": "per step and case: x host->device, SpMV, y device->host through rgcsr_spmv_host (pinned "
+                    "buffers, matrix resident); the six cases on three streams so copies overlap SpMVs"}
 
 
 # ---------------------------------------------------------------------------
@@ -553,24 +688,6 @@ def run_ours(args):
 def _ev():
     import torch
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-
-
-def time_rotating(fns, reps, stream):
-    """Mean microseconds per call of each fn, calling them in turn (so that
-    consecutive calls touch different data and L2 holds none of it)."""
-    import torch
-    for f in fns:
-        f()
-    torch.cuda.synchronize()
-    ev = [[_ev() for _ in fns] for _ in range(reps)]
-    for r in range(reps):
-        for i, f in enumerate(fns):
-            ev[r][i][0].record(stream)
-            f()
-            ev[r][i][1].record(stream)
-    torch.cuda.synchronize()
-    return [1e3 * statistics.fmean(ev[r][i][0].elapsed_time(ev[r][i][1]) for r in range(reps))
-            for i in range(len(fns))]
 
 
 def time_flushed(fn, reps, flush, stream):
@@ -630,57 +747,68 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None)
     TT = {"f32": torch.float32, "f64": torch.float64}
 
     if want("hyb"):
-        # -- HYB (ELL + COO), the paper's comparison format -----------------------
-        hyb = []
+        # -- HYB (ELL + COO), the paper's comparison format, timed like the
+        # RgCSR cases (three rotating copies in a graph) ---------------------
+        forms["hyb"] = {}
         for name, A, x in mats:
             for dt in DTYPES:
-                H = HybMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dt]), A.n_cols, dtype=TT[dt])
                 c = by[f"{name}_{dt}"]
-                hyb.append((c, H, torch.empty_like(c["y"])))
-        us = time_rotating([lambda h=h: h[1].spmv(h[0]["x"], out=h[2]) for h in hyb], 30, stream)
-        forms["hyb"] = {}
-        for (c, H, _), t in zip(hyb, us):
-            A = c["A"]
-            nb = roofline.hyb_spmv_bytes(A.n_rows, A.n_cols, A.nnz, H.nnz_coo, VB[c["dt"]])
-            forms["hyb"][c["key"]] = {"gbs": nb / t / 1e3, "gflops": 2 * A.nnz / t / 1e3, "us": t,
-                                      "ell_width": H.ell_width, "nnz_coo": H.nnz_coo,
-                                      "rgcsr_speedup": t / detail[c["key"]]["us"]}
-        del hyb
+                Hs = [HybMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dt]), A.n_cols, dtype=TT[dt])
+                      for _ in range(COPIES)]
+                ys = [torch.empty_like(c["y"]) for _ in range(COPIES)]
+                t = rotating_us([lambda H=H, xj=cp[1], y=y: H.spmv(xj, out=y)
+                                 for H, cp, y in zip(Hs, c["copies"], ys)], stream)
+                H = Hs[0]
+                nb = roofline.hyb_spmv_bytes(A.n_rows, A.n_cols, A.nnz, H.nnz_coo, VB[dt])
+                forms["hyb"][c["key"]] = {"gbs": nb / t / 1e3, "gflops": 2 * A.nnz / t / 1e3, "us": t,
+                                          "ell_width": H.ell_width, "nnz_coo": H.nnz_coo,
+                                          "rgcsr_speedup": t / detail[c["key"]]["us"]}
+                del Hs, ys
+        torch.cuda.empty_cache()
 
     if want("quantized"):
-        # -- reduced-precision values (bf16 / fp16 + per-row scale) ----------------
+        # -- reduced-precision values (bf16 / fp16 + per-row scale), timed like
+        # the FP32 cases: three rotating copies (quantised from the three FP64
+        # copies) in a graph, x and y in float ------------------------------
         # The error is taken against the library's FP64 product (itself within
         # 1e-12 |A||x| of the CPU oracle in the parity tests), scaled by |A||x|.
-        quant, ref = [], {}
+        forms["quantized"] = {}
         for name in ("a", "b", "c"):
             c64, c32 = by[f"{name}_f64"], by[f"{name}_f32"]
             A = c32["A"]
             absA = RgCSRMatrix.from_csr(A.rowptr, A.col, np.abs(A.val), A.n_cols, dtype=torch.float64)
-            ref[name] = (c64["M"].spmv(c64["x"]), absA.spmv(c64["x"].abs()))
+            y64, absy = c64["M"].spmv(c64["x"]), absA.spmv(c64["x"].abs())
             del absA
+            # Q has c64's layout; take the FP32 case's schedule when the two
+            # layouts agree (Q computes in float), else c64's
+            same = all(c32["config"].get(k) == c64["config"].get(k) for k in ("group_size", "row_order"))
             for fmt in ("bf16", "f16"):
-                Q = c64["M"].quantized(fmt)
-                # Q has c64's layout; take the FP32 case's schedule when the two
-                # layouts agree (Q computes in float), else c64's
-                same = all(c32["config"].get(k) == c64["config"].get(k) for k in ("group_size", "row_order"))
-                Q.copy_schedule(c32["M"] if same else c64["M"])
-                yq = torch.empty(A.n_rows, dtype=torch.float32, device=dev)
+                Qs = []
+                for j in range(COPIES):
+                    Q = c64["copies"][j][0].quantized(fmt)
+                    Q.copy_schedule(c32["copies"][j][0] if same else c64["copies"][j][0])
+                    Qs.append(Q)
+                ys = [torch.empty(A.n_rows, dtype=torch.float32, device=dev) for _ in range(COPIES)]
+                xs = [cp[1] for cp in c32["copies"]]
                 # kernel: the default, or (G = 32, no schedule) 16-byte loads, whichever is faster here
                 kws = [{}]
-                if Q.group_size == 32 and Q._tiles is None and Q._long is None:
+                if Qs[0].group_size == 32 and Qs[0]._tiles is None and Qs[0]._long is None:
                     kws += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4)]
-                kw = min(kws, key=lambda k: autotune._time(lambda: Q.spmv(c32["x"], out=yq, **k), 8, flush))
-                quant.append((name, fmt, Q, c32["x"], yq, A, kw))
-        us = time_rotating([lambda q=q: q[2].spmv(q[3], out=q[4], **q[6]) for q in quant], 30, stream)
-        forms["quantized"] = {}
-        for (name, fmt, Q, x32, y, A, kw), t in zip(quant, us):
-            nb = roofline.rgcsr_spmv_bytes(A.n_rows, A.n_cols, A.nnz, Q.s.n_groups, 2, x_bytes=4, row_scale=True)
-            y64, absy = ref[name]
-            forms["quantized"][f"{name}_{fmt}"] = {
-                "gbs": nb / t / 1e3, "gflops": 2 * A.nnz / t / 1e3, "us": t,
-                "speedup_vs_f32": detail[f"{name}_f32"]["us"] / t, "kernel": kw or "default",
-                "max_err_over_absAx_vs_f64": max_scaled_error(y, y64, absy)}
-        del quant, ref
+                ts = {i: rotating_us([lambda Q=Q, xj=xj, y=y, k=k: Q.spmv(xj, out=y, **k)
+                                      for Q, xj, y in zip(Qs, xs, ys)], stream)
+                      for i, k in enumerate(kws)}
+                best = min(ts, key=ts.get)
+                t, kw = ts[best], kws[best]
+                Qs[0].spmv(xs[0], out=ys[0], **kw)
+                nb = roofline.rgcsr_spmv_bytes(A.n_rows, A.n_cols, A.nnz, Qs[0].s.n_groups, 2, x_bytes=4,
+                                               row_scale=True)
+                forms["quantized"][f"{name}_{fmt}"] = {
+                    "gbs": nb / t / 1e3, "gflops": 2 * A.nnz / t / 1e3, "us": t,
+                    "speedup_vs_f32": detail[f"{name}_f32"]["us"] / t, "kernel": kw or "default",
+                    "max_err_over_absAx_vs_f64": max_scaled_error(ys[0], y64, absy)}
+                del Qs, ys
+            del y64, absy
+        torch.cuda.empty_cache()
 
     if want("spmm"):
         # -- multi-RHS SpMM on (b) ------------------------------------------------

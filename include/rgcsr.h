@@ -183,8 +183,8 @@ int rgcsr_descending_order(const rgcsr_csr *A, int32_t *row_perm, void *workspac
  * rgcsr_plan_workspace_bytes(n_rows, group_size) fits in that array (up to
  * 16,709,631 groups, i.e. about 534 million rows at G = 32); larger ones
  * return RGCSR_ERR_WORKSPACE without touching the device.
- * The first call on a device looks up the array's device address for that
- * (current) device; make that first call before any stream capture.
+ * Every call looks up the array's device address on the current device
+ * (nothing is cached, so a device reset does not leave a stale address).
  * All calls share the one array: calls whose GPU work overlaps (several
  * host threads or streams at once) race on it and must be serialised. */
 #define RGCSR_PLAN_NOALLOC_SCRATCH_BYTES 65536

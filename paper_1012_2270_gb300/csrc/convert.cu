@@ -218,34 +218,12 @@ RGCSR_API int rgcsr_convert(const rgcsr_csr *A, const rgcsr_matrix *M, rgcsr_str
 // memory.  Its scratch (the plan's status block and scan partials) is one
 // fixed array of this library, resident on every GPU that loads it until
 // the process exits.  Host code must not hand the array's name to a kernel:
-// on the host that symbol is only a stand-in, so the device address is
-// looked up once per device with cudaGetSymbolAddress.
+// on the host that symbol is only a stand-in, so every call looks up the
+// array's device address on the current device with cudaGetSymbolAddress.
+// The lookup is not cached: after a device reset or a new primary context
+// the address may change, and the plan synchronises its stream anyway.
 // ---------------------------------------------------------------------------
-#include <mutex>
-
 static __device__ __align__(256) unsigned char g_plan_scratch[RGCSR_PLAN_NOALLOC_SCRATCH_BYTES];
-
-namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mutex;
-void *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_plan_scratch on the current device (first call per
-// device looks it up).
-int plan_scratch_address(void **out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return RGCSR_ERR_CUDA;
-    if (dev < 0 || dev >= kMaxDevices) return RGCSR_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_plan_scratch) != cudaSuccess || !p) return RGCSR_ERR_CUDA;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
-    return RGCSR_OK;
-}
-}  // namespace
 
 RGCSR_API int rgcsr_plan_noalloc(const rgcsr_csr *A, rgcsr_matrix *M, rgcsr_stream_t stream) {
     int st = check_csr(A);
@@ -254,7 +232,7 @@ RGCSR_API int rgcsr_plan_noalloc(const rgcsr_csr *A, rgcsr_matrix *M, rgcsr_stre
     const size_t need = rgcsr_plan_workspace_bytes(A->n_rows, M->group_size);
     if (need > sizeof(g_plan_scratch)) return RGCSR_ERR_WORKSPACE;   // beyond the fixed maximum
     void *scratch = nullptr;
-    if ((st = plan_scratch_address(&scratch)) != RGCSR_OK) return st;
+    if (cudaGetSymbolAddress(&scratch, g_plan_scratch) != cudaSuccess || !scratch) return RGCSR_ERR_CUDA;
     // rgcsr_plan clears the status block itself and overwrites every scan
     // partial it reads, so stale contents of the shared array do not matter.
     return rgcsr_plan(A, M, scratch, sizeof(g_plan_scratch), stream);

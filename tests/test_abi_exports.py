@@ -62,7 +62,15 @@ def test_workspace_sizes_host_only(lib):
     assert lib.hyb_workspace_bytes(1000, 1000) >= 8 * 1001
 
 
-def test_argument_errors_without_gpu(lib):
+def _argument_checks():
+    """Host-side argument checks, run by test_argument_errors_without_gpu
+    in a child process that sees no GPU.  Several calls below pass small
+    integers as device pointers; they are never dereferenced because the
+    library rejects the call first.  Without a visible device a check that
+    failed to fire would end in RGCSR_ERR_CUDA (and fail the test), never
+    in a device access."""
+    B.build()
+    lib = L.lib()
     assert lib.rgcsr_plan(None, None, None, 0, None) == L.RGCSR_ERR_INVALID_ARG
     A = L.CSR(n_rows=-1)
     M = L.Matrix(group_size=32)
@@ -103,6 +111,17 @@ def test_argument_errors_without_gpu(lib):
     M64 = L.Matrix(n_rows=4, n_cols=4, group_size=64, n_groups=1, value_type=L.F32, group_ptr=8, row_lengths=8)
     T = L.Tiles(**full)
     assert lib.rgcsr_spmv_tiles(ctypes.byref(M64), ctypes.byref(T), 8, 8, None) == L.RGCSR_ERR_INVALID_ARG
+
+
+def test_argument_errors_without_gpu():
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    code = ("import sys; sys.path[:0] = [%r, %r]; import test_abi_exports as t; t._argument_checks()"
+            % (here, os.path.dirname(here)))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
 
 
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):

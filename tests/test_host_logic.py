@@ -148,3 +148,42 @@ def test_algorithmic_bytes_count_the_arrays_read_and_written(G):
     nnz_coo = h.coo_row.size
     got = roofline.hyb_spmv_bytes(A.n_rows, A.n_cols, A.nnz, nnz_coo, 8)
     assert got == (A.nnz * 12 + h.coo_row.astype(np.int32).nbytes + A.n_cols * 8 + A.n_rows * 8)
+
+
+def test_bench_headline_is_short_and_parses():
+    # the bench ends with one JSON line that a reader keeping only the last
+    # few KB of output can parse: every field at its longest realistic size
+    # (six cases, every form summary, long sample strings) stays under
+    # HEADLINE_MAX_BYTES and round-trips through json
+    import json
+    import bench
+    big = 123456.789012345
+    roof = {"bound": "hbm", "achieved": big, "peak": big, "unit": "GB/s", "frac": 0.123456789,
+            "traffic": big * 1e3, "kernel": "rgcsr_spmv_tiles_pipe_kernel<double>",
+            "cases": ["b_f32", "b_f64", "c_f64"], "peak_source": "measured", "share_of_step": 0.3,
+            "bytes_per_launch": big * 1e3, "avg_launch_us": big,
+            "same_size_read": {"gbs": big, "frac": 0.5},
+            "gather_request_ceiling": {"us": big, "frac": 0.6, "sm_mhz": 2070.0}}
+    e2e = {"value": big, "unit": "GB/s", "h2d_bytes_per_step": 123456789, "d2h_bytes_per_step": 123456789}
+    cpu = {"value": big, "unit": "GB/s", "cores": 144, "kind": "oracle",
+           "sample": "x" * 90}
+    clocks = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap", "hw_slowdown"]}
+    cases = {f"{n}_{d}": [big, big] for n in "abc" for d in ("f32", "f64")}
+    forms = {"quantized": {"a_bf16": {"speedup_vs_f32": 1.123456, "max_err_over_absAx_vs_f64": 1.2345e-7}},
+             "batched_512_f32": {"gbs": big, "speedup_vs_plain": 10.123456},
+             "backward_b_k8_f32": {"backward_over_forward": 2.123456},
+             "hyb": {k: {"rgcsr_speedup": 1.123456} for k in cases},
+             "ir_cg_poisson128": {"fp64_cg_ms": 50.123, "ms": 40.123},
+             "spmm_b_f32": {"k8": {"gflops": big}}}
+    line = bench.headline(value=big, world=8, steps=300, warmup=10, ms_per_step=0.351234567, gflops=big,
+                          launches=2400, clocks=clocks, roof=roof, e2e=e2e, cpu=cpu, cases=cases,
+                          forms_summary=bench.forms_summary(forms),
+                          detail_file="some/dir/bench_detail.json")
+    text = json.dumps(line)
+    assert len(text.encode()) < bench.HEADLINE_MAX_BYTES, len(text)
+    back = json.loads(text)
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "dtype", "config", "clocks", "roofline", "cpu_baseline", "e2e", "gpu_launches"):
+        assert key in back
+    assert back["roofline"]["frac"] == pytest.approx(0.1235, rel=1e-3)
+    assert "workload" in back["config"]

@@ -6,7 +6,7 @@ workspace, on consecutive calls that share its one fixed scratch array, and
 refuses matrices whose scratch would exceed that array.
 
 This file is collected last on purpose, and passes alone or after the
-other tests (the array's device address is looked up on first use)."""
+other tests (every call looks up the array's device address)."""
 import ctypes
 
 import numpy as np
@@ -89,10 +89,22 @@ def test_noalloc_plan_reports_validation_errors(lib):
 
 
 def test_noalloc_plan_rejects_beyond_fixed_maximum(lib):
-    # 16,709,632 groups need more than the fixed array; refused before any
-    # device access (the pointers below are never dereferenced)
-    c = L.CSR(n_rows=16_709_632, n_cols=10, nnz=0, row_ptr=16, row_ptr_type=L.I64T,
-              value_type=L.F32, col_idx=0, values=0)
-    M = L.Matrix(group_size=1, value_type=L.F32, row_lengths=16, group_ptr=16)
-    assert lib.rgcsr_plan_noalloc(ctypes.byref(c), ctypes.byref(M), None) == L.RGCSR_ERR_WORKSPACE
-    assert lib.rgcsr_plan_workspace_bytes(16_709_631, 1) <= 65536
+    # 16,709,632 groups (G = 1) need more scratch than the fixed array holds:
+    # refused with RGCSR_ERR_WORKSPACE.  Every buffer is a real device array
+    # of the size the call declares (an empty valid CSR), so even a missed
+    # check could only touch memory that belongs to the call.
+    n = 16_709_632
+    assert lib.rgcsr_plan_workspace_bytes(n - 1, 1) <= 65536
+    assert lib.rgcsr_plan_workspace_bytes(n, 1) > 65536
+    rp = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    col = torch.zeros(1, dtype=torch.int32, device="cuda")
+    val = torch.zeros(1, dtype=torch.float32, device="cuda")
+    rl = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    gp = torch.full((n + 1,), -7, dtype=torch.int64, device="cuda")
+    c = L.CSR(n_rows=n, n_cols=10, nnz=0, row_ptr=rp.data_ptr(), row_ptr_type=L.I64T,
+              value_type=L.F32, col_idx=col.data_ptr(), values=val.data_ptr())
+    M = L.Matrix(group_size=1, value_type=L.F32, row_lengths=rl.data_ptr(), group_ptr=gp.data_ptr())
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.rgcsr_plan_noalloc(ctypes.byref(c), ctypes.byref(M), stream) == L.RGCSR_ERR_WORKSPACE
+    torch.cuda.synchronize()
+    assert int(rl[0]) == -7 and int(gp[-1]) == -7          # nothing written
