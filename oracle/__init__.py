@@ -86,6 +86,7 @@ def _load():
         "orc_spmm_grad_values": (None, [I64, I64, P, P, P, P, P]),
         "orc_jacobi": (None, [I64, P, P, P, P, P, ctypes.c_double, I64, P]),
         "orc_jacobi_grad": (ctypes.c_double, [I64, P, P, P, P, P, ctypes.c_double, I64, P, P]),
+        "orc_jacobi_grad_bound": (None, [I64, P, P, P, P, P, ctypes.c_double, I64, ctypes.c_double, P, P]),
         "orc_cg": (I64, [I64, P, P, P, P, ctypes.c_double, I64, P]),
     }
     for name, (res, args) in sig.items():
@@ -412,6 +413,22 @@ def jacobi_grad(rowptr, col, val, dinv, b, omega: float, steps: int):
     loss = _load().orc_jacobi_grad(n, _p(rowptr), _p(col), _p(val), _p(dinv), _p(b),
                                    float(omega), int(steps), _p(db), _p(dval))
     return float(loss), db, dval
+
+
+def jacobi_grad_bound(rowptr, col, val, dinv, b, omega: float, steps: int, u: float):
+    """Elementwise bounds on the error of (d loss/d b, d loss/d values) of
+    ``jacobi_grad`` when they are computed in a floating-point format with
+    unit roundoff u (2**-24 for float), any summation order: the running
+    error recursions of oracle.c (first order in u)."""
+    rowptr, col, val = _csr(rowptr, col, val)
+    dinv = np.ascontiguousarray(dinv, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n = rowptr.size - 1
+    db = np.empty(n, np.float64)
+    dval = np.empty(val.size, np.float64)
+    _load().orc_jacobi_grad_bound(n, _p(rowptr), _p(col), _p(val), _p(dinv), _p(b), float(omega), int(steps),
+                                  float(u), _p(db), _p(dval))
+    return db, dval
 
 
 def cg(rowptr, col, val, b, tol: float, maxit: int):

@@ -472,6 +472,160 @@ double orc_jacobi_grad(int64_t n, const int64_t *rowptr, const int32_t *col,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Elementwise error bounds for the Jacobi gradients of orc_jacobi_grad    */
+/* when they are computed in a floating-point format of unit roundoff u    */
+/* (2^-24 for float), first order in u.  This is the tolerance of a        */
+/* reduced-precision implementation, not a result of the method; it        */
+/* follows the standard model fl(a op b) = (a op b)(1 + e), |e| <= u, and   */
+/* gamma_m = m u / (1 - m u) (any m-term sum or product chain).           */
+/*                                                                          */
+/* Rounding model covered (any order of the sums, fused or not):            */
+/*   forward:  y = fl(A x) (sum of at most La terms, La = longest row of A) */
+/*             x' = fl(x + fl(fl(w_r d_r) fl(b_r - y)))  with omega, dinv  */
+/*             and b first rounded to the format (w_r, d_r, b_r);           */
+/*   adjoint:  lam_T = 2 x_T (exact);  w = fl(fl(w_r d_r) lam),             */
+/*             g = fl(A^T w) (at most Lt terms, Lt = longest row of A^T),   */
+/*             lam' = fl(lam - g);                                          */
+/*   db   = the sum over the T steps of w (any order);                      */
+/*   dval = the sum over the T steps of fl(fl(-w_r d_r) lam) * x (any       */
+/*          order).                                                         */
+/* With x_s, lam_s the exact iterates, J = I - omega D A (D = diag(dinv)),  */
+/* a_s = |x_s| + E_s and l_s = |lam_s| + M_s:                               */
+/*   E_0 = 0,  E_{s+1} = |J| E_s + g(La+7) omega |D| (|b| + |A| a_s)        */
+/*                        + u a_s                                           */
+/*   M_T = 2 E_T,  M_s = |J|^T M_{s+1} + g(Lt+6) |A|^T (omega |D| l_{s+1})  */
+/*                        + u l_{s+1}                                       */
+/*   |db~ - db| <= sum_s [omega |D| M_{s+1} + g4 omega |D| l_{s+1}]         */
+/*                 + g(T-1) sum_s (1+g4) omega |D| l_{s+1}                  */
+/*   |dval~_p - dval_p| <= sum_s omega|d_i| [M_{s+1,i} a_{s,j}              */
+/*                 + |lam_{s+1,i}| E_{s,j} + g5 l_{s+1,i} a_{s,j}]          */
+/*                 + g(T-1) sum_s (1+g5) omega |d_i| l_{s+1,i} a_{s,j}      */
+/* for entry p in row i, column j.  Derivation: the computed step differs  */
+/* from the exact step applied to the computed iterate by at most the      */
+/* rounding terms above, and that difference propagates through J (or J^T  */
+/* in the adjoint); second-order terms are absorbed by the gamma constants */
+/* (gamma_a + gamma_b + gamma_a gamma_b <= gamma_{a+b}).  u = 0 gives 0.    */
+/* ------------------------------------------------------------------------ */
+static double orc_gamma(double m, double u)
+{
+    return m * u / (1.0 - m * u);
+}
+
+/* y = |A| v (or |A|^T v when transposed is non-zero), entries of |A| are |val|. */
+static void orc_abs_matvec(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val,
+                           const double *v, double *y, int transposed)
+{
+    if (!transposed) {
+        for (int64_t i = 0; i < n; i++) {
+            double s = 0.0;
+            for (int64_t p = rowptr[i]; p < rowptr[i + 1]; p++) s += fabs(val[p]) * v[col[p]];
+            y[i] = s;
+        }
+    } else {
+        for (int64_t i = 0; i < n; i++) y[i] = 0.0;
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t p = rowptr[i]; p < rowptr[i + 1]; p++) y[col[p]] += fabs(val[p]) * v[i];
+    }
+}
+
+/* y = |J| v or |J|^T v for J = I - omega D A (square A). */
+static void orc_abs_jacobi_matvec(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val,
+                                  const double *dinv, double omega, const double *v, double *y,
+                                  int transposed)
+{
+    for (int64_t i = 0; i < n; i++) y[i] = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double diag = 1.0;                  /* J_ii = 1 - omega d_i a_ii (duplicates summed) */
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; p++)
+            if (col[p] == i) diag -= omega * dinv[i] * val[p];
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            if (col[p] == i) continue;
+            double jij = fabs(omega * dinv[i] * val[p]);
+            if (!transposed) y[i] += jij * v[col[p]];
+            else y[col[p]] += jij * v[i];
+        }
+        y[i] += fabs(diag) * v[i];
+    }
+}
+
+void orc_jacobi_grad_bound(int64_t n, const int64_t *rowptr, const int32_t *col,
+                           const double *val, const double *dinv, const double *b,
+                           double omega, int64_t steps, double u,
+                           double *db_bound, double *dval_bound)
+{
+    int64_t nnz = rowptr[n];
+    int64_t La = 0, Lt = 0;
+    int64_t *ccount = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    for (int64_t i = 0; i < n; i++) {
+        if (rowptr[i + 1] - rowptr[i] > La) La = rowptr[i + 1] - rowptr[i];
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; p++) ccount[col[p]]++;
+    }
+    for (int64_t j = 0; j < n; j++) if (ccount[j] > Lt) Lt = ccount[j];
+    free(ccount);
+    const double gf = orc_gamma((double)(La + 7), u), gb = orc_gamma((double)(Lt + 6), u);
+    const double g4 = orc_gamma(4.0, u), g5 = orc_gamma(5.0, u);
+    const double gT = orc_gamma((double)(steps > 1 ? steps - 1 : 0), u);
+    /* exact iterates x_s and their bounds E_s, s = 0..T */
+    double *xs = (double *)calloc((size_t)(n * (steps + 1)), sizeof(double));
+    double *Es = (double *)calloc((size_t)(n * (steps + 1)), sizeof(double));
+    double *t1 = (double *)malloc((size_t)n * sizeof(double));
+    double *t2 = (double *)malloc((size_t)n * sizeof(double));
+    double *a = (double *)malloc((size_t)n * sizeof(double));
+    for (int64_t s = 0; s < steps; s++) {
+        double *xc = xs + s * n, *xn = xs + (s + 1) * n, *Ec = Es + s * n, *En = Es + (s + 1) * n;
+        orc_csr_spmv(n, rowptr, col, val, xc, t1, NULL);
+        for (int64_t i = 0; i < n; i++) xn[i] = xc[i] + omega * dinv[i] * (b[i] - t1[i]);
+        for (int64_t i = 0; i < n; i++) a[i] = fabs(xc[i]) + Ec[i];
+        orc_abs_matvec(n, rowptr, col, val, a, t1, 0);                        /* |A| a_s */
+        orc_abs_jacobi_matvec(n, rowptr, col, val, dinv, omega, Ec, t2, 0);    /* |J| E_s */
+        for (int64_t i = 0; i < n; i++)
+            En[i] = t2[i] + gf * omega * fabs(dinv[i]) * (fabs(b[i]) + t1[i]) + u * a[i];
+    }
+    /* adjoint: exact lam_s and its bound M_s, accumulated into the bounds */
+    double *lam = (double *)malloc((size_t)n * sizeof(double));
+    double *M = (double *)malloc((size_t)n * sizeof(double));
+    double *l = (double *)malloc((size_t)n * sizeof(double));
+    double *wl = (double *)malloc((size_t)n * sizeof(double));
+    double *dval_sum = (double *)calloc((size_t)(nnz > 0 ? nnz : 1), sizeof(double));
+    double *db_sum = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    for (int64_t i = 0; i < n; i++) {
+        lam[i] = 2.0 * xs[steps * n + i];
+        M[i] = 2.0 * Es[steps * n + i];
+        db_bound[i] = 0.0;
+    }
+    for (int64_t p = 0; p < nnz; p++) dval_bound[p] = 0.0;
+    for (int64_t s = steps - 1; s >= 0; s--) {
+        const double *xc = xs + s * n, *Ec = Es + s * n;
+        /* here lam = lam_{s+1}, M = M_{s+1} */
+        for (int64_t i = 0; i < n; i++) {
+            l[i] = fabs(lam[i]) + M[i];
+            wl[i] = omega * fabs(dinv[i]) * l[i];
+            db_bound[i] += omega * fabs(dinv[i]) * M[i] + g4 * wl[i];
+            db_sum[i] += (1.0 + g4) * wl[i];
+        }
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t p = rowptr[i]; p < rowptr[i + 1]; p++) {
+                const int64_t j = col[p];
+                const double aj = fabs(xc[j]) + Ec[j], od = omega * fabs(dinv[i]);
+                dval_bound[p] += od * (M[i] * aj + fabs(lam[i]) * Ec[j]) + g5 * od * l[i] * aj;
+                dval_sum[p] += (1.0 + g5) * od * l[i] * aj;
+            }
+        /* lam_s = lam_{s+1} - A^T (omega D lam_{s+1}) */
+        for (int64_t i = 0; i < n; i++) t1[i] = omega * dinv[i] * lam[i];
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t p = rowptr[i]; p < rowptr[i + 1]; p++) lam[col[p]] -= val[p] * t1[i];
+        /* M_s = |J|^T M_{s+1} + gamma(Lt+6) |A|^T (omega |D| l_{s+1}) + u l_{s+1} */
+        orc_abs_jacobi_matvec(n, rowptr, col, val, dinv, omega, M, t2, 1);
+        orc_abs_matvec(n, rowptr, col, val, wl, t1, 1);
+        for (int64_t i = 0; i < n; i++) M[i] = t2[i] + gb * t1[i] + u * l[i];
+    }
+    for (int64_t i = 0; i < n; i++) db_bound[i] += gT * db_sum[i];
+    for (int64_t p = 0; p < nnz; p++) dval_bound[p] += gT * dval_sum[p];
+    free(xs); free(Es); free(t1); free(t2); free(a);
+    free(lam); free(M); free(l); free(wl); free(dval_sum); free(db_sum);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Conjugate gradients in double precision (Krylov context of Sec. 1: CG    */
 /* needs SpMV, SAXPY and SDOT).  Textbook CG from x_0 = 0, stopping when    */
 /* ||r||_2 <= tol * ||b||_2 or after maxit iterations.  Returns iterations. */

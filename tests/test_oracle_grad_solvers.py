@@ -113,3 +113,132 @@ def test_cg_solves_poisson():
     assert np.linalg.norm(D @ x - b) <= 1e-12 * np.linalg.norm(b) * 1.01
     assert np.linalg.norm(x - xr) <= 1e-10 * np.linalg.norm(xr)
     assert 0 < it < 2000
+
+
+# ---------------------------------------------------------------------------
+# the error bound of reduced-precision Jacobi gradients (the tolerance of the
+# 96^3 FP32 parity test), pinned against an independent float32 evaluation
+# ---------------------------------------------------------------------------
+def _ell(rowptr, col, val, n):
+    """Rows padded to the longest (column 0, value 0): slot j of every row."""
+    L = np.diff(rowptr)
+    K = int(L.max()) if n else 0
+    C = np.zeros((n, K), np.int64)
+    V = np.zeros((n, K), np.float64)
+    for i in range(n):
+        C[i, :L[i]] = col[rowptr[i]:rowptr[i + 1]]
+        V[i, :L[i]] = val[rowptr[i]:rowptr[i + 1]]
+    return C, V
+
+
+def _f32_jacobi_grads(A, dinv, b, omega, steps, order):
+    """The damped-Jacobi gradient evaluated step by step in float32 (numpy
+    rounds every operation to float32): row sums in stored order ("fwd"),
+    reversed ("rev"), or each row summed exactly and rounded once ("once",
+    like a fused accumulation)."""
+    f = np.float32
+    n = A.n_rows
+    C, V = _ell(A.rowptr, A.col, A.val, n)
+    rows = np.repeat(np.arange(n), np.diff(A.rowptr))
+    # A^T in the same padded form
+    Ct, Vt = _ell(*_transpose(A.rowptr, A.col, A.val, n), n)
+    V32, Vt32 = V.astype(f), Vt.astype(f)
+
+    def matvec(Cm, Vm, Vm32, x):
+        if order == "once":
+            return (Vm * x.astype(np.float64)[Cm]).sum(axis=1).astype(f)
+        js = range(Cm.shape[1]) if order == "fwd" else reversed(range(Cm.shape[1]))
+        y = np.zeros(n, f)
+        for j in js:
+            y = y + Vm32[:, j] * x[Cm[:, j]]
+        return y
+
+    d32, b32, w32 = dinv.astype(f), b.astype(f), f(omega)
+    xs = [np.zeros(n, f)]
+    for _ in range(steps):
+        x = xs[-1]
+        xs.append(x + (w32 * d32) * (b32 - matvec(C, V, V32, x)))
+    lam = f(2) * xs[-1]
+    db = np.zeros(n, f)
+    dval = np.zeros(A.nnz, f)
+    for s in range(steps - 1, -1, -1):
+        w = (w32 * d32) * lam
+        db = db + w
+        dval = dval + ((-w32) * d32 * lam)[rows] * xs[s][A.col]
+        lam = lam - matvec(Ct, Vt, Vt32, w)
+    return db.astype(np.float64), dval.astype(np.float64)
+
+
+def _transpose(rowptr, col, val, m):
+    trp, tc, perm = oracle.csr_transpose(rowptr, col, m)
+    return trp, tc, np.asarray(val)[perm]
+
+
+def _dominant_matrix(n, seed):
+    """Non-symmetric, diagonally dominant, values exact in float32."""
+    rng = np.random.default_rng(seed)
+    A = synth.random_csr(n, n, rng.integers(2, 9, n), seed=seed)
+    A.val = np.round(rng.uniform(-1, 1, A.nnz) * 1024) / 1024
+    rows = np.repeat(np.arange(n), np.diff(A.rowptr))
+    off = A.col != rows
+    A.val[~off] = 0.0
+    dsum = np.bincount(rows[off], np.abs(A.val[off]), minlength=n)
+    # make every diagonal entry present: rows without one get it added
+    keep = [(i, A.col[A.rowptr[i]:A.rowptr[i + 1]], A.val[A.rowptr[i]:A.rowptr[i + 1]]) for i in range(n)]
+    rp, cols, vals = [0], [], []
+    for i, c, v in keep:
+        c = c.copy(); v = v.copy()
+        d = np.ceil((1.0 + dsum[i]) * 8) / 8
+        if i in c:
+            v[c == i] = d
+        else:
+            c = np.append(c, i); v = np.append(v, d)
+            o = np.argsort(c, kind="stable"); c, v = c[o], v[o]
+        cols.append(c); vals.append(v); rp.append(rp[-1] + c.size)
+    A.rowptr = np.array(rp, np.int64)
+    A.col = np.concatenate(cols).astype(np.int32)
+    A.val = np.concatenate(vals)
+    return A
+
+
+@pytest.mark.parametrize("which", ["laplace", "dominant"])
+def test_jacobi_grad_bound_holds_for_float32_and_is_not_vacuous(which):
+    if which == "laplace":
+        A = synth.laplacian_3d(8)
+        dinv = np.full(A.n_rows, 1.0 / 6.0)
+    else:
+        A = _dominant_matrix(300, 4)
+        rows = np.repeat(np.arange(A.n_rows), np.diff(A.rowptr))
+        dinv = 1.0 / A.val[A.col == rows]
+    b = synth.uniform_vector(A.n_rows, seed=2)
+    omega, steps = 2.0 / 3.0, 100
+    _, db_ref, dval_ref = oracle.jacobi_grad(A.rowptr, A.col, A.val, dinv, b, omega, steps)
+    u = 2.0 ** -24
+    db_b, dval_b = oracle.jacobi_grad_bound(A.rowptr, A.col, A.val, dinv, b, omega, steps, u)
+    worst = 0.0
+    for order in ("fwd", "rev", "once"):
+        db, dval = _f32_jacobi_grads(A, dinv, b, omega, steps, order)
+        e_db, e_dv = np.abs(db - db_ref), np.abs(dval - dval_ref)
+        assert (e_db <= db_b).all() and (e_dv <= dval_b).all(), order
+        worst = max(worst, (e_db / db_b).max(), (e_dv / dval_b).max())
+    # not vacuous: the observed float32 error reaches about 1-3% of it (a
+    # worst-case first-order bound against errors that partly cancel), and
+    # the same bound for a format with 256x less roundoff is violated
+    assert worst > 5e-3
+    db_t, dval_t = oracle.jacobi_grad_bound(A.rowptr, A.col, A.val, dinv, b, omega, steps, u / 256)
+    db, dval = _f32_jacobi_grads(A, dinv, b, omega, steps, "fwd")
+    assert (np.abs(db - db_ref) > db_t).any() or (np.abs(dval - dval_ref) > dval_t).any()
+    # and useful: far below the gradients themselves
+    assert np.median(dval_b / np.maximum(np.abs(dval_ref), 1e-30)) < 1e-3
+
+
+def test_jacobi_grad_bound_vanishes_without_rounding_and_grows_with_u():
+    A = synth.laplacian_3d(5)
+    dinv = np.full(A.n_rows, 1.0 / 6.0)
+    b = synth.uniform_vector(A.n_rows, seed=1)
+    db0, dv0 = oracle.jacobi_grad_bound(A.rowptr, A.col, A.val, dinv, b, 2 / 3, 20, 0.0)
+    assert not db0.any() and not dv0.any()
+    db1, dv1 = oracle.jacobi_grad_bound(A.rowptr, A.col, A.val, dinv, b, 2 / 3, 20, 2.0 ** -30)
+    db2, dv2 = oracle.jacobi_grad_bound(A.rowptr, A.col, A.val, dinv, b, 2 / 3, 20, 2.0 ** -29)
+    # first order in u: doubling u doubles the bound (to within the gamma terms)
+    assert np.allclose(db2, 2 * db1, rtol=1e-6) and np.allclose(dv2, 2 * dv1, rtol=1e-6)
