@@ -64,6 +64,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip HYB and the other forms")
     p.add_argument("--forms", default="", help="comma-separated subset of the forms to run (default: all)")
+    p.add_argument("--cases", default="",
+                   help="comma-separated subset of the six cases (a_f32, ..., c_f64) for profiling runs; "
+                        "the default runs all six (the step the metric is defined on)")
     p.add_argument("--detail-out", default=None,
                    help="write the full record (per-case detail, forms) to this JSON file; "
                         "default: print it on one line starting with 'detail: ' before the headline")
@@ -120,6 +123,8 @@ def kernel_name(cfg, M, A, dt):
     k = cfg.get("kernel", 0)
     if k == 4 and cfg.get("variant", 0) in (1, 2, 4):
         return f"rgcsr_spmv_vec<{t}>"
+    if k == 4 and cfg.get("variant", 0) in (5, 6, 7):
+        return f"rgcsr_spmv_vecp<{t}>"
     if k == 0:
         n = A.n_rows
         dense = (M.n_stored * 4 <= M.nnz * 5 and
@@ -447,8 +452,11 @@ def run_ours(args):
     if args.tune_cache:
         autotune.CACHE_PATH = os.path.abspath(args.tune_cache)
     cases = []
+    only = set(args.cases.split(",")) if args.cases else None
     for name, A, x in mats:
         for dt in DTYPES:
+            if only is not None and f"{name}_{dt}" not in only:
+                continue
             tdt = torch.float32 if dt == "f32" else torch.float64
             vals = A.val.astype(NP[dt])
             # group size, kernel and long-row schedule chosen by timing on this GPU
@@ -538,15 +546,31 @@ def run_ours(args):
     for c in cases:
         if c["dt"] == "f64":
             detail[c["key"]]["fp64_fma_floor_us"] = 1e6 * c["nnz"] / fma_rate
+    # ---- random-gather rate (the library's probe: scattered 8-byte loads of
+    # an 8 MB vector resident in L2), the ceiling of the power-law matrix's
+    # x gathers ----
+    from paper_1012_2270_gb300.rgcsr import gather_probe
+    gx = torch.ones(1 << 20, dtype=torch.float64, device=dev)
+    gather_probe(gx, 16, stream)
+    g_t = []
+    for _ in range(3):
+        e0, e1 = _ev()
+        e0.record(stream)
+        n_loads = gather_probe(gx, 256, stream)
+        e1.record(stream)
+        e1.synchronize()
+        g_t.append(e0.elapsed_time(e1) * 1e-3)
+    gather_rate = n_loads / statistics.median(g_t)                 # loads/s
+    del gx
 
-    roof = roofline_of(cases, per_case_us, detail, fma_rate, clk, dev)
+    roof = roofline_of(cases, per_case_us, detail, fma_rate, clk, dev, gather_rate)
 
     # ---- end to end: host x in, host y out, through rgcsr_spmv_host ----
     e2e = measure_e2e(cases, world, step_bytes, K, stream, barrier, dev)
 
     # ---- forms beside plain ----
     forms = {}
-    if not args.no_forms and rank == 0:
+    if not args.no_forms and rank == 0 and only is None:         # the forms compare against all six cases
         forms = measure_forms(mats, cases, detail, dev, stream, tune_cache=bool(args.tune_cache),
                               only=set(args.forms.split(",")) if args.forms else None)
 
@@ -580,7 +604,7 @@ def run_ours(args):
     return 0
 
 
-def roofline_of(cases, per_case_us, detail, fma_rate, clk, dev):
+def roofline_of(cases, per_case_us, detail, fma_rate, clk, dev, gather_rate):
     """Roofline of the dominant kernel (the one with the largest share of
     the step): algorithmic bytes per launch / its mean time per launch from
     the per-case graphs, against the measured HBM copy bandwidth."""
@@ -622,16 +646,18 @@ def roofline_of(cases, per_case_us, detail, fma_rate, clk, dev):
             "hbm_floor_us": 1e6 * sum(c["bytes"] for c, _ in dom_cases) / (peak_hbm * 1e9),
             "kernel_us": t_us, "frac_of_probe": (1e6 * nnz / fma_rate) / t_us}
     if all(c["name"] == "b" for c, _ in dom_cases):
-        # random columns: every x gather is its own L2 request, and an SM
-        # sends at most about one request per clock -- a second ceiling below
-        # HBM (one request per non-zero plus one per 128-byte line of the
-        # algorithmic bytes)
+        # random columns: every x gather is its own L2 request.  The
+        # library's gather probe measures how many scattered loads per second
+        # the SMs issue (about one per SM clock); the kernel's requests -- one
+        # per non-zero plus one per 128-byte line of the algorithmic bytes --
+        # at that rate are a second ceiling, below HBM
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         mhz = (clk or {}).get("sm_mhz") or 1920.0
         reqs = [c["nnz"] + c["bytes"] / 128 for c, _ in dom_cases]
-        ceil_us = statistics.fmean(r / (sms * mhz) for r in reqs)
+        ceil_us = statistics.fmean(1e6 * r / gather_rate for r in reqs)
         t_us = statistics.fmean(us for _, us in dom_cases)
-        roof["gather_request_ceiling"] = {"us": ceil_us, "frac": ceil_us / t_us, "sm_mhz": mhz}
+        roof["gather_request_ceiling"] = {"us": ceil_us, "frac": ceil_us / t_us,
+                                          "probe_loads_per_sm_clk": gather_rate / (sms * mhz * 1e6)}
     return roof
 
 
@@ -725,8 +751,8 @@ def max_scaled_error(y, y_ref, absy):
 
 def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None):
     """The forms beside the plain SpMV; `only` (a set of names: hyb,
-    quantized, spmm, backward, ir_cg, jacobi, conversion, group_size_sweep,
-    table6, batched) limits them, None runs all."""
+    quantized, x_read_path, spmm, backward, ir_cg, jacobi, conversion,
+    group_size_sweep, table6, batched) limits them, None runs all."""
     import torch
     from paper_1012_2270_gb300 import solvers
     from paper_1012_2270_gb300.autograd import SparseOperator, spmm
@@ -793,7 +819,7 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None)
                 # kernel: the default, or (G = 32, no schedule) 16-byte loads, whichever is faster here
                 kws = [{}]
                 if Qs[0].group_size == 32 and Qs[0]._tiles is None and Qs[0]._long is None:
-                    kws += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4)]
+                    kws += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4, 5, 6, 7)]
                 ts = {i: rotating_us([lambda Q=Q, xj=xj, y=y, k=k: Q.spmv(xj, out=y, **k)
                                       for Q, xj, y in zip(Qs, xs, ys)], stream)
                       for i, k in enumerate(kws)}
@@ -809,6 +835,40 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None)
                 del Qs, ys
             del y64, absy
         torch.cuda.empty_cache()
+
+    if want("x_read_path"):
+        # -- the x read-path study (Sec. 4.3: texture cache on/off), redone on
+        # the same thread-per-row mapping (G = 32, the cases' own layouts) with
+        # the four read paths: read-only loads, plain loads, texture fetches,
+        # and x ranges staged in shared memory per block of 256 rows ---------
+        # (the power-law matrix, whose rows reach 10,000 entries, takes the
+        # warp-split kernel, and its blocks touch too many scattered columns
+        # for any window: every one of them would gather from global memory)
+        xr = {}
+        for c in cases:
+            stencil = c["name"] != "b"
+            k_ = L.KERNEL_LEAN if stencil else L.KERNEL_SPLIT
+            row = {"kernel": "thread per row" if stencil else "warp split"}
+            for key, kw in (("nc", dict(kernel=k_, x_load=L.XLOAD_NC)),
+                            ("plain", dict(kernel=k_, x_load=L.XLOAD_PLAIN)),
+                            ("tex", dict(kernel=k_, x_load=L.XLOAD_TEX))):
+                row[key + "_us"] = rotating_us([lambda M=M, xj=xj, y=y, kw=kw: M.spmv(xj, out=y, **kw)
+                                                for M, xj, y in c["copies"]], stream)
+            if stencil:
+                for cp in c["copies"]:
+                    cp[0].plan_x_window()
+                recs = c["copies"][0][0].x_window_records()
+                row["staged_blocks_pct"] = 100.0 * sum(1 for r in recs if r[0] > 0) / max(len(recs), 1)
+                row["mean_staged_elems"] = statistics.fmean([r[1] for r in recs if r[0] > 0] or [0])
+                row["smem_window_us"] = rotating_us([lambda M=M, xj=xj, y=y: M.spmv_xwindow(xj, out=y)
+                                                     for M, xj, y in c["copies"]], stream)
+                for cp in c["copies"]:
+                    cp[0]._xwin = None
+            for k in ("nc", "plain", "tex", "smem_window"):
+                if k + "_us" in row:
+                    row[k + "_gbs"] = c["bytes"] / row[k + "_us"] / 1e3
+            xr[c["key"]] = row
+        forms["x_read_path_g32"] = xr
 
     if want("spmm"):
         # -- multi-RHS SpMM on (b) ------------------------------------------------
@@ -875,10 +935,12 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None)
         rhs = torch.from_numpy(synth.uniform_vector(a.n_rows, seed=0)).to(dev)
         lo = M64.quantized("bf16")
         e0, e1 = _ev()
+        torch.cuda.nvtx.range_push("ir_cg")                # a profiler can pick it out
         e0.record(stream)
         x_ir, outer, inner, rel = solvers.ir_cg(M64, lo, rhs, outer_tol=1e-10, max_outer=50, inner_tol=1e-4,
                                                  max_inner=500)
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         t_ir = e0.elapsed_time(e1)
         e0, e1 = _ev()
@@ -1066,6 +1128,7 @@ def measure_tables(mats, flush, stream):
                 row = {"artificial_zero_pct": M.artificial_zero_percent()}
                 for key, kw in (("paper_readonly_x", dict(kernel=L.KERNEL_PAPER)),
                                 ("paper_plain_x", dict(kernel=L.KERNEL_PAPER, x_load=L.XLOAD_PLAIN)),
+                                ("paper_texture_x", dict(kernel=L.KERNEL_PAPER, x_load=L.XLOAD_TEX)),
                                 ("split", dict(kernel=L.KERNEL_SPLIT)),
                                 ("sliced_ellpack", dict(kernel=L.KERNEL_SELL))):
                     t = time_flushed(lambda: M.spmv(xd, out=y, **kw), 5, flush, stream)

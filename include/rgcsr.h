@@ -118,6 +118,15 @@ typedef struct {
                                     slots of its group, padding multiplied          */
 #define RGCSR_XLOAD_NC      0    /* x through the read-only (non-coherent) path    */
 #define RGCSR_XLOAD_PLAIN   1    /* x with ordinary global loads                   */
+#define RGCSR_XLOAD_TEX     2    /* x by texture fetches from a texture object over
+                                    x (the paper's texture binding, Sec. 3.4, 4.3);
+                                    the library creates one per x buffer on first
+                                    use and keeps it (at most 64 per device: the
+                                    65th clears the cache after a device
+                                    synchronisation).  PLAIN and TEX need an
+                                    explicit PAPER, SPLIT or LEAN (variant 0)
+                                    kernel; x up to the device's 1D linear texture
+                                    width (RGCSR_ERR_INVALID_ARG beyond)           */
 typedef struct {
     int32_t kernel;             /* RGCSR_KERNEL_*                                  */
     int32_t block_threads;      /* 0 = default (256); multiple of 32, <= 256       */
@@ -131,8 +140,21 @@ typedef struct {
                                    (F64: 2) of a group, 2 slot-rows in flight
                                    (1), or 2 rows, 4 slot-rows in flight (2), or
                                    4 rows (F64: 2), 4 slot-rows in flight (4);
-                                   16-byte aligned values and columns; other
-                                   kernels: 0                                     */
+                                   5, 6, 7 = the same software-pipelined (the
+                                   next slot-rows' loads issued before the
+                                   current x gathers) with 16-byte value loads
+                                   (a lane owns 16 / value size rows: F64 2,
+                                   F32 4, BF16/F16 8), 2, 1 or 4 slot-rows per
+                                   stage; 16-byte aligned values and columns;
+                                   other kernels: 0                               */
+    int32_t wait_limit;         /* TMA kernel: non-blocking probes of a stage's
+                                   mbarrier before a wait gives up, 0 = default
+                                   (2^26, about a second).  A wait that runs out
+                                   records RGCSR_STATUS_TIMEOUT, lets the warp's
+                                   copies in flight finish (default bound), leaves
+                                   the rows of its remaining groups unwritten and
+                                   ends the warp.  Small values exist to test that
+                                   path; other kernels ignore the field.          */
 } rgcsr_launch;
 
 /* ----------------------------------------------------------------------- */
@@ -199,6 +221,37 @@ int rgcsr_plan_noalloc(const rgcsr_csr *A, rgcsr_matrix *M, rgcsr_stream_t strea
 int rgcsr_spmv(const rgcsr_matrix *M, const void *x, void *y, rgcsr_stream_t stream);
 int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
                   const rgcsr_launch *launch, rgcsr_stream_t stream);
+
+/* x staged in shared memory (the x read-path study of Sec. 4.3, not the
+ * paper's kernel).  For every block of RGCSR_XWINDOW_ROWS consecutive stored
+ * rows, rgcsr_xwindow_plan finds the columns the block's stored entries use
+ * (padding excluded), sorts them and cuts them into ranges wherever two
+ * consecutive used columns lie more than RGCSR_XWINDOW_GAP apart; a block
+ * with at most RGCSR_XWINDOW_MAX_RANGES ranges of at most
+ * RGCSR_XWINDOW_CAP_BYTES of x in all (x elements are 8 bytes for F64
+ * storage, else 4) is "staged", any other block (or one with more than 8,192
+ * stored entries) gets n_ranges = 0.  rgcsr_spmv_xwindow computes y = A x with
+ * one thread per stored row; a staged block first copies its ranges of x into
+ * shared memory and gathers from there, the others read x through the
+ * read-only path.  A 3D 7-point stencil's block of 256 rows touches three
+ * bands of x (1,024 elements), a banded matrix one.
+ *   windows: caller-allocated device array of rgcsr_xwindow_count(n_rows)
+ *   records, filled by rgcsr_xwindow_plan (async) and valid for M's pattern.
+ *   Every value type.  Async. */
+#define RGCSR_XWINDOW_ROWS        256
+#define RGCSR_XWINDOW_MAX_RANGES  4
+#define RGCSR_XWINDOW_GAP         64
+#define RGCSR_XWINDOW_CAP_BYTES   32768
+typedef struct {
+    int32_t n_ranges;           /* 0 = not staged                             */
+    int32_t total;              /* staged elements, sum of len                */
+    int32_t lo[RGCSR_XWINDOW_MAX_RANGES];    /* first column of each range    */
+    int32_t len[RGCSR_XWINDOW_MAX_RANGES];   /* columns in each range         */
+} rgcsr_xwindow;
+int64_t rgcsr_xwindow_count(int64_t n_rows);
+int rgcsr_xwindow_plan(const rgcsr_matrix *M, rgcsr_xwindow *windows, rgcsr_stream_t stream);
+int rgcsr_spmv_xwindow(const rgcsr_matrix *M, const rgcsr_xwindow *windows, const void *x, void *y,
+                       rgcsr_stream_t stream);
 
 /* Long-row segments, for matrices whose row lengths vary wildly (the
  * paper's weak point, Sec. 4.4.2: one very long row makes its whole group
@@ -416,6 +469,22 @@ int rgcsr_csr_row_index(const rgcsr_csr *A, int32_t *row_index, rgcsr_stream_t s
  * kept in CSR order, e.g. with src_index = M->slot_to_csr.  Async. */
 int rgcsr_gather_values(const rgcsr_matrix *M, const void *src, const int64_t *src_index,
                         rgcsr_stream_t stream);
+/* rgcsr_gather_values, skipped when M already holds these values: `state`
+ * is a caller-allocated device record of RGCSR_VALUES_STATE_BYTES bytes
+ * (8-byte aligned), zero-filled before its first use ("holds nothing"),
+ * one per matrix.  The call hashes src[0, n_src) -- two 64-bit sums over
+ * the elements of a bijective mix (the SplitMix64 finalizer) of the
+ * element's bits combined with its position, so any single changed element
+ * changes the hash -- compares the hash with the one the record holds,
+ * stores the new one, and gathers only if they differ or the record held
+ * nothing; the decision is taken on the device (two launches, no host
+ * synchronisation).  Several elements changed at once leave the hash
+ * unchanged only by chance (both sums equal, about 2^-128); zero the
+ * record to force a refresh.  One call per record in flight.  F64 or F32.
+ * Async. */
+#define RGCSR_VALUES_STATE_BYTES 8192
+int rgcsr_gather_values_if_changed(const rgcsr_matrix *M, const void *src, int64_t n_src,
+                                   const int64_t *src_index, void *state, rgcsr_stream_t stream);
 /* out[s] = inner[outer[s]], or -1 where outer[s] < 0 (n entries).  Async. */
 int rgcsr_compose_index(const int64_t *outer, const int64_t *inner, int64_t n, int64_t *out,
                         rgcsr_stream_t stream);
@@ -466,6 +535,17 @@ int rgcsr_convert_vector(int64_t n, const void *src, int32_t src_type, void *dst
  * a memory-bound kernel that moves the same bytes.  RGCSR_ERR_INVALID_ARG
  * for an unaligned pointer or size. */
 int rgcsr_stream_read(const void *data, int64_t bytes, void *sink, rgcsr_stream_t stream);
+/* Random-gather ceiling: *loads (host int64, written before the launch) =
+ * SMs x 1024 threads x 4 x iters random 8-byte loads of x[0, n) (device
+ * doubles, n a power of two, 32 <= n <= 2^32), indices from a per-thread
+ * xorshift generator, four loads in flight per thread; writes nothing (sink,
+ * one device double, is written only if the loads sum to exactly -1234567).
+ * Not part of the method: with x resident in L2 it measures how many
+ * scattered x gathers per second the SMs can issue, the ceiling of an SpMV
+ * whose columns have no locality.  RGCSR_ERR_INVALID_ARG for a bad n or
+ * iters < 1. */
+int rgcsr_gather_probe(const void *x, int64_t n, int32_t iters, void *sink, int64_t *loads,
+                       rgcsr_stream_t stream);
 /* Runs *fmas (host int64, written before the launch) = SMs x 2048 threads x
  * 8 independent chains x iters double-precision FMAs, and writes nothing
  * (sink, one device double, is written only if the chains end at exactly

@@ -25,7 +25,9 @@ F64, F32, BF16, F16, I32T, I64T = 0, 1, 2, 3, 4, 5
 
 KERNEL_AUTO, KERNEL_PAPER, KERNEL_SPLIT, KERNEL_TMA, KERNEL_LEAN, KERNEL_SELL = 0, 1, 2, 3, 4, 5
 STATUS_TIMEOUT = 1
-XLOAD_NC, XLOAD_PLAIN = 0, 1
+XLOAD_NC, XLOAD_PLAIN, XLOAD_TEX = 0, 1, 2
+XWINDOW_ROWS, XWINDOW_MAX_RANGES, XWINDOW_GAP, XWINDOW_CAP_BYTES = 256, 4, 64, 32768
+VALUES_STATE_BYTES = 8192
 
 
 class CSR(ctypes.Structure):
@@ -44,7 +46,7 @@ class Matrix(ctypes.Structure):
 
 class Launch(ctypes.Structure):
     _fields_ = [("kernel", I32), ("block_threads", I32), ("x_load", I32), ("split_weight", I32),
-                ("variant", I32)]
+                ("variant", I32), ("wait_limit", I32)]
 
 
 class Hyb(ctypes.Structure):
@@ -63,6 +65,10 @@ class Tiles(ctypes.Structure):
     _fields_ = [("tile", I32), ("variant", I32), ("n_groups", I64), ("n_extra", I64), ("n_split", I64),
                 ("n_partials", I64), ("first_extra", P), ("part_base", P), ("extra_group", P),
                 ("arrivals", P), ("partials", P)]
+
+
+class XWindow(ctypes.Structure):
+    _fields_ = [("n_ranges", I32), ("total", I32), ("lo", I32 * 4), ("len", I32 * 4)]
 
 
 class BatchDesc(ctypes.Structure):
@@ -98,6 +104,9 @@ SIGNATURES = {
     "rgcsr_tiles_build": (ctypes.c_int, [_PM, ctypes.POINTER(Tiles), P]),
     "rgcsr_spmv_tiles": (ctypes.c_int, [_PM, ctypes.POINTER(Tiles), P, P, P]),
     "rgcsr_quantize": (ctypes.c_int, [_PM, _PM, P]),
+    "rgcsr_xwindow_count": (I64, [I64]),
+    "rgcsr_xwindow_plan": (ctypes.c_int, [_PM, P, P]),
+    "rgcsr_spmv_xwindow": (ctypes.c_int, [_PM, P, P, P, P]),
     "rgcsr_long_rows_workspace_bytes": (SZ, [I64]),
     "rgcsr_long_rows_plan": (ctypes.c_int, [_PM, ctypes.POINTER(LongRows), P, SZ, P]),
     "rgcsr_long_rows_build": (ctypes.c_int, [_PM, ctypes.POINTER(LongRows), P, SZ, P]),
@@ -109,6 +118,7 @@ SIGNATURES = {
     "rgcsr_csr_transpose": (ctypes.c_int, [_PCSR, P, P, P, P, P, SZ, P]),
     "rgcsr_csr_row_index": (ctypes.c_int, [_PCSR, P, P]),
     "rgcsr_gather_values": (ctypes.c_int, [_PM, P, P, P]),
+    "rgcsr_gather_values_if_changed": (ctypes.c_int, [_PM, P, I64, P, P, P]),
     "rgcsr_compose_index": (ctypes.c_int, [P, P, I64, P, P]),
     "rgcsr_sampled_dot": (ctypes.c_int, [I64, I32, P, P, P, I64, P, I64, P, I32, P]),
     "rgcsr_spmv_bwd_values": (ctypes.c_int, [_PM, I32, P, I64, P, I64, P, P]),
@@ -122,6 +132,7 @@ SIGNATURES = {
     "rgcsr_convert_vector": (ctypes.c_int, [I64, P, I32, P, I32, P]),
     "rgcsr_stream_read": (ctypes.c_int, [P, I64, P, P]),
     "rgcsr_fp64_fma_probe": (ctypes.c_int, [I32, P, ctypes.POINTER(I64), P]),
+    "rgcsr_gather_probe": (ctypes.c_int, [P, I64, I32, P, ctypes.POINTER(I64), P]),
     "rgcsr_cg_workspace_bytes": (SZ, [I64, I32]),
     "rgcsr_cg": (ctypes.c_int, [_PM, P, P, D, I32, I32, P, SZ, PI32, PD, P]),
     "rgcsr_ir_cg_workspace_bytes": (SZ, [I64]),

@@ -3,7 +3,10 @@
 ``SparseOperator`` keeps, on the GPU, the RgCSR matrix of A, the RgCSR matrix
 of A^T (built once from a stable CSR transposition) and the maps from their
 slots to the CSR-ordered value array, so values that change between calls
-(trainable weights) are refreshed with two gather kernels.
+(trainable weights) are refreshed with a gather kernel: into A when a
+forward product sees new values, into A^T when a backward product needs
+them; values the matrix already holds (same content, checked on the
+device by a hash) are not gathered again.
 
 ``spmm(op, values, X)`` computes A X (X a vector or an [n_cols, k] block) and
 is differentiable with respect to both the values and X:
@@ -56,6 +59,9 @@ class SparseOperator:
         self.at_src = torch.empty(self.AT.n_stored, dtype=torch.int64, device=device)
         L.call("rgcsr_compose_index", _ptr(self.AT.slot_to_csr), _ptr(perm), self.AT.n_stored,
                _ptr(self.at_src), st)
+        # what values A and A^T hold (device records: zero = nothing yet)
+        self._a_state = torch.zeros(L.VALUES_STATE_BYTES // 8, dtype=torch.int64, device=device)
+        self._at_state = torch.zeros(L.VALUES_STATE_BYTES // 8, dtype=torch.int64, device=device)
         self.row_index = torch.empty(self.nnz, dtype=torch.int32, device=device)
         L.call("rgcsr_csr_row_index", ctypes.byref(csr), _ptr(self.row_index), st)
         if long_rows is not None:
@@ -65,13 +71,27 @@ class SparseOperator:
             self.A.tile_groups(tiles)
             self.AT.tile_groups(tiles)
 
-    def set_values(self, values: torch.Tensor) -> None:
-        """Loads CSR-ordered values into the RgCSR matrices of A and A^T."""
+    def load_values(self, values: torch.Tensor, transposed: bool = False, force: bool = False) -> None:
+        """Loads CSR-ordered values into the RgCSR matrix of A (or of A^T)
+        unless that matrix already holds them: the library hashes the values
+        on the device and gathers only when the hash differs from the one it
+        recorded for the matrix (rgcsr_gather_values_if_changed), so a
+        change made any way -- in place, through ``.data``, by another
+        kernel -- is seen, and unchanged values cost one read instead of a
+        gather.  force=True forgets the record first."""
         if values.dtype != self.dtype or values.numel() != self.nnz or not values.is_contiguous():
             raise ValueError(f"values must be a contiguous {self.dtype} vector of length {self.nnz}")
-        st = _stream_ptr()
-        L.call("rgcsr_gather_values", ctypes.byref(self.A.s), _ptr(values), _ptr(self.A.slot_to_csr), st)
-        L.call("rgcsr_gather_values", ctypes.byref(self.AT.s), _ptr(values), _ptr(self.at_src), st)
+        M, src, state = (self.AT, self.at_src, self._at_state) if transposed else \
+            (self.A, self.A.slot_to_csr, self._a_state)
+        if force:
+            state.zero_()
+        L.call("rgcsr_gather_values_if_changed", ctypes.byref(M.s), _ptr(values), self.nnz, _ptr(src),
+               _ptr(state), _stream_ptr())
+
+    def set_values(self, values: torch.Tensor, force: bool = False) -> None:
+        """Loads CSR-ordered values into the RgCSR matrices of A and A^T."""
+        self.load_values(values, False, force)
+        self.load_values(values, True, force)
 
     def matmul(self, X: torch.Tensor) -> torch.Tensor:
         return self.A.spmv(X) if X.dim() == 1 else self.A.spmm(X)
@@ -96,7 +116,7 @@ class SparseOperator:
 class _SparseMatmul(torch.autograd.Function):
     @staticmethod
     def forward(ctx, values, X, op):
-        op.set_values(values)
+        op.load_values(values)                 # A only; A^T is loaded by the backward that needs it
         ctx.op = op
         ctx.save_for_backward(values, X)
         return op.matmul(X.contiguous())
@@ -109,7 +129,7 @@ class _SparseMatmul(torch.autograd.Function):
         d_values = op.sampled_dot(dY, X.contiguous()) if ctx.needs_input_grad[0] else None
         dX = None
         if ctx.needs_input_grad[1]:
-            op.set_values(values)          # the operator may have served other values since
+            op.load_values(values, transposed=True)    # skipped if A^T already holds them
             dX = op.matmul_t(dY)
         return d_values, dX, None
 

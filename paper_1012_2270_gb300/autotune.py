@@ -125,7 +125,7 @@ def candidates(rowptr, dtype: torch.dtype):
         cands += [dict(group_size=32, kernel=L.KERNEL_TMA, variant=v) for v in range(4)]
         cands += [dict(group_size=G, kernel=k) for G in (32, 64) for k in (L.KERNEL_LEAN, L.KERNEL_SPLIT)]
         if dtype in (torch.float32, torch.float64):
-            cands += [dict(group_size=32, kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4)]
+            cands += [dict(group_size=32, kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4, 5, 6, 7)]
     else:
         Gm = model_group_size(rowptr, dtype.itemsize)
         cands += [dict(group_size=G, kernel=L.KERNEL_SPLIT) for G in sorted({1, 2, 4, 8, Gm})]

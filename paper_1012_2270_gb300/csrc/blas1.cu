@@ -9,20 +9,6 @@ namespace {
 
 constexpr int kDotThreads = 256;
 
-template <typename T>
-__device__ __forceinline__ double block_sum(double v, double *sh) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    v = warp_sum(v);
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (w == 0) {
-        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
-        t = warp_sum(t);
-    }
-    __syncthreads();
-    return t;
-}
 
 // One thread's share of x . y over its grid-stride packs of W elements (in
 // element order within a pack), then the last n mod W elements.
@@ -41,24 +27,6 @@ __device__ __forceinline__ double dot_share(int64_t n, const double *__restrict_
     return s;
 }
 
-// Float vectors: the compensated dot product "Dot2" of Ogita, Rump and Oishi
-// (Accurate sum and dot product, SIAM J. Sci. Comput. 26, 2005) in float,
-// so that no FP64 instruction runs per element (GB300's FP64 pipe is
-// narrow).  Each product is split exactly into p + e (TwoProduct: a rounded
-// product and its FMA residual), the running sum s absorbs p with its exact
-// rounding error q (TwoSum), and c collects q + e.  A thread's s + c is as
-// accurate as a dot product in twice the working precision; it is widened to
-// double and the block sums it in double.  The _rn intrinsics keep the
-// compiler from contracting or reordering these steps.
-__device__ __forceinline__ void dot2_step(float a, float b, float &s, float &c) {
-    const float p = __fmul_rn(a, b);
-    const float e = fmaf(a, b, -p);                            // a b = p + e exactly
-    const float t = __fadd_rn(s, p);
-    const float z = __fsub_rn(t, s);
-    const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));   // s + p = t + q exactly
-    s = t;
-    c = __fadd_rn(c, __fadd_rn(q, e));
-}
 
 template <int W>
 __device__ __forceinline__ double dot_share(int64_t n, const float *__restrict__ x, const float *__restrict__ y) {
@@ -78,7 +46,7 @@ template <typename T, int W>
 __global__ void __launch_bounds__(kDotThreads)
 dot_partial(int64_t n, const T *__restrict__ x, const T *__restrict__ y, double *__restrict__ part) {
     __shared__ double sh[32];
-    const double t = block_sum<double>(dot_share<W>(n, x, y), sh);
+    const double t = block_sum(dot_share<W>(n, x, y), sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -91,7 +59,7 @@ dot_onepass(int64_t n, const T *__restrict__ x, const T *__restrict__ y, double 
             unsigned *__restrict__ count, double *__restrict__ out) {
     __shared__ double sh[32];
     __shared__ bool last;
-    const double t = block_sum<double>(dot_share<W>(n, x, y), sh);
+    const double t = block_sum(dot_share<W>(n, x, y), sh);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = t;
         __threadfence();
@@ -102,7 +70,7 @@ dot_onepass(int64_t n, const T *__restrict__ x, const T *__restrict__ y, double 
     __threadfence();
     double s = 0.0;
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(part + i);
-    const double total = block_sum<double>(s, sh);
+    const double total = block_sum(s, sh);
     if (threadIdx.x == 0) {
         *out = total;
         *count = 0u;
@@ -114,7 +82,7 @@ dot_final(int nparts, const double *__restrict__ part, double *__restrict__ out)
     __shared__ double sh[32];
     double s = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
-    const double t = block_sum<double>(s, sh);
+    const double t = block_sum(s, sh);
     if (threadIdx.x == 0) *out = t;
 }
 
@@ -215,6 +183,23 @@ fp64_fma_kernel(int32_t iters, double m, double c, double *__restrict__ sink) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) s += a[k];
     if (s == -1234567.0) *sink = s;
+}
+
+// Random 8-byte loads of x[0, n) (n a power of two): each thread draws
+// indices with a xorshift generator (Marsaglia 2003) and keeps four loads
+// in flight per step; nothing is written unless the sum is exactly
+// -1234567.  The gather pattern of an SpMV with random columns, without the
+// matrix: its rate is the ceiling such an SpMV's x gathers can reach.
+__global__ void __launch_bounds__(256)
+gather_probe_kernel(const double *__restrict__ x, uint32_t mask, int32_t iters, double *__restrict__ sink) {
+    uint32_t s = 0x9E3779B9u ^ ((uint32_t)(blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u);
+    auto next = [&s]() { s ^= s << 13; s ^= s >> 17; s ^= s << 5; return s; };
+    double acc = 0.0;
+    for (int32_t i = 0; i < iters; ++i) {
+        const uint32_t a = next() & mask, b = next() & mask, c = next() & mask, d = next() & mask;
+        acc += __ldg(x + a) + __ldg(x + b) + __ldg(x + c) + __ldg(x + d);
+    }
+    if (acc == -1234567.0) *sink = acc;
 }
 
 }  // namespace
@@ -363,6 +348,20 @@ RGCSR_API int rgcsr_stream_read(const void *data, int64_t bytes, void *sink, rgc
     if (ceil_div(n16, (int64_t)256) < grid) grid = ceil_div(n16, (int64_t)256);
     stream_read_kernel<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(static_cast<const float4 *>(data), n16,
                                                                          static_cast<float *>(sink));
+    return launch_status();
+}
+
+RGCSR_API int rgcsr_gather_probe(const void *x, int64_t n, int32_t iters, void *sink, int64_t *loads,
+                                 rgcsr_stream_t stream) {
+    if (!x || !sink || !loads || iters < 1 || n < 32 || n > ((int64_t)1 << 32) || (n & (n - 1)) != 0)
+        return RGCSR_ERR_INVALID_ARG;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = sms * 4;                            // 4 CTAs of 256 threads per SM
+    *loads = (int64_t)grid * 256 * 4 * iters;
+    gather_probe_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(static_cast<const double *>(x),
+                                                                (uint32_t)(n - 1), iters,
+                                                                static_cast<double *>(sink));
     return launch_status();
 }
 

@@ -185,6 +185,44 @@ int launch_row_lengths(const rgcsr_csr *A, const int32_t *perm, int32_t *row_len
 // sets bit 4 of *flags unless perm is a permutation of [0, n); seen: n ints of scratch
 int launch_check_perm(const int32_t *perm, int64_t n, int32_t *seen, int *flags, cudaStream_t s);
 
+// Sum of v over the block (blockDim.x a multiple of 32, <= 1024); sh: 32
+// doubles of shared memory.  Every thread returns the total.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        t = warp_sum(t);
+        if (lane == 0) sh[0] = t;
+    }
+    __syncthreads();
+    t = sh[0];
+    __syncthreads();
+    return t;
+}
+
+// Float vectors: the compensated dot product "Dot2" of Ogita, Rump and Oishi
+// (Accurate sum and dot product, SIAM J. Sci. Comput. 26, 2005) in float,
+// so that no FP64 instruction runs per element (GB300's FP64 pipe is
+// narrow).  Each product is split exactly into p + e (TwoProduct: a rounded
+// product and its FMA residual), the running sum s absorbs p with its exact
+// rounding error q (TwoSum), and c collects q + e.  A thread's s + c is as
+// accurate as a dot product in twice the working precision; it is widened to
+// double and the block sums it in double.  The _rn intrinsics keep the
+// compiler from contracting or reordering these steps.
+__device__ __forceinline__ void dot2_step(float a, float b, float &s, float &c) {
+    const float p = __fmul_rn(a, b);
+    const float e = fmaf(a, b, -p);                            // a b = p + e exactly
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));   // s + p = t + q exactly
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(q, e));
+}
+
 // Vector kernels (blas1.cu).  dot_device writes the dot product of x and y
 // (deterministic; double vectors in double, float vectors by a compensated
 // float dot per thread summed in double) to the device scalar *out, using
@@ -199,6 +237,10 @@ int convert_device(int64_t n, const void *src, int src_type, void *dst, int dst_
 
 // TMA-staged SpMV for G = 32 (spmv_tma.cu).
 bool tma_eligible(const rgcsr_matrix *M);
-int launch_spmv_tma(const rgcsr_matrix *M, const void *x, void *y, int variant, cudaStream_t s);
+// A texture object over x[0, n) (elements of elem_bytes = 4 or 8 bytes),
+// created on first use and cached per device and buffer (xpath.cu).
+int x_texture(const void *x, int64_t n, int elem_bytes, cudaTextureObject_t *out);
+int launch_spmv_tma(const rgcsr_matrix *M, const void *x, void *y, int variant, uint32_t wait_limit,
+                    cudaStream_t s);
 
 }  // namespace rgcsr

@@ -33,17 +33,29 @@ namespace {
 constexpr int kDefaultThreads = 256;
 constexpr int kUnroll = 8;          // slots in flight per thread
 
-template <typename A, bool NC>
-__device__ __forceinline__ A gather(const A *x, int c) {
-    if constexpr (NC) return __ldg(x + c);
-    else return x[c];
+// x[c] through the chosen read path XL: the read-only (non-coherent) path
+// (RGCSR_XLOAD_NC), an ordinary load (RGCSR_XLOAD_PLAIN), or a texture fetch
+// from a texture object bound to x (RGCSR_XLOAD_TEX) -- the read paths of
+// the paper's texture study (Sec. 4.3) on this architecture.
+template <typename A, int XL>
+__device__ __forceinline__ A gather(const A *x, cudaTextureObject_t tex, int c) {
+    if constexpr (XL == RGCSR_XLOAD_NC) {
+        return __ldg(x + c);
+    } else if constexpr (XL == RGCSR_XLOAD_PLAIN) {
+        return x[c];
+    } else if constexpr (sizeof(A) == 8) {
+        const int2 v = tex1Dfetch<int2>(tex, c);
+        return __hiloint2double(v.y, v.x);
+    } else {
+        return tex1Dfetch<float>(tex, c);
+    }
 }
 
-template <typename T, bool NC>
+template <typename T, int XL>
 __global__ void rgcsr_spmv_paper(int64_t n, int32_t G, const T *__restrict__ val,
                                  const int32_t *__restrict__ col, const int64_t *__restrict__ gp,
                                  const int32_t *__restrict__ rl, const T *__restrict__ x,
-                                 T *__restrict__ y, const int32_t *__restrict__ perm) {
+                                 T *__restrict__ y, const int32_t *__restrict__ perm, cudaTextureObject_t tex) {
     const int64_t g = blockIdx.x;
     const int64_t row = g * G + threadIdx.x;
     if (row >= n) return;
@@ -52,18 +64,19 @@ __global__ void rgcsr_spmv_paper(int64_t n, int32_t G, const T *__restrict__ val
     const int len = rl[row];
     T acc = 0;
     for (int j = 0; j < len; ++j) {
-        acc += val[ptr] * gather<T, NC>(x, col[ptr]);
+        acc += val[ptr] * gather<T, XL>(x, tex, col[ptr]);
         ptr += R;
     }
     y[out_row(perm, row)] = acc;
 }
 
-template <typename V, bool NC>
+template <typename V, int XL>
 __global__ void __launch_bounds__(kDefaultThreads)
 rgcsr_spmv_split(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *__restrict__ col,
                  const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
                  const float *__restrict__ scale, const typename VT<V>::A *__restrict__ x,
-                 typename VT<V>::A *__restrict__ y, const int32_t *__restrict__ perm, int w4, int cap) {
+                 typename VT<V>::A *__restrict__ y, const int32_t *__restrict__ perm, int w4, int cap,
+                 cudaTextureObject_t tex) {
     using A = typename VT<V>::A;
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -98,7 +111,7 @@ rgcsr_spmv_split(int64_t n, int32_t G, const V *__restrict__ val, const int32_t 
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u)
-            if (j + u < jend) acc = fma(v[u], gather<A, NC>(x, c[u]), acc);
+            if (j + u < jend) acc = fma(v[u], gather<A, XL>(x, tex, c[u]), acc);
     }
 
     // Phase 2: the whole warp finishes each row longer than j0.
@@ -124,7 +137,7 @@ rgcsr_spmv_split(int64_t n, int32_t G, const V *__restrict__ val, const int32_t 
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u)
-                if (j + 32 * u < Lr) part = fma(v[u], gather<A, NC>(x, c[u]), part);
+                if (j + 32 * u < Lr) part = fma(v[u], gather<A, XL>(x, tex, c[u]), part);
         }
         part = warp_sum(part);
         if (lane == r) acc += part;
@@ -136,12 +149,12 @@ rgcsr_spmv_split(int64_t n, int32_t G, const V *__restrict__ val, const int32_t 
 // (FP32: <= 32 registers, 64 warps per SM; FP64: 48 warps per SM) so that
 // enough loads stay in flight.  For matrices whose rows within a warp have
 // similar lengths.
-template <typename V, int U, int MIN_BLOCKS>
+template <typename V, int U, int MIN_BLOCKS, int XL>
 __global__ void __launch_bounds__(kDefaultThreads, MIN_BLOCKS)
 rgcsr_spmv_lean(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *__restrict__ col,
                 const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
                 const float *__restrict__ scale, const typename VT<V>::A *__restrict__ x,
-                typename VT<V>::A *__restrict__ y, const int32_t *__restrict__ perm) {
+                typename VT<V>::A *__restrict__ y, const int32_t *__restrict__ perm, cudaTextureObject_t tex) {
     using A = typename VT<V>::A;
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= n) return;
@@ -165,7 +178,7 @@ rgcsr_spmv_lean(int64_t n, int32_t G, const V *__restrict__ val, const int32_t *
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (j + u < len) acc = fma(v[u], __ldg(x + c[u]), acc);
+            if (j + u < len) acc = fma(v[u], gather<A, XL>(x, tex, c[u]), acc);
         vp += (int64_t)U * stride;
         cp += (int64_t)U * stride;
     }
@@ -255,6 +268,116 @@ rgcsr_spmv_vec(int64_t n, const V *__restrict__ val, const int32_t *__restrict__
         if (t0 + r < R) y[out_row(perm, first + t0 + r)] = finish<V>(acc[r], scale, first + t0 + r);
 }
 
+// The same mapping software-pipelined, with every value load 16 bytes wide:
+// a lane owns RPL = 16 / sizeof(V) consecutive rows of a group (FP64 2,
+// FP32 4, BF16/FP16 8) and keeps two stages of U slot-rows in registers.
+// The loads of the next stage (values, and RPL columns in 8- or 16-byte
+// pieces) are issued before the x gathers of the current one, so every
+// warp has streamed bytes in flight while it gathers; without that, the
+// dependent load -> gather -> FMA chain of each step leaves the memory
+// system idle between steps and the kernel's time stops falling with its
+// bytes (reduced storage then runs no faster than FP32).
+template <typename V, int RPL>
+struct VecStage {
+    using R = typename RawVec<RPL * sizeof(V)>::T;
+    R v;
+    int c[RPL];
+    __device__ __forceinline__ void load(const V *p, const int32_t *q) {
+        v = __ldcs(reinterpret_cast<const R *>(p));
+        if constexpr (RPL == 2) {
+            const int2 a = __ldcs(reinterpret_cast<const int2 *>(q));
+            c[0] = a.x; c[1] = a.y;
+        } else {
+#pragma unroll
+            for (int h = 0; h < RPL / 4; ++h) {
+                const int4 a = __ldcs(reinterpret_cast<const int4 *>(q) + h);
+                c[4 * h] = a.x; c[4 * h + 1] = a.y; c[4 * h + 2] = a.z; c[4 * h + 3] = a.w;
+            }
+        }
+    }
+    // 32-bit word i of the 16 bytes (i known at compile time after unrolling)
+    __device__ __forceinline__ uint32_t word(int i) const {
+        return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+    }
+    __device__ __forceinline__ typename VT<V>::A value(int r) const {
+        if constexpr (sizeof(V) == 8) {
+            return __hiloint2double((int)word(2 * r + 1), (int)word(2 * r));
+        } else if constexpr (sizeof(V) == 4) {
+            return __uint_as_float(word(r));
+        } else {
+            const unsigned short h = (unsigned short)(word(r >> 1) >> (16 * (r & 1)));
+            if constexpr (std::is_same<V, __nv_bfloat16>::value) return __bfloat162float(__ushort_as_bfloat16(h));
+            else return __half2float(__ushort_as_half(h));
+        }
+    }
+};
+
+template <typename V, int U, int MIN_BLOCKS>
+__global__ void __launch_bounds__(kDefaultThreads, MIN_BLOCKS)
+rgcsr_spmv_vecp(int64_t n, const V *__restrict__ val, const int32_t *__restrict__ col,
+                const int64_t *__restrict__ gp, const int32_t *__restrict__ rl, const float *__restrict__ scale,
+                const typename VT<V>::A *__restrict__ x, typename VT<V>::A *__restrict__ y,
+                const int32_t *__restrict__ perm) {
+    using A = typename VT<V>::A;
+    constexpr int RPL = 16 / (int)sizeof(V);
+    constexpr int LPG = 32 / RPL;                                   // lanes per group
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = tid / LPG;
+    const int t0 = (int)(tid % LPG) * RPL;                          // first row within the group
+    const int64_t first = g * 32;
+    if (first >= n) return;
+    const int R = (int)min((int64_t)32, n - first);
+    const int64_t base = __ldg(gp + g);
+    int len[RPL];
+    int lmax = 0;
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        len[r] = (t0 + r < R) ? __ldg(rl + first + t0 + r) : 0;
+        lmax = max(lmax, len[r]);
+    }
+    A acc[RPL];
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) acc[r] = 0;
+    if (R == 32) {
+        const V *vp = val + base + t0;
+        const int32_t *cp = col + base + t0;
+        VecStage<V, RPL> cur[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (u < lmax) cur[u].load(vp + u * 32, cp + u * 32);
+        for (int j = 0; j < lmax; j += U) {
+            VecStage<V, RPL> nxt[U];
+            const int jn = j + U;
+#pragma unroll
+            for (int u = 0; u < U; ++u)                             // next stage first
+                if (jn + u < lmax) nxt[u].load(vp + (int64_t)(jn + u) * 32, cp + (int64_t)(jn + u) * 32);
+            A xv[U][RPL];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int r = 0; r < RPL; ++r)
+                    if (j + u < len[r]) xv[u][r] = __ldg(x + cur[u].c[r]);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int r = 0; r < RPL; ++r)
+                    if (j + u < len[r]) acc[r] = fma(cur[u].value(r), xv[u][r], acc[r]);
+#pragma unroll
+            for (int u = 0; u < U; ++u) cur[u] = nxt[u];
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < RPL; ++r)
+            for (int j = 0; j < len[r]; ++j) {
+                const int64_t p = base + (int64_t)j * R + t0 + r;
+                acc[r] = fma(VT<V>::ld(val + p), __ldg(x + __ldcs(col + p)), acc[r]);
+            }
+    }
+#pragma unroll
+    for (int r = 0; r < RPL; ++r)
+        if (t0 + r < R) y[out_row(perm, first + t0 + r)] = finish<V>(acc[r], scale, first + t0 + r);
+}
+
 // Sliced ELLPACK on the same slabs (the related format discussed in
 // Sec. 3.4): one thread per row, but every row of group g runs all
 // K_g = (gp[g+1] - gp[g]) / R_g slots -- no rowLengths -- so the padding is
@@ -300,12 +423,42 @@ template <typename V>
 int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V>::A *y,
                 const rgcsr_launch *L, cudaStream_t s) {
     const int kernel = L ? L->kernel : RGCSR_KERNEL_AUTO;
-    const bool nc = !L || L->x_load == RGCSR_XLOAD_NC;
+    const int xl = L ? L->x_load : RGCSR_XLOAD_NC;
+    if (xl != RGCSR_XLOAD_NC && xl != RGCSR_XLOAD_PLAIN && xl != RGCSR_XLOAD_TEX) return RGCSR_ERR_INVALID_ARG;
+    if (xl != RGCSR_XLOAD_NC && kernel != RGCSR_KERNEL_PAPER && kernel != RGCSR_KERNEL_SPLIT &&
+        !(kernel == RGCSR_KERNEL_LEAN && (!L || L->variant == 0)))
+        return RGCSR_ERR_INVALID_ARG;          // the other kernels read x through the read-only path only
+    cudaTextureObject_t tex = 0;
+    if (xl == RGCSR_XLOAD_TEX && M->n_cols > 0) {
+        const int st = x_texture(x, M->n_cols, (int)sizeof(typename VT<V>::A), &tex);
+        if (st != RGCSR_OK) return st;
+    }
     const V *val = static_cast<const V *>(M->values);
     const int64_t n = M->n_rows;
     const int32_t G = M->group_size;
     const float *scale = M->row_scale;
     if (VT<V>::scaled && !scale) return RGCSR_ERR_INVALID_ARG;
+    if (kernel == RGCSR_KERNEL_LEAN && L && L->variant >= 5 && L->variant <= 7) {
+        auto aligned = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+        if (G != 32 || !aligned(val) || !aligned(M->columns)) return RGCSR_ERR_INVALID_ARG;
+        // variants 5, 6, 7: software-pipelined, 16-byte value loads, U = 2, 1, 4
+        constexpr int lpg = 32 / (16 / (int)sizeof(V));
+        const int64_t blocks = ceil_div(M->n_groups * lpg, (int64_t)kDefaultThreads);
+        if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
+        // resident blocks per SM: as many as the registers allow without
+        // spills (8 rows per lane for 2-byte values need more registers)
+        constexpr bool two = sizeof(V) == 2;
+        if (L->variant == 5)
+            rgcsr_spmv_vecp<V, 2, two ? 2 : 3><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
+                n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
+        else if (L->variant == 6)
+            rgcsr_spmv_vecp<V, 1, two ? 3 : 4><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
+                n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
+        else
+            rgcsr_spmv_vecp<V, 4, 2><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
+                n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
+        return launch_status();
+    }
     if (kernel == RGCSR_KERNEL_LEAN && L && (L->variant == 1 || L->variant == 2 || L->variant == 4)) {
         auto aligned = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
         if (G != 32 || !aligned(val) || !aligned(M->columns)) return RGCSR_ERR_INVALID_ARG;
@@ -333,8 +486,13 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
         if (L && L->variant != 0) return RGCSR_ERR_INVALID_ARG;
         // 8 blocks (32 registers) fit plain FP32; FP64 and scaled storage need 6
         constexpr int min_blocks = (std::is_same<V, float>::value) ? 8 : 6;
-        rgcsr_spmv_lean<V, 4, min_blocks><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
-            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
+#define RGCSR_LEAN(XL_)                                                                             \
+    rgcsr_spmv_lean<V, 4, min_blocks, XL_><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(             \
+        n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm, tex)
+        if (xl == RGCSR_XLOAD_NC) RGCSR_LEAN(RGCSR_XLOAD_NC);
+        else if (xl == RGCSR_XLOAD_PLAIN) RGCSR_LEAN(RGCSR_XLOAD_PLAIN);
+        else RGCSR_LEAN(RGCSR_XLOAD_TEX);
+#undef RGCSR_LEAN
         return launch_status();
     }
     if (kernel == RGCSR_KERNEL_SELL) {
@@ -350,12 +508,13 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
             return RGCSR_ERR_UNSUPPORTED_DTYPE;
         } else {
             if (G > 1024) return RGCSR_ERR_INVALID_ARG;
-            if (nc)
-                rgcsr_spmv_paper<V, true><<<(unsigned)M->n_groups, G, 0, s>>>(
-                    n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y, M->row_perm);
-            else
-                rgcsr_spmv_paper<V, false><<<(unsigned)M->n_groups, G, 0, s>>>(
-                    n, G, val, M->columns, M->group_ptr, M->row_lengths, x, y, M->row_perm);
+#define RGCSR_PAPER(XL_)                                                                            \
+    rgcsr_spmv_paper<V, XL_><<<(unsigned)M->n_groups, G, 0, s>>>(n, G, val, M->columns, M->group_ptr, \
+                                                              M->row_lengths, x, y, M->row_perm, tex)
+            if (xl == RGCSR_XLOAD_NC) RGCSR_PAPER(RGCSR_XLOAD_NC);
+            else if (xl == RGCSR_XLOAD_PLAIN) RGCSR_PAPER(RGCSR_XLOAD_PLAIN);
+            else RGCSR_PAPER(RGCSR_XLOAD_TEX);
+#undef RGCSR_PAPER
             return launch_status();
         }
     }
@@ -365,12 +524,13 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
     const int w4 = (L && L->split_weight > 0) ? L->split_weight : 8;
     const int64_t blocks = ceil_div(n, threads);
     if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
-    if (nc)
-        rgcsr_spmv_split<V, true><<<(unsigned)blocks, threads, 0, s>>>(
-            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm, w4, INT_MAX);
-    else
-        rgcsr_spmv_split<V, false><<<(unsigned)blocks, threads, 0, s>>>(
-            n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm, w4, INT_MAX);
+#define RGCSR_SPLIT(XL_)                                                                            \
+    rgcsr_spmv_split<V, XL_><<<(unsigned)blocks, threads, 0, s>>>(                                   \
+        n, G, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm, w4, INT_MAX, tex)
+    if (xl == RGCSR_XLOAD_NC) RGCSR_SPLIT(RGCSR_XLOAD_NC);
+    else if (xl == RGCSR_XLOAD_PLAIN) RGCSR_SPLIT(RGCSR_XLOAD_PLAIN);
+    else RGCSR_SPLIT(RGCSR_XLOAD_TEX);
+#undef RGCSR_SPLIT
     return launch_status();
 }
 
@@ -488,9 +648,9 @@ int launch_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *S, const type
     if (VT<V>::scaled && !scale) return RGCSR_ERR_INVALID_ARG;
     const int64_t blocks = ceil_div(n, kDefaultThreads);
     if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
-    rgcsr_spmv_split<V, true><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
+    rgcsr_spmv_split<V, RGCSR_XLOAD_NC><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
         n, M->group_size, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm, 8,
-        S->threshold);
+        S->threshold, 0);
     if (S->n_segments == 0) return launch_status();
     int64_t sb = ceil_div(S->n_segments, kDefaultThreads / 32);
     if (sb > 152 * 16) sb = 152 * 16;
@@ -524,6 +684,13 @@ RGCSR_API int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
     cudaStream_t s = (cudaStream_t)stream;
     int kernel = launch ? launch->kernel : RGCSR_KERNEL_AUTO;
     int variant = launch ? launch->variant : 0;
+    // x read paths other than the read-only one are an ablation of the
+    // paper's, scalar, x gathers: they need an explicit PAPER, SPLIT or LEAN
+    // (variant 0) kernel
+    if (launch && launch->x_load != RGCSR_XLOAD_NC &&
+        !(kernel == RGCSR_KERNEL_PAPER || kernel == RGCSR_KERNEL_SPLIT ||
+          (kernel == RGCSR_KERNEL_LEAN && variant == 0)))
+        return RGCSR_ERR_INVALID_ARG;
     if (kernel == RGCSR_KERNEL_AUTO) {
         // Dense groups (padding <= 25% of the stored slots), as timed on
         // GB300: short rows (<= 8 per row) at G = 32 take the vector-load
@@ -551,7 +718,8 @@ RGCSR_API int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
     }
     if (kernel == RGCSR_KERNEL_TMA) {
         if (!tma_eligible(M)) return RGCSR_ERR_INVALID_ARG;
-        return launch_spmv_tma(M, x, y, variant, s);
+        if (launch && launch->wait_limit < 0) return RGCSR_ERR_INVALID_ARG;
+        return launch_spmv_tma(M, x, y, variant, launch ? (uint32_t)launch->wait_limit : 0u, s);
     }
     rgcsr_launch resolved = launch ? *launch : rgcsr_launch{};
     resolved.kernel = kernel;

@@ -95,21 +95,24 @@ struct SlabRing {
         ++issued;
         return true;
     }
-    // Bounded wait for chunk k (its stage's (k / STAGES)-th completion: the
-    // warp never waits more than one phase ahead, since it consumes its own
-    // chunks in order); false after a timeout, with the error recorded and
-    // the warp's remaining copies drained with the same bound.
-    __device__ bool wait(int k) {
+    // Probes chunk k's stage (its (k / STAGES)-th completion: the warp never
+    // waits more than one phase ahead, since it consumes its own chunks in
+    // order) at most `limit` times; the whole warp takes the same decision.
+    __device__ bool probe(int k, uint32_t limit) const {
         const int s = k % STAGES;
         const uint32_t parity = (uint32_t)(k / STAGES) & 1u;
-        for (uint32_t t = 0; t < kSpinLimit; ++t)
-            if (ptx::mbar_test_wait(&bars[s], parity)) return true;
+        for (uint32_t t = 0; t < limit; ++t)
+            if (__all_sync(0xffffffffu, ptx::mbar_test_wait(&bars[s], parity))) return true;
+        return false;
+    }
+    // Bounded wait for chunk k; false after `limit` probes, with the error
+    // recorded and every copy of this warp still in flight -- chunk k's own
+    // and the ones issued after it -- waited for (default bound) before the
+    // warp ends, so none lands in shared memory after the warp has gone.
+    __device__ bool wait(int k, uint32_t limit) {
+        if (probe(k, limit)) return true;
         if (lane == 0) atomicOr(&g_spmv_status, RGCSR_STATUS_TIMEOUT);
-        for (int k2 = k + 1; k2 < issued; ++k2) {
-            const int s2 = k2 % STAGES;
-            const uint32_t p2 = (uint32_t)(k2 / STAGES) & 1u;
-            for (uint32_t t = 0; t < kSpinLimit && !ptx::mbar_test_wait(&bars[s2], p2); ++t) {}
-        }
+        for (int k2 = k; k2 < issued; ++k2) (void)probe(k2, kSpinLimit);
         return false;
     }
     __device__ const unsigned char *stage(int k) const { return ring + (size_t)(k % STAGES) * C::STAGE_BYTES; }
@@ -142,7 +145,8 @@ template <typename T, int CAP, int STAGES>
 __global__ void __launch_bounds__(kTmaWarps * 32)
 rgcsr_spmv_tma(int64_t n, int64_t nb_full, const T *__restrict__ val, const int32_t *__restrict__ col,
                const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
-               const T *__restrict__ x, T *__restrict__ y, const int32_t *__restrict__ perm) {
+               const T *__restrict__ x, T *__restrict__ y, const int32_t *__restrict__ perm,
+               uint32_t wait_limit) {
     using C = TmaCfg<T, CAP, STAGES>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[kTmaWarps][STAGES];
@@ -172,7 +176,7 @@ rgcsr_spmv_tma(int64_t n, int64_t nb_full, const T *__restrict__ val, const int3
 
     T acc = 0;
     for (int it = 0; it < R.issued; ++it) {
-        if (!R.wait(it)) return;
+        if (!R.wait(it, wait_limit)) return;
         __syncwarp();
         const int4 m = R.meta[it % STAGES];
         const unsigned char *st = R.stage(it);
@@ -213,7 +217,7 @@ int sm_count() {
 }
 
 template <typename T, int CAP, int STAGES>
-int launch_tma_cfg(const rgcsr_matrix *M, const T *x, T *y, cudaStream_t s) {
+int launch_tma_cfg(const rgcsr_matrix *M, const T *x, T *y, uint32_t wait_limit, cudaStream_t s) {
     using C = TmaCfg<T, CAP, STAGES>;
     auto kern = rgcsr_spmv_tma<T, CAP, STAGES>;
     static std::once_flag once[64];
@@ -236,18 +240,18 @@ int launch_tma_cfg(const rgcsr_matrix *M, const T *x, T *y, cudaStream_t s) {
     if (need < grid) grid = need > 0 ? need : 1;
     kern<<<(unsigned)grid, kTmaWarps * 32, C::SMEM, s>>>(
         M->n_rows, nb_full, static_cast<const T *>(M->values), M->columns, M->group_ptr,
-        M->row_lengths, x, y, M->row_perm);
+        M->row_lengths, x, y, M->row_perm, wait_limit ? wait_limit : kSpinLimit);
     return launch_status();
 }
 
 // Ring configurations (slot-rows per chunk, stages), selectable for tuning.
 template <typename T>
-int launch_tma_t(const rgcsr_matrix *M, const T *x, T *y, int variant, cudaStream_t s) {
+int launch_tma_t(const rgcsr_matrix *M, const T *x, T *y, int variant, uint32_t wl, cudaStream_t s) {
     switch (variant) {
-        case 0: return launch_tma_cfg<T, 8, 2>(M, x, y, s);
-        case 1: return launch_tma_cfg<T, 8, 4>(M, x, y, s);
-        case 2: return launch_tma_cfg<T, 16, 2>(M, x, y, s);
-        case 3: return launch_tma_cfg<T, 4, 4>(M, x, y, s);
+        case 0: return launch_tma_cfg<T, 8, 2>(M, x, y, wl, s);
+        case 1: return launch_tma_cfg<T, 8, 4>(M, x, y, wl, s);
+        case 2: return launch_tma_cfg<T, 16, 2>(M, x, y, wl, s);
+        case 3: return launch_tma_cfg<T, 4, 4>(M, x, y, wl, s);
         default: return RGCSR_ERR_INVALID_ARG;
     }
 }
@@ -262,11 +266,14 @@ bool tma_eligible(const rgcsr_matrix *M) {
            aligned(M->columns) && aligned(M->row_lengths);
 }
 
-int launch_spmv_tma(const rgcsr_matrix *M, const void *x, void *y, int variant, cudaStream_t s) {
+int launch_spmv_tma(const rgcsr_matrix *M, const void *x, void *y, int variant, uint32_t wait_limit,
+                    cudaStream_t s) {
     if (!tma_eligible(M)) return RGCSR_ERR_INVALID_ARG;
     if (M->value_type == RGCSR_F64)
-        return launch_tma_t<double>(M, static_cast<const double *>(x), static_cast<double *>(y), variant, s);
-    return launch_tma_t<float>(M, static_cast<const float *>(x), static_cast<float *>(y), variant, s);
+        return launch_tma_t<double>(M, static_cast<const double *>(x), static_cast<double *>(y), variant,
+                                    wait_limit, s);
+    return launch_tma_t<float>(M, static_cast<const float *>(x), static_cast<float *>(y), variant, wait_limit,
+                               s);
 }
 
 }  // namespace rgcsr

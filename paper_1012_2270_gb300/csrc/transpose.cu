@@ -176,6 +176,94 @@ __global__ void gather_kernel(const V *__restrict__ src, const int64_t *__restri
     }
 }
 
+// Only when the values changed: flags is the state record's word 1, whose
+// bit 1 the hash kernel sets when the hash differs from the held one.
+template <typename V>
+__global__ void gather_if_kernel(const V *__restrict__ src, const int64_t *__restrict__ index, int64_t n,
+                                 V *__restrict__ dst, const unsigned long long *__restrict__ flags) {
+    if (!(*flags & 2ull)) return;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = index[s];
+        dst[s] = i >= 0 ? src[i] : V(0);
+    }
+}
+
+// Hash of n value words, two 64-bit sums
+//   h1 = sum_i mix(b_i ^ ((i + 1) K1)),  h2 = sum_i mix(b_i + (i + 1) K2)  (mod 2^64)
+// with b_i the bits of element i and mix the SplitMix64 finalizer (Steele,
+// Lea and Flood 2014; constants as published), a bijection of 64-bit words.
+// Because mix is a bijection, changing any one element always changes both
+// sums; several elements changed at once leave a sum unchanged only by
+// chance, since mix destroys the structure a common change of bits (e.g.
+// every value scaled by one factor) would otherwise carry into the sums.
+// The sums are exact modular arithmetic, so they do not depend on the order
+// of the additions.  The last block to finish (a ticket after a fence) adds
+// the block sums and updates the state record: words 0 and 3 the hash,
+// word 1 bit 0 "holds values", bit 1 "changed by this call".
+constexpr int kHashParts = 304;
+constexpr int kHashThreads = 256;
+
+__device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int o) {
+    const unsigned lo = __shfl_xor_sync(kFull, (unsigned)v, o), hi = __shfl_xor_sync(kFull, (unsigned)(v >> 32), o);
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <typename W>
+__global__ void __launch_bounds__(kHashThreads)
+values_hash_kernel(const W *__restrict__ v, int64_t n, unsigned long long *__restrict__ state) {
+    __shared__ unsigned long long sh[2][kHashThreads / 32];
+    __shared__ bool last;
+    unsigned long long h1 = 0, h2 = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long b = (unsigned long long)v[i], k = (unsigned long long)(i + 1);
+        h1 += mix64(b ^ (k * 0x9E3779B97F4A7C15ull));
+        h2 += mix64(b + k * 0xD1B54A32D192ED03ull);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        h1 += shfl_xor_u64(h1, o);
+        h2 += shfl_xor_u64(h2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = h1;
+        sh[1][threadIdx.x >> 5] = h2;
+    }
+    __syncthreads();
+    unsigned long long *part = state + 8;               // [kHashParts] h1, then [kHashParts] h2
+    unsigned *ticket = reinterpret_cast<unsigned *>(state + 2);
+    if (threadIdx.x == 0) {
+        unsigned long long b1 = 0, b2 = 0;
+        for (int w = 0; w < kHashThreads / 32; ++w) {
+            b1 += sh[0][w];
+            b2 += sh[1][w];
+        }
+        part[blockIdx.x] = b1;
+        part[kHashParts + blockIdx.x] = b2;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    unsigned long long t1 = 0, t2 = 0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+        t1 += __ldcg(part + b);
+        t2 += __ldcg(part + kHashParts + b);
+    }
+    const bool held = (state[1] & 1ull) != 0;
+    const bool changed = !held || state[0] != t1 || state[3] != t2;
+    state[0] = t1;
+    state[3] = t2;
+    state[1] = 1ull | (changed ? 2ull : 0ull);
+    *ticket = 0u;
+}
+
 __global__ void compose_kernel(const int64_t *__restrict__ outer, const int64_t *__restrict__ inner,
                                int64_t n, int64_t *__restrict__ out) {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
@@ -321,6 +409,32 @@ RGCSR_API int rgcsr_gather_values(const rgcsr_matrix *M, const void *src, const 
                                                static_cast<float *>(M->values));
     else
         return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    return launch_status();
+}
+
+RGCSR_API int rgcsr_gather_values_if_changed(const rgcsr_matrix *M, const void *src, int64_t n_src,
+                                             const int64_t *src_index, void *state, rgcsr_stream_t stream) {
+    static_assert(8 * (8 + 2 * kHashParts) <= RGCSR_VALUES_STATE_BYTES, "state record too small");
+    if (!M || M->n_stored < 0 || n_src < 0 || !state) return RGCSR_ERR_INVALID_ARG;
+    if (M->value_type != RGCSR_F64 && M->value_type != RGCSR_F32) return RGCSR_ERR_UNSUPPORTED_DTYPE;
+    if ((n_src > 0 && !src) || (M->n_stored > 0 && (!M->values || !src_index))) return RGCSR_ERR_INVALID_ARG;
+    if (((uintptr_t)state & 7) != 0) return RGCSR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto *st = static_cast<unsigned long long *>(state);
+    const unsigned g = grid_for(M->n_stored, 256);
+    if (M->value_type == RGCSR_F64) {
+        values_hash_kernel<unsigned long long><<<kHashParts, kHashThreads, 0, s>>>(
+            static_cast<const unsigned long long *>(src), n_src, st);
+        if (M->n_stored > 0)
+            gather_if_kernel<double><<<g, 256, 0, s>>>(static_cast<const double *>(src), src_index, M->n_stored,
+                                                       static_cast<double *>(M->values), st + 1);
+    } else {
+        values_hash_kernel<unsigned><<<kHashParts, kHashThreads, 0, s>>>(static_cast<const unsigned *>(src),
+                                                                       n_src, st);
+        if (M->n_stored > 0)
+            gather_if_kernel<float><<<g, 256, 0, s>>>(static_cast<const float *>(src), src_index, M->n_stored,
+                                                      static_cast<float *>(M->values), st + 1);
+    }
     return launch_status();
 }
 

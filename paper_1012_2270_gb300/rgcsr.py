@@ -56,6 +56,19 @@ def fp64_fma_probe(iters: int = 1024, stream=None) -> int:
 _FMA_SINKS: dict = {}
 
 
+def gather_probe(x: torch.Tensor, iters: int = 256, stream=None) -> int:
+    """Launches the library's random-gather kernel over the double vector x
+    (length a power of two) and returns how many 8-byte loads it issues."""
+    if not (x.is_cuda and x.is_contiguous() and x.dtype == torch.float64):
+        raise ValueError("gather_probe needs a contiguous CUDA float64 tensor")
+    sink = _FMA_SINKS.get(x.device)
+    if sink is None:
+        sink = _FMA_SINKS[x.device] = torch.zeros(1, dtype=torch.float64, device=x.device)
+    n = ctypes.c_int64(0)
+    L.call("rgcsr_gather_probe", _ptr(x), x.numel(), int(iters), _ptr(sink), ctypes.byref(n), _stream_ptr(stream))
+    return n.value
+
+
 def _dev(a, dtype=None, device="cuda") -> torch.Tensor:
     t = torch.as_tensor(np.ascontiguousarray(a)) if isinstance(a, np.ndarray) else a
     if dtype is not None and t.dtype != dtype:
@@ -100,6 +113,7 @@ class RgCSRMatrix:
         self.row_perm = None
         self._long = None          # long-row segment schedule, if enabled
         self._tiles = None         # group-tile schedule, if enabled
+        self._xwin = None          # shared-memory x windows, if planned
 
     # -- construction ------------------------------------------------------
     @classmethod
@@ -218,6 +232,32 @@ class RgCSRMatrix:
             self.split_long_rows(other._long[0].threshold, other._long[0].segment)
         return self
 
+    def plan_x_window(self, stream=None) -> "RgCSRMatrix":
+        """Plans the shared-memory x window of every block of 256 stored rows
+        (rgcsr_xwindow_plan) for spmv_xwindow()."""
+        nb = L.lib().rgcsr_xwindow_count(self.s.n_rows)
+        self._xwin = torch.empty(max(nb, 1) * ctypes.sizeof(L.XWindow), dtype=torch.uint8,
+                                 device=self.group_ptr.device)
+        L.call("rgcsr_xwindow_plan", ctypes.byref(self.s), _ptr(self._xwin), _stream_ptr(stream))
+        return self
+
+    def x_window_records(self) -> list:
+        """The planned windows as (n_ranges, total, lo, len) per block (host copy)."""
+        raw = self._xwin.cpu().numpy().view(np.int32).reshape(-1, 10)
+        nb = L.lib().rgcsr_xwindow_count(self.s.n_rows)
+        return [(int(r[0]), int(r[1]), r[2:6].tolist(), r[6:10].tolist()) for r in raw[:nb]]
+
+    def spmv_xwindow(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """y = A x with each planned block's x ranges staged in shared memory."""
+        if getattr(self, "_xwin", None) is None:
+            raise ValueError("call plan_x_window() first")
+        if x.dtype != self.x_dtype or x.numel() != self.s.n_cols or not x.is_contiguous():
+            raise ValueError(f"x must be a contiguous {self.x_dtype} vector of length {self.s.n_cols}")
+        y = out if out is not None else torch.empty(self.s.n_rows, dtype=self.x_dtype, device=x.device)
+        L.call("rgcsr_spmv_xwindow", ctypes.byref(self.s), _ptr(self._xwin), _ptr(x), _ptr(y),
+               _stream_ptr(stream))
+        return y
+
     @property
     def n_extra_tiles(self) -> int:
         return 0 if self._tiles is None else self._tiles[0].n_extra
@@ -281,13 +321,15 @@ class RgCSRMatrix:
     # -- products --------------------------------------------------------------
     def spmv(self, x: torch.Tensor, out: torch.Tensor | None = None,
              kernel: int = L.KERNEL_AUTO, x_load: int = L.XLOAD_NC, block_threads: int = 0,
-             split_weight: int = 0, variant: int = 0, stream=None) -> torch.Tensor:
-        """y = A x (overwrites ``out`` if given)."""
+             split_weight: int = 0, variant: int = 0, wait_limit: int = 0, stream=None) -> torch.Tensor:
+        """y = A x (overwrites ``out`` if given).  wait_limit: probes before a
+        bounded wait of the TMA kernel gives up (0 = the library's default;
+        small values only to exercise the timeout path)."""
         if x.dtype != self.x_dtype or x.numel() != self.s.n_cols or not x.is_contiguous():
             raise ValueError(f"x must be a contiguous {self.x_dtype} vector of length {self.s.n_cols}")
         y = out if out is not None else torch.empty(self.s.n_rows, dtype=self.x_dtype, device=x.device)
         default = (kernel == L.KERNEL_AUTO and x_load == L.XLOAD_NC and not block_threads
-                   and not split_weight and not variant)
+                   and not split_weight and not variant and not wait_limit)
         if default and self._tiles is not None:
             L.call("rgcsr_spmv_tiles", ctypes.byref(self.s), ctypes.byref(self._tiles[0]), _ptr(x), _ptr(y),
                    _stream_ptr(stream))
@@ -297,7 +339,7 @@ class RgCSRMatrix:
         elif default:
             L.call("rgcsr_spmv", ctypes.byref(self.s), _ptr(x), _ptr(y), _stream_ptr(stream))
         else:
-            ln = L.Launch(kernel, block_threads, x_load, split_weight, variant)
+            ln = L.Launch(kernel, block_threads, x_load, split_weight, variant, wait_limit)
             L.call("rgcsr_spmv_ex", ctypes.byref(self.s), _ptr(x), _ptr(y), ctypes.byref(ln),
                    _stream_ptr(stream))
         return y

@@ -134,7 +134,7 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
 # ctypes mirror -> C typedef of include/rgcsr.h
 STRUCTS = {"CSR": "rgcsr_csr", "Matrix": "rgcsr_matrix", "Launch": "rgcsr_launch", "Hyb": "hyb_matrix",
            "LongRows": "rgcsr_long_rows", "Tiles": "rgcsr_tiles", "BatchDesc": "rgcsr_batch_desc",
-           "Batch": "rgcsr_batch"}
+           "Batch": "rgcsr_batch", "XWindow": "rgcsr_xwindow"}
 
 
 def declared_structs():

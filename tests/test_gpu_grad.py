@@ -185,3 +185,56 @@ def test_bwd_values_from_rgcsr(dtype, G, order, k):
     _, dval_ref = oracle.spmm_grads(A.rowptr, A.col, vals, X, Gy, A.n_cols)
     _, dval_abs = abs_bounds(A, vals, X, Gy)
     assert_within_bound(dval, dval_ref, dval_abs, TAU[dtype], f"bwd values G={G} {order}")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_values_reloaded_only_when_they_change(dtype):
+    # the operator gathers values into A (forward) or A^T (backward) only
+    # when the values tensor changed: products stay right when values are
+    # updated in place, when another tensor is used, and when a backward
+    # runs after a forward with other values
+    rng = np.random.default_rng(9)
+    A = synth.random_csr(700, 500, rng.integers(0, 30, 700), seed=9)
+    op = SparseOperator(A.rowptr, A.col, A.n_cols, dtype=TT[dtype])
+    X = synth.uniform_matrix(A.n_cols, 3, seed=4).astype(NP[dtype])
+    Xt = torch.tensor(X, device="cuda")
+
+    def expect(vals):
+        y, absy = oracle.csr_spmm(A.rowptr, A.col, vals.astype(np.float64), X.astype(np.float64))
+        return y, absy
+
+    v1 = torch.tensor(A.val.astype(NP[dtype]), device="cuda")
+    with torch.no_grad():
+        y = spmm(op, v1, Xt)
+        assert_within_bound(y.cpu().numpy(), *expect(A.val.astype(NP[dtype])), TAU[dtype], "first")
+        y = spmm(op, v1, Xt)                                   # unchanged: no reload, same product
+        assert_within_bound(y.cpu().numpy(), *expect(A.val.astype(NP[dtype])), TAU[dtype], "again")
+        v1.mul_(-2.0)                                          # in place
+        y = spmm(op, v1, Xt)
+        assert_within_bound(y.cpu().numpy(), *expect(-2.0 * A.val.astype(NP[dtype])), TAU[dtype], "in place")
+        v1.data[17] = 5.0                                      # through .data: no version change, still seen
+        vals = -2.0 * A.val.astype(NP[dtype])
+        vals[17] = 5.0
+        y = spmm(op, v1, Xt)
+        assert_within_bound(y.cpu().numpy(), *expect(vals), TAU[dtype], ".data")
+        # unchanged values are not gathered again: overwrite the matrix's own
+        # slab, and a product with the same values keeps the overwritten slab
+        op.A.values.zero_()
+        y = spmm(op, v1, Xt)
+        assert not y.any()
+        op.load_values(v1, force=True)
+        y = spmm(op, v1, Xt)
+        assert_within_bound(y.cpu().numpy(), *expect(vals), TAU[dtype], "forced reload")
+    # backward of a product with v2 after a forward with v3: dX uses v2
+    v2 = torch.tensor((0.5 * A.val).astype(NP[dtype]), device="cuda", requires_grad=True)
+    v3 = torch.tensor((3.0 * A.val).astype(NP[dtype]), device="cuda")
+    Xg = torch.tensor(X, device="cuda", requires_grad=True)
+    Y = spmm(op, v2, Xg)
+    with torch.no_grad():
+        spmm(op, v3, Xt)
+    Gy = torch.ones_like(Y)
+    Y.backward(Gy)
+    vals2 = (0.5 * A.val).astype(NP[dtype]).astype(np.float64)
+    trp, tc, perm = oracle.csr_transpose(A.rowptr, A.col, A.n_cols)
+    dX_ref, dX_abs = oracle.csr_spmm(trp, tc, vals2[perm], np.ones((A.n_rows, 3)))
+    assert_within_bound(Xg.grad.cpu().numpy(), dX_ref, dX_abs, TAU[dtype], "dX after other values")

@@ -42,7 +42,7 @@ def check(A, src, fmt, x, G=32, kernels=({}, {"kernel": L.KERNEL_SPLIT}, {"kerne
     y_orig, a_orig = oracle.csr_spmv(A.rowptr, A.col, A.val, x)
     xd = torch.from_numpy(x32).cuda()
     if G == 32:
-        kernels = tuple(kernels) + tuple({"kernel": L.KERNEL_LEAN, "variant": v} for v in (1, 2, 4))   # vector loads
+        kernels = tuple(kernels) + tuple({"kernel": L.KERNEL_LEAN, "variant": v} for v in (1, 2, 4, 5, 6, 7))   # vector loads
     for kw in kernels:
         y = Q.spmv(xd, **kw).cpu().numpy()
         assert_within_bound(y, y_deq, a_deq, 2e-6, f"{A.name} {fmt} kernel error {kw}")

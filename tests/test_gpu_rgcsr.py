@@ -19,7 +19,10 @@ TT = {"f32": torch.float32, "f64": torch.float64}
 VARIANTS = [dict(), dict(kernel=L.KERNEL_PAPER), dict(kernel=L.KERNEL_SPLIT, x_load=L.XLOAD_PLAIN),
             dict(kernel=L.KERNEL_SPLIT, block_threads=64, split_weight=4), dict(kernel=L.KERNEL_LEAN)]
 VARIANTS += [dict(kernel=L.KERNEL_TMA, variant=v) for v in range(0, 4)]
-VARIANTS += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4)]   # vector loads, G = 32
+VARIANTS += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4, 5, 6, 7)]   # vector loads, G = 32
+# the x read paths: texture fetches and plain loads besides the read-only path
+VARIANTS += [dict(kernel=k, x_load=xl) for k in (L.KERNEL_PAPER, L.KERNEL_SPLIT, L.KERNEL_LEAN)
+             for xl in (L.XLOAD_TEX, L.XLOAD_PLAIN)]
 
 
 def variants(M):
@@ -28,7 +31,7 @@ def variants(M):
     for kw in VARIANTS:
         if kw.get("kernel") == L.KERNEL_TMA and (M.group_size != 32 or M.shape[0] < 32):
             continue
-        if kw.get("kernel") == L.KERNEL_LEAN and kw.get("variant") in (1, 2, 4) and M.group_size != 32:
+        if kw.get("kernel") == L.KERNEL_LEAN and kw.get("variant", 0) > 0 and M.group_size != 32:
             continue
         if kw.get("kernel") == L.KERNEL_PAPER and M.group_size > 1024:
             continue
@@ -229,6 +232,54 @@ def test_full_size_spmv(name, dtype):
     assert device_status() == 0
 
 
+_FULL_CACHE = {}
+
+
+def full_matrix(name):
+    if name not in _FULL_CACHE:
+        _FULL_CACHE.clear()                      # one full-size matrix in host memory at a time
+        _FULL_CACHE[name] = FULL[name]()
+    return _FULL_CACHE[name]
+
+
+def assert_equal_chunked(dev, ref, chunk=1 << 25):
+    """Device tensor == host array, element by element (bit patterns for
+    floating point), compared in chunks to bound host memory."""
+    assert dev.numel() == ref.size
+    flat = dev.reshape(-1)
+    ui = {8: np.uint64, 4: np.uint32, 2: np.uint16}[ref.itemsize]
+    for lo in range(0, ref.size, chunk):
+        hi = min(ref.size, lo + chunk)
+        got = flat[lo:hi].cpu().numpy()
+        if not np.array_equal(got.view(ui), ref[lo:hi].view(ui)):
+            bad = lo + int(np.flatnonzero(got.view(ui) != ref[lo:hi].view(ui))[0])
+            raise AssertionError(f"first difference at element {bad}")
+
+
+@pytest.mark.parametrize("name,order", [("a", None), ("c", None), ("b", "descending"), ("b", None)])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_full_size_layout_bit_exact(name, order, dtype):
+    # every group of the full-size layouts against the oracle's layout
+    # builder: row lengths, group pointers, value bits, columns and the slot
+    # map (in natural order (b) stores 1,677% artificial zeros at G = 32)
+    A = full_matrix(name)
+    vals = A.val.astype(NP[dtype])
+    perm = oracle.descending_order(A.rowptr) if order else None
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, vals, A.n_cols, group_size=32, dtype=TT[dtype],
+                             keep_slot_map=True, row_order=order)
+    lay = oracle.rgcsr_layout(A.rowptr, A.col, vals, 32, row_order=perm)
+    if order:
+        assert_equal_chunked(M.row_perm, perm.astype(np.int32))
+    assert M.n_stored == lay.n_stored
+    assert_equal_chunked(M.row_lengths, lay.row_lengths)
+    assert_equal_chunked(M.group_ptr, lay.group_ptr)
+    assert_equal_chunked(M.columns, lay.columns)
+    assert_equal_chunked(M.values, lay.values)
+    assert_equal_chunked(M.slot_to_csr, lay.slot_to_csr)
+    del M, lay
+    torch.cuda.empty_cache()
+
+
 def oracle_sizes(A, G):
     return oracle.rgcsr_sizes(A.rowptr, G)
 
@@ -268,6 +319,152 @@ def test_tma_sizes_and_partial_group(dtype, n):
     check_spmv(M, A, dtype, x, kernel=L.KERNEL_TMA)
     check_spmv(M, A, dtype, x)
     assert device_status() == 0
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_tma_bounded_wait_runs_out_then_next_launch_is_correct(dtype):
+    # the TMA kernel's waits are bounded: with a limit of one probe the first
+    # wait of (nearly) every warp runs out before its bulk copy lands, the
+    # kernel records RGCSR_STATUS_TIMEOUT, waits for its own copies in flight
+    # and ends; the status read clears the bit, and the next launch with the
+    # default limit is correct (the context stays usable)
+    A = synth.laplacian_3d(32)
+    M = to_gpu_matrix(A, dtype, 32, slot_map=False)
+    x = synth.uniform_vector(A.n_cols, seed=3)
+    xd = torch.from_numpy(x.astype(NP[dtype])).cuda()
+    assert device_status() == 0
+    y = torch.full((A.n_rows,), float("nan"), dtype=TT[dtype], device="cuda")
+    M.spmv(xd, out=y, kernel=L.KERNEL_TMA, wait_limit=1)
+    torch.cuda.synchronize()
+    assert device_status() == L.STATUS_TIMEOUT
+    assert torch.isnan(y).any()                    # rows of the abandoned groups stay unwritten
+    assert device_status() == 0                    # the read cleared the bit
+    check_spmv(M, A, dtype, x, kernel=L.KERNEL_TMA)
+    assert device_status() == 0
+    with pytest.raises(L.RgCSRError):
+        M.spmv(xd, out=y, kernel=L.KERNEL_TMA, wait_limit=-1)
+
+
+# ---------------------------------------------------------------------------
+# x staged in shared memory (x-window arm of the read-path study)
+# ---------------------------------------------------------------------------
+def expected_windows(A, G, perm, x_bytes):
+    """The plan's definition restated on the host: per block of 256 stored
+    rows, the sorted distinct columns of its entries cut where consecutive
+    columns are more than 64 apart; kept if at most 4 ranges of at most
+    32 KB of x, with at most 8,192 entries in the block."""
+    n = A.n_rows
+    rows = np.arange(n) if perm is None else np.asarray(perm)
+    out = []
+    for b in range((n + 255) // 256):
+        cols = [A.col[A.rowptr[r]:A.rowptr[r + 1]] for r in rows[b * 256:(b + 1) * 256]]
+        total = sum(c.size for c in cols)
+        if total == 0 or total > 8192:
+            out.append((0, 0, [], []))
+            continue
+        u = np.unique(np.concatenate(cols))
+        cut = np.flatnonzero(np.diff(u) > 64)
+        if cut.size > 3:
+            out.append((0, 0, [], []))
+            continue
+        starts = np.concatenate([[u[0]], u[cut + 1]])
+        ends = np.concatenate([u[cut], [u[-1]]]) + 1
+        lens = ends - starts
+        if lens.sum() > 32768 // x_bytes:
+            out.append((0, 0, [], []))
+            continue
+        out.append((len(starts), int(lens.sum()), starts.tolist(), lens.tolist()))
+    return out
+
+
+def banded(n, half, seed):
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    for i in range(n):
+        c = np.arange(max(0, i - half), min(n, i + half + 1))
+        rows.append(c.size)
+        cols.append(c)
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(rows, out=rp[1:])
+    return synth.CSRMatrix(n, n, rp, np.concatenate(cols).astype(np.int32), rng.uniform(-1, 1, int(rp[-1])),
+                           f"band{half}")
+
+
+def four_bands(n, seed):
+    """Row i holds columns i, i + n/4, i + n/2, i + 3n/4 (mod n): four
+    separated ranges per block, five where a block wraps around."""
+    rng = np.random.default_rng(seed)
+    cols = np.sort((np.arange(n)[:, None] + np.arange(4)[None, :] * (n // 4)) % n, axis=1)
+    rp = np.arange(n + 1, dtype=np.int64) * 4
+    return synth.CSRMatrix(n, n, rp, cols.reshape(-1).astype(np.int32), rng.uniform(-1, 1, 4 * n), "four_bands")
+
+
+XWIN_CASES = {
+    "four_bands": lambda: four_bands(4000, 3),                  # four ranges (five: not staged)
+    "ragged_6k": lambda: ragged(2000, 6000, seed=7, maxlen=20),  # one range of > 4,096: FP32 only
+    "laplace3d_32": lambda: synth.laplacian_3d(32),              # three bands per block
+    "laplace3d_16": lambda: synth.laplacian_3d(16),              # adjacent planes: one range
+    "laplace2d_64": lambda: synth.workload_small_laplacian(),    # one range
+    "stencil27_12": lambda: synth.stencil27_random(12),
+    "band_13_odd_n": lambda: banded(5003, 13, 1),                # one range; partial last block
+    "band_37": lambda: banded(3000, 37, 1),                      # > 8,192 entries per block: not staged
+    "ragged_narrow": lambda: ragged(3001, 2000, seed=4),         # random columns, narrow: one range
+    "ragged_wide": lambda: ragged(3001, 200000, seed=4, maxlen=20),   # random columns: not staged
+    "long_row": lambda: ragged(1000, 900, seed=5, long_rows=[(3, 850)]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(XWIN_CASES))
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("G,order", [(32, None), (7, None), (32, "descending")])
+def test_xwindow_plan_and_spmv(name, dtype, G, order):
+    A = XWIN_CASES[name]()
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dtype]), A.n_cols, group_size=G, dtype=TT[dtype],
+                             row_order=order).plan_x_window()
+    perm = None if M.row_perm is None else M.row_perm.cpu().numpy()
+    got = M.x_window_records()
+    want = expected_windows(A, G, perm, 8 if dtype == "f64" else 4)
+    for b, (g_, w_) in enumerate(zip(got, want)):
+        assert g_[0] == w_[0] and g_[1] == w_[1], (b, g_, w_)
+        assert g_[2][:w_[0]] == w_[2] and g_[3][:w_[0]] == w_[3], (b, g_, w_)
+    x = synth.uniform_vector(A.n_cols, seed=2)
+    xd = torch.from_numpy(x.astype(NP[dtype])).cuda()
+    y = M.spmv_xwindow(xd).cpu().numpy()
+    y_ref, absy = oracle.csr_spmv(A.rowptr, A.col, rounded_values(A.val, dtype), rounded_values(x, dtype))
+    assert_within_bound(y, y_ref, absy, TAU[dtype], f"{name} xwindow")
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_xwindow_reduced_storage(fmt):
+    A = synth.laplacian_3d(32)
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val, A.n_cols, group_size=32, dtype=torch.float64)
+    Q = M.quantized(fmt).plan_x_window()
+    recs = Q.x_window_records()
+    assert [r[:2] for r in recs] == [w[:2] for w in expected_windows(A, 32, None, 4)]
+    assert all(r[0] == 3 for r in recs[4:-4])     # blocks off the first and last z-planes: three bands
+    x = synth.uniform_vector(A.n_cols, seed=3).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    assert torch.equal(Q.spmv_xwindow(xd), Q.spmv(xd, kernel=L.KERNEL_LEAN))   # same order, same sums
+
+
+def test_texture_cache_overflow():
+    # more x buffers than the library keeps texture objects for: the cache
+    # is cleared (after a device synchronisation) and products stay right
+    A = ragged(500, 400, seed=6)
+    M = to_gpu_matrix(A, "f32", 8, slot_map=False)
+    for i in range(70):
+        x = synth.uniform_vector(A.n_cols, seed=100 + i)
+        check_spmv(M, A, "f32", x, kernel=L.KERNEL_SPLIT, x_load=L.XLOAD_TEX)
+
+
+def test_x_load_needs_a_scalar_kernel():
+    A = synth.workload_small_laplacian()
+    M = to_gpu_matrix(A, "f32", 32, slot_map=False)
+    xd = torch.zeros(A.n_cols, dtype=torch.float32, device="cuda")
+    for kw in (dict(x_load=L.XLOAD_TEX), dict(kernel=L.KERNEL_TMA, x_load=L.XLOAD_PLAIN),
+               dict(kernel=L.KERNEL_LEAN, variant=1, x_load=L.XLOAD_TEX), dict(kernel=L.KERNEL_SPLIT, x_load=3)):
+        with pytest.raises(L.RgCSRError):
+            M.spmv(xd, **kw)
 
 
 # ---------------------------------------------------------------------------
@@ -335,7 +532,7 @@ def test_unknown_kernel_variants_rejected():
     A = ragged(300, 200, seed=2)
     M = to_gpu_matrix(A, "f32", 32)
     x = torch.zeros(A.n_cols, dtype=torch.float32, device="cuda")
-    for kw in (dict(kernel=L.KERNEL_LEAN, variant=3), dict(kernel=L.KERNEL_LEAN, variant=5),
+    for kw in (dict(kernel=L.KERNEL_LEAN, variant=3), dict(kernel=L.KERNEL_LEAN, variant=8),
                dict(kernel=L.KERNEL_TMA, variant=4),
                dict(kernel=L.KERNEL_LEAN, variant=-1)):
         with pytest.raises(L.RgCSRError) as e:
@@ -408,3 +605,15 @@ def test_table6_standins(name):
     H = HybMatrix.from_csr(A.rowptr, A.col, A.val, A.n_cols, dtype=torch.float64)
     check_spmv(H, A, "f64", x)
     assert device_status() == 0
+
+
+def test_gather_probe_counts_and_writes_nothing():
+    from paper_1012_2270_gb300.rgcsr import gather_probe, _FMA_SINKS
+    x = torch.ones(1 << 12, dtype=torch.float64, device="cuda")
+    n = gather_probe(x, iters=2)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert n == sms * 1024 * 4 * 2
+    torch.cuda.synchronize()
+    assert float(_FMA_SINKS[x.device]) == 0.0
+    with pytest.raises(L.RgCSRError):
+        gather_probe(torch.ones(1000, dtype=torch.float64, device="cuda"))      # not a power of two

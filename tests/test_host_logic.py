@@ -163,7 +163,7 @@ def test_bench_headline_is_short_and_parses():
             "cases": ["b_f32", "b_f64", "c_f64"], "peak_source": "measured", "share_of_step": 0.3,
             "bytes_per_launch": big * 1e3, "avg_launch_us": big,
             "same_size_read": {"gbs": big, "frac": 0.5},
-            "gather_request_ceiling": {"us": big, "frac": 0.6, "sm_mhz": 2070.0}}
+            "gather_request_ceiling": {"us": big, "frac": 0.6, "probe_loads_per_sm_clk": 0.9987654}}
     e2e = {"value": big, "unit": "GB/s", "h2d_bytes_per_step": 123456789, "d2h_bytes_per_step": 123456789}
     cpu = {"value": big, "unit": "GB/s", "cores": 144, "kind": "oracle",
            "sample": "x" * 90}
