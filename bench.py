@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip HYB and the other forms")
     p.add_argument("--forms", default="", help="comma-separated subset of the forms to run (default: all)")
+    p.add_argument("--no-ir-sweep", action="store_true",
+                   help="skip the inner-tolerance sweep of the IR-CG form (shorter profiling runs)")
     p.add_argument("--cases", default="",
                    help="comma-separated subset of the six cases (a_f32, ..., c_f64) for profiling runs; "
                         "the default runs all six (the step the metric is defined on)")
@@ -121,7 +123,7 @@ def kernel_name(cfg, M, A, dt):
     if "long_rows" in cfg:
         return f"rgcsr_spmv_split+segments<{t}>"
     k = cfg.get("kernel", 0)
-    if k == 4 and cfg.get("variant", 0) in (1, 2, 4):
+    if k == 4 and cfg.get("variant", 0) in (1, 2, 4, 8):
         return f"rgcsr_spmv_vec<{t}>"
     if k == 4 and cfg.get("variant", 0) in (5, 6, 7):
         return f"rgcsr_spmv_vecp<{t}>"
@@ -135,6 +137,8 @@ def kernel_name(cfg, M, A, dt):
             k = 3
         else:
             k = 4 if dense else 2
+    if k == 3 and cfg.get("variant", 0) >= 4:
+        return f"rgcsr_spmv_tma_multi<{t}>"
     return {1: "rgcsr_spmv_paper", 2: "rgcsr_spmv_split", 3: "rgcsr_spmv_tma", 4: "rgcsr_spmv_lean"}[k] + f"<{t}>"
 
 
@@ -405,12 +409,12 @@ def forms_summary(forms):
     s = {}
     q = forms.get("quantized") or {}
     if "a_bf16" in q:
-        s["bf16_a_speedup_vs_f32"] = q["a_bf16"]["speedup_vs_f32"]
+        s["bf16_a_vs_f32"] = q["a_bf16"]["speedup_vs_f32"]
         s["bf16_a_err"] = q["a_bf16"]["max_err_over_absAx_vs_f64"]
     bt = forms.get("batched_512_f32")
     if bt:
         s["batched_gbs"] = bt["gbs"]
-        s["batched_speedup_vs_512_launches"] = bt["speedup_vs_plain"]
+        s["batched_vs_512_launches"] = bt["speedup_vs_plain"]
     bw = forms.get("backward_b_k8_f32")
     if bw:
         s["bwd_over_fwd"] = bw["backward_over_forward"]
@@ -419,7 +423,10 @@ def forms_summary(forms):
         s["rgcsr_over_hyb"] = {k: v["rgcsr_speedup"] for k, v in h.items() if k.startswith("b")}
     ic = forms.get("ir_cg_poisson128")
     if ic:
-        s["ir_cg_speedup_vs_fp64_cg"] = ic["fp64_cg_ms"] / ic["ms"]
+        s["ir_cg_vs_fp64_cg"] = ic["fp64_cg_ms"] / ic["ms"]
+        ok = [v for v in (ic.get("inner_tol_sweep") or {}).values() if v["final_rel_residual"] <= 1e-10]
+        if ok:
+            s["ir_cg_best_vs_fp64_cg"] = max(v["speedup_vs_fp64_cg"] for v in ok)
     sp = forms.get("spmm_b_f32")
     if sp and "k8" in sp:
         s["spmm_b_k8_gflops"] = sp["k8"]["gflops"]
@@ -570,9 +577,12 @@ def run_ours(args):
 
     # ---- forms beside plain ----
     forms = {}
-    if not args.no_forms and rank == 0 and only is None:         # the forms compare against all six cases
+    # with a subset of the cases (profiling runs) only explicitly requested
+    # forms run, each on the cases it needs that are present
+    if not args.no_forms and rank == 0 and (only is None or args.forms):
         forms = measure_forms(mats, cases, detail, dev, stream, tune_cache=bool(args.tune_cache),
-                              only=set(args.forms.split(",")) if args.forms else None)
+                              only=set(args.forms.split(",")) if args.forms else None,
+                              ir_sweep=not args.no_ir_sweep)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -749,7 +759,7 @@ def max_scaled_error(y, y_ref, absy):
     return float((err[ok] / den[ok]).max()) if bool(ok.any()) else 0.0
 
 
-def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None):
+def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None, ir_sweep=True):
     """The forms beside the plain SpMV; `only` (a set of names: hyb,
     quantized, x_read_path, spmm, backward, ir_cg, jacobi, conversion,
     group_size_sweep, table6, batched) limits them, None runs all."""
@@ -778,6 +788,8 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None)
         forms["hyb"] = {}
         for name, A, x in mats:
             for dt in DTYPES:
+                if f"{name}_{dt}" not in by:
+                    continue
                 c = by[f"{name}_{dt}"]
                 Hs = [HybMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dt]), A.n_cols, dtype=TT[dt])
                       for _ in range(COPIES)]
@@ -800,6 +812,8 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None)
         # 1e-12 |A||x| of the CPU oracle in the parity tests), scaled by |A||x|.
         forms["quantized"] = {}
         for name in ("a", "b", "c"):
+            if f"{name}_f64" not in by or f"{name}_f32" not in by:
+                continue
             c64, c32 = by[f"{name}_f64"], by[f"{name}_f32"]
             A = c32["A"]
             absA = RgCSRMatrix.from_csr(A.rowptr, A.col, np.abs(A.val), A.n_cols, dtype=torch.float64)
@@ -819,7 +833,8 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None)
                 # kernel: the default, or (G = 32, no schedule) 16-byte loads, whichever is faster here
                 kws = [{}]
                 if Qs[0].group_size == 32 and Qs[0]._tiles is None and Qs[0]._long is None:
-                    kws += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4, 5, 6, 7)]
+                    kws += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4, 5, 6, 7, 8)]
+                    kws += [dict(kernel=L.KERNEL_TMA, variant=v) for v in (4, 5, 6)]
                 ts = {i: rotating_us([lambda Q=Q, xj=xj, y=y, k=k: Q.spmv(xj, out=y, **k)
                                       for Q, xj, y in zip(Qs, xs, ys)], stream)
                       for i, k in enumerate(kws)}
@@ -831,6 +846,8 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None)
                 forms["quantized"][f"{name}_{fmt}"] = {
                     "gbs": nb / t / 1e3, "gflops": 2 * A.nnz / t / 1e3, "us": t,
                     "speedup_vs_f32": detail[f"{name}_f32"]["us"] / t, "kernel": kw or "default",
+                    "us_by_kernel": {("default" if not k else f"k{k['kernel']}v{k['variant']}"): ts[i]
+                                     for i, k in enumerate(kws)},
                     "max_err_over_absAx_vs_f64": max_scaled_error(ys[0], y64, absy)}
                 del Qs, ys
             del y64, absy
@@ -906,29 +923,57 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None)
         del Mb, Mt, Md, Hb
 
     if want("backward"):
-        # -- backward of Y = A X on (b), batch of 8 right-hand sides ---------------
+        # -- backward of Y = A X on (b), batch of 8 right-hand sides: three
+        # operators (own matrices, values and X) called in turn, ten rounds
+        # back to back, one event pair: the device time per call, with the
+        # host's autograd overhead hidden behind the queued kernels and no
+        # call finding its matrix in L2 ---------------------------------------
         G = 32
-        op = SparseOperator(b.rowptr, b.col, b.n_cols, dtype=torch.float32, group_size=G, row_order="descending",
-                            tiles=64)
-        vals = torch.from_numpy(b.val.astype(np.float32)).to(dev).requires_grad_(True)
-        X = torch.rand(b.n_cols, 8, device=dev, requires_grad=True)
+        ops = []
+        for _ in range(COPIES):
+            op = SparseOperator(b.rowptr, b.col, b.n_cols, dtype=torch.float32, group_size=G,
+                                row_order="descending", tiles=64)
+            vals = torch.from_numpy(b.val.astype(np.float32)).to(dev).requires_grad_(True)
+            X = torch.rand(b.n_cols, 8, device=dev, requires_grad=True)
+            ops.append((op, vals, X))
 
-        def fwd():
+        def per_call_us(fn, rounds=10):
+            for o in ops:
+                fn(*o)
+            torch.cuda.synchronize()
+            e0, e1 = _ev()
+            e0.record(stream)
+            for _ in range(rounds):
+                for o in ops:
+                    fn(*o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return 1e3 * e0.elapsed_time(e1) / (rounds * len(ops))
+
+        def fwd(op, vals, X):
             with torch.no_grad():
                 return spmm(op, vals, X)
 
-        def fwd_bwd():
+        def fwd_bwd(op, vals, X):
             vals.grad = None
             X.grad = None
             Y = spmm(op, vals, X)
             (Y * Y).sum().backward()
-        t_f = time_flushed(fwd, 10, flush, stream)
-        t_fb = time_flushed(fwd_bwd, 10, flush, stream)
-        forms["backward_b_k8_f32"] = {"group_size": G, "schedule": "descending row order, group tiles C=64", "forward_us": t_f, "forward_backward_us": t_fb,
-                                      "backward_over_forward": (t_fb - t_f) / t_f}
-        del op, vals, X
 
-    if want("ir_cg"):
+        def spmm_only(op, vals, X):
+            op.A.spmm(X.detach(), out=op._bench_y)
+
+        for o in ops:
+            o[0]._bench_y = torch.empty(b.n_rows, 8, device=dev)
+        t_mm = per_call_us(spmm_only)
+        t_f = per_call_us(fwd)
+        t_fb = per_call_us(fwd_bwd)
+        forms["backward_b_k8_f32"] = {"group_size": G, "schedule": "descending row order, group tiles C=64",
+                                      "spmm_us": t_mm, "forward_us": t_f, "forward_backward_us": t_fb,
+                                      "forward_over_spmm": t_f / t_mm, "backward_over_forward": (t_fb - t_f) / t_f}
+        del ops
+
+    if want("ir_cg") and "a_f64" in by:
         # -- mixed-precision iterative refinement CG, Poisson 128^3 ---------------
         a = [m for m in mats if m[0] == "a"][0][1]
         M64 = by["a_f64"]["M"]
@@ -937,8 +982,8 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None)
         e0, e1 = _ev()
         torch.cuda.nvtx.range_push("ir_cg")                # a profiler can pick it out
         e0.record(stream)
-        x_ir, outer, inner, rel = solvers.ir_cg(M64, lo, rhs, outer_tol=1e-10, max_outer=50, inner_tol=1e-4,
-                                                 max_inner=500)
+        x_ir, outer, inner, rel = solvers.ir_cg(M64, lo, rhs, outer_tol=1e-10, max_outer=50, inner_tol=1e-6,
+                                                 max_inner=2000)
         e1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
@@ -948,10 +993,25 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None)
         x64, its64, rel64 = solvers.cg(M64, rhs, rel_tol=1e-10, max_iter=5000)
         e1.record(stream)
         torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1)
+        # the inner tolerance sets how the iterations split into corrections:
+        # each correction restarts the inner CG, so fewer, deeper inner solves
+        # need fewer iterations in all (float CG reaches about 1e-6)
+        sweep = {}
+        for tol in (1e-3, 1e-4, 1e-5, 1e-6) if ir_sweep else ():
+            e0, e1 = _ev()
+            e0.record(stream)
+            xs, o_, i_, r_ = solvers.ir_cg(M64, lo, rhs, outer_tol=1e-10, max_outer=50, inner_tol=tol, max_inner=2000)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sweep[f"{tol:g}"] = {"ms": e0.elapsed_time(e1), "corrections": o_, "inner_iterations": i_,
+                                 "final_rel_residual": r_, "speedup_vs_fp64_cg": t64 / e0.elapsed_time(e1)}
+            del xs
         forms["ir_cg_poisson128"] = {
             "ms": t_ir, "corrections": outer, "inner_iterations": inner, "final_rel_residual": rel,
-            "fp64_cg_ms": e0.elapsed_time(e1), "fp64_cg_iterations": its64,
-            "rel_diff_vs_fp64_cg": float((x_ir - x64).norm() / x64.norm())}
+            "fp64_cg_ms": t64, "fp64_cg_iterations": its64,
+            "rel_diff_vs_fp64_cg": float((x_ir - x64).norm() / x64.norm()),
+            "inner_tol_sweep": sweep}
         del lo, x_ir, x64
 
     if want("jacobi"):

@@ -108,9 +108,12 @@ typedef struct {
 #define RGCSR_KERNEL_SPLIT  2    /* one thread per row; long rows of a warp finished
                                     by the whole warp with a shuffle reduction      */
 #define RGCSR_KERNEL_TMA    3    /* G == 32 only: group slabs staged in shared memory by
-                                    bulk copies (cp.async.bulk), one warp per group,
+                                    bulk copies (cp.async.bulk) into a ring per warp,
                                     persistent grid; needs 16-byte aligned values,
-                                    columns and row_lengths and n_rows >= 32       */
+                                    columns and row_lengths and n_rows >= 32.
+                                    Variants 0-3 (F64/F32): one group (or a piece
+                                    of one) per copy; 4-6 (every value type):
+                                    several whole groups per copy while they fit  */
 #define RGCSR_KERNEL_LEAN   4    /* one thread per row, no long-row split, sized for
                                     full occupancy (rows of similar lengths)        */
 #define RGCSR_KERNEL_SELL   5    /* comparator, not the method: sliced ELLPACK on the
@@ -135,7 +138,10 @@ typedef struct {
                                    relative to one thread-per-row step, x 4        */
     int32_t variant;            /* configuration of the chosen kernel, 0 = default:
                                    TMA: 0..3 = (slot-rows per chunk, ring stages)
-                                   (8,2), (8,4), (16,2), (4,4); LEAN: 1, 2, 4 =
+                                   (8,2), (8,4), (16,2), (4,4); 4..6 = chunks of
+                                   whole consecutive groups (up to 16) while they
+                                   fit: (32,2), (32,3), (16,4), four warps per
+                                   CTA; LEAN: 1, 2, 4 =
                                    G = 32 with vector loads: a lane owns 4 rows
                                    (F64: 2) of a group, 2 slot-rows in flight
                                    (1), or 2 rows, 4 slot-rows in flight (2), or
@@ -145,8 +151,10 @@ typedef struct {
                                    current x gathers) with 16-byte value loads
                                    (a lane owns 16 / value size rows: F64 2,
                                    F32 4, BF16/F16 8), 2, 1 or 4 slot-rows per
-                                   stage; 16-byte aligned values and columns;
-                                   other kernels: 0                               */
+                                   stage; 8 = as 1 with 8 slot-rows in flight
+                                   (a short row's whole slab at once);
+                                   16-byte aligned values and columns; other
+                                   kernels: 0                                     */
     int32_t wait_limit;         /* TMA kernel: non-blocking probes of a stage's
                                    mbarrier before a wait gives up, 0 = default
                                    (2^26, about a second).  A wait that runs out

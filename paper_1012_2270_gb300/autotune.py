@@ -7,7 +7,7 @@
   per GPU by experiment (Sec. 4.3: 128 was best on a GTX 280); here the
   choice follows the matrix.
 * ``tune``: times candidate (group size, kernel, variant) configurations
-  with CUDA events, flushing L2 (by a read) between launches, and caches
+  in CUDA graphs, flushing L2 (by a read) before each launch, and caches
   the fastest per (matrix pattern, value type, GPU name) in a JSON file;
   the default configuration stays unless another is more than 2% faster.
 * ``tune_hyb_width``: the same for the ELL width of the HYB format around
@@ -89,24 +89,47 @@ def flush_l2(flush: torch.Tensor) -> None:
     flush.sum()
 
 
-def _time(fn, reps: int, flush: torch.Tensor) -> float:
-    """Time in microseconds of fn() with L2 flushed before each call: the
-    mean of the middle half of the samples, which resolves differences
-    finer than the event timer's tick when the samples jitter across it."""
-    fn()
+def _graph(fns):
+    """A CUDA graph of fns called in order on a capture stream (each call
+    enqueues its kernels on the current stream)."""
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        for f in fns:
+            f()
+    torch.cuda.current_stream().wait_stream(side)
+    return g
+
+
+def _replay_median(g, replays: int) -> float:
+    g.replay()
     torch.cuda.synchronize()
-    ts = []
-    for _ in range(reps):
-        flush_l2(flush)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(replays)]
+    for e0, e1 in ev:
         e0.record()
-        fn()
+        g.replay()
         e1.record()
-        e1.synchronize()
-        ts.append(1e3 * e0.elapsed_time(e1))
-    ts.sort()
-    q = len(ts) // 4
-    return statistics.fmean(ts[q:len(ts) - q])
+    torch.cuda.synchronize()
+    return statistics.median(e0.elapsed_time(e1) for e0, e1 in ev)
+
+
+def _time(fn, reps: int, flush: torch.Tensor) -> float:
+    """Time in microseconds of fn() with L2 flushed before each call, from
+    CUDA graphs: one of `reps` (flush, fn) pairs and one of the `reps`
+    flushes alone, the difference of their median replay times divided by
+    reps.  The graph leaves out host launch gaps, as the benchmark's own
+    timing does, so the tuner ranks configurations the way they are
+    measured."""
+    fn()
+    flush_l2(flush)
+    torch.cuda.synchronize()
+    r = max(reps, 4)
+    g1 = _graph([f for _ in range(r) for f in (lambda: flush_l2(flush), fn)])
+    g0 = _graph([lambda: flush_l2(flush) for _ in range(r)])
+    t = (_replay_median(g1, 5) - _replay_median(g0, 5)) * 1e3 / r
+    del g1, g0
+    return max(t, 0.0)
 
 
 def candidates(rowptr, dtype: torch.dtype):
@@ -122,10 +145,10 @@ def candidates(rowptr, dtype: torch.dtype):
     irregular = stored_slots(lengths, 32) * 4 > nnz * 5
     cands = [dict(group_size=32, kernel=L.KERNEL_AUTO)]
     if not irregular:
-        cands += [dict(group_size=32, kernel=L.KERNEL_TMA, variant=v) for v in range(4)]
+        cands += [dict(group_size=32, kernel=L.KERNEL_TMA, variant=v) for v in range(7)]
         cands += [dict(group_size=G, kernel=k) for G in (32, 64) for k in (L.KERNEL_LEAN, L.KERNEL_SPLIT)]
         if dtype in (torch.float32, torch.float64):
-            cands += [dict(group_size=32, kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4, 5, 6, 7)]
+            cands += [dict(group_size=32, kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4, 5, 6, 7, 8)]
     else:
         Gm = model_group_size(rowptr, dtype.itemsize)
         cands += [dict(group_size=G, kernel=L.KERNEL_SPLIT) for G in sorted({1, 2, 4, 8, Gm})]

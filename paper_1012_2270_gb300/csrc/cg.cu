@@ -3,15 +3,17 @@
 // a CG iteration is one SpMV plus SAXPY and SDOT operations).
 //
 // rgcsr_cg:    textbook CG from x0 = 0; the step lengths live in device
-//              scalars, so an iteration is five kernels and no host
-//              round trip; the host reads the residual norm every
-//              `check_every` iterations to test convergence.
+//              scalars, so an iteration is four kernels (the SpMV and the
+//              three below) and no host round trip; the host reads the
+//              residual norm every `check_every` iterations to test
+//              convergence.
 // rgcsr_ir_cg: outer loop in FP64 -- r = b - A x with the FP64 matrix,
 //              stop when ||r|| <= tol ||b||; inner CG in float on a
 //              lower-precision copy of A (float, bfloat16 or half values)
 //              solves A d = r to a loose tolerance; x += d in FP64.
 #include "common.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace rgcsr {
@@ -19,64 +21,183 @@ namespace {
 
 constexpr int kThreads = 256;
 
-unsigned grid(int64_t n) {
-    int64_t b = ceil_div(n, kThreads);
-    if (b > 152 * 16) b = 152 * 16;
-    return (unsigned)(b > 0 ? b : 1);
+// One CG iteration after the SpMV q = A d is three kernels, each moving 16
+// bytes per access:
+//   cg_dq:    dq = d . q; the last block to finish sets alpha = rr / dq;
+//   cg_xr_rr: x += alpha d, r -= alpha q, and rr' = r . r from the new r in
+//             the same pass; the last block sets beta = rr' / rr;
+//   cg_d:     d = r + beta d.
+// The step lengths are computed once, in double, by the last block of a
+// reduction and read by every thread as scalars (a division per thread
+// would run on the narrow FP64 pipe).  Dots are deterministic: a fixed grid
+// for a given n, a fixed order within each thread (float vectors by the
+// compensated Dot2 step, double vectors by FMAs), a block tree, then the
+// block sums in block order.  Scalar block (doubles): [0], [1] rr (the slot
+// `cur` holds the current one), [2] dq, [3] alpha, [4] beta; the ticket of
+// the last-block reductions is the unsigned at byte 64.
+constexpr int kCgParts = 1216;          // blocks of the fused kernels at most (8 per SM)
+constexpr int kU = 4;                   // packs a reducing thread loads before it uses them
+
+template <typename T>
+__device__ __forceinline__ void acc_dot(T a, T b, float &s, float &c, double &sd) {
+    if constexpr (sizeof(T) == 4) dot2_step(a, b, s, c);
+    else sd = fma((double)a, (double)b, sd);
 }
 
-// alpha = rr / dq;  x += alpha d;  r -= alpha q   (W elements per access)
+// The block's partial (every thread passes its own) goes to parts; true in
+// the block that finishes last, whose threads then get the grand total.
+__device__ __forceinline__ bool reduce_last(double v, double *parts, unsigned *ticket, double *sh, double &total) {
+    __shared__ bool last;
+    const double b = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        parts[blockIdx.x] = b;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double t = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(parts + i);
+    total = block_sum(t, sh);
+    return true;
+}
+
 template <typename T, int W>
-__global__ void cg_xr_kernel(int64_t n, const double *__restrict__ rr, const double *__restrict__ dq,
-                             T *__restrict__ x, T *__restrict__ r, const T *__restrict__ d,
-                             const T *__restrict__ q) {
-    const T alpha = (T)(*rr / *dq);
+__global__ void __launch_bounds__(kThreads)
+cg_dq_kernel(int64_t n, const T *__restrict__ d, const T *__restrict__ q, double *scal, int cur, double *parts,
+             unsigned *ticket) {
+    __shared__ double sh[32];
     const int64_t S = (int64_t)gridDim.x * blockDim.x, tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nw = n / W;
-    for (int64_t i = tid; i < nw; i += S) {
-        Pack<T, W> xv = ld_pack<T, W>(x + i * W), rv = ld_pack<T, W>(r + i * W);
-        const Pack<T, W> dv = ld_pack<T, W>(d + i * W), qv = ld_pack<T, W>(q + i * W);
+    float s = 0.0f, c = 0.0f;
+    double sd = 0.0;
+    // packs tid, tid + S, tid + 2S, ... in that order; kU of them loaded
+    // before any is used, so each thread keeps kU * 32 bytes in flight
+#pragma unroll 1
+    for (int64_t i0 = tid; i0 < nw; i0 += kU * S) {
+        Pack<T, W> dv[kU], qv[kU];
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-            xv.v[k] = fma(alpha, dv.v[k], xv.v[k]);
-            rv.v[k] = fma(-alpha, qv.v[k], rv.v[k]);
-        }
-        st_pack<T, W>(x + i * W, xv);
-        st_pack<T, W>(r + i * W, rv);
+        for (int u = 0; u < kU; ++u)
+            if (i0 + u * S < nw) {
+                dv[u] = ld_pack<T, W>(d + (i0 + u * S) * W);
+                qv[u] = ld_pack<T, W>(q + (i0 + u * S) * W);
+            }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (i0 + u * S < nw) {
+#pragma unroll
+                for (int k = 0; k < W; ++k) acc_dot(dv[u].v[k], qv[u].v[k], s, c, sd);
+            }
+    }
+    for (int64_t i = nw * W + tid; i < n; i += S) acc_dot(d[i], q[i], s, c, sd);
+    double total;
+    if (!reduce_last(sizeof(T) == 4 ? (double)s + (double)c : sd, parts, ticket, sh, total)) return;
+    if (threadIdx.x == 0) {
+        scal[2] = total;
+        scal[3] = scal[cur] / total;
+        *ticket = 0u;
+    }
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads)
+cg_xr_rr_kernel(int64_t n, T *__restrict__ x, T *__restrict__ r, const T *__restrict__ d,
+                const T *__restrict__ q, double *scal, int cur, double *parts, unsigned *ticket) {
+    __shared__ double sh[32];
+    const T alpha = (T)scal[3];
+    const int64_t S = (int64_t)gridDim.x * blockDim.x, tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nw = n / W;
+    float s = 0.0f, c = 0.0f;
+    double sd = 0.0;
+#pragma unroll 1
+    for (int64_t i0 = tid; i0 < nw; i0 += kU * S) {
+        Pack<T, W> xv[kU], rv[kU], dv[kU], qv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (i0 + u * S < nw) {
+                const int64_t i = i0 + u * S;
+                xv[u] = ld_pack<T, W>(x + i * W);
+                rv[u] = ld_pack<T, W>(r + i * W);
+                dv[u] = ld_pack<T, W>(d + i * W);
+                qv[u] = ld_pack<T, W>(q + i * W);
+            }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (i0 + u * S < nw) {
+                const int64_t i = i0 + u * S;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    xv[u].v[k] = fma(alpha, dv[u].v[k], xv[u].v[k]);
+                    rv[u].v[k] = fma(-alpha, qv[u].v[k], rv[u].v[k]);
+                    acc_dot(rv[u].v[k], rv[u].v[k], s, c, sd);
+                }
+                st_pack<T, W>(x + i * W, xv[u]);
+                st_pack<T, W>(r + i * W, rv[u]);
+            }
     }
     for (int64_t i = nw * W + tid; i < n; i += S) {
         x[i] = fma(alpha, d[i], x[i]);
-        r[i] = fma(-alpha, q[i], r[i]);
+        const T ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        acc_dot(ri, ri, s, c, sd);
+    }
+    double total;
+    if (!reduce_last(sizeof(T) == 4 ? (double)s + (double)c : sd, parts, ticket, sh, total)) return;
+    if (threadIdx.x == 0) {
+        scal[1 - cur] = total;
+        scal[4] = total / scal[cur];
+        *ticket = 0u;
     }
 }
 
-// beta = rr_new / rr_old;  d = r + beta d
 template <typename T, int W>
-__global__ void cg_d_kernel(int64_t n, const double *__restrict__ rr_new, const double *__restrict__ rr_old,
-                            const T *__restrict__ r, T *__restrict__ d) {
-    const T beta = (T)(*rr_new / *rr_old);
+__global__ void __launch_bounds__(kThreads)
+cg_d_kernel(int64_t n, const double *__restrict__ scal, const T *__restrict__ r, T *__restrict__ d) {
+    const T beta = (T)scal[4];
     const int64_t S = (int64_t)gridDim.x * blockDim.x, tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nw = n / W;
+#pragma unroll 1
     for (int64_t i = tid; i < nw; i += S) {
-        const Pack<T, W> rv = ld_pack<T, W>(r + i * W);
-        Pack<T, W> dv = ld_pack<T, W>(d + i * W);
+        const Pack<T, W> rv = ld_pack<T, W>(r + i * W), dv = ld_pack<T, W>(d + i * W);
+        Pack<T, W> o;
 #pragma unroll
-        for (int k = 0; k < W; ++k) dv.v[k] = fma(beta, dv.v[k], rv.v[k]);
-        st_pack<T, W>(d + i * W, dv);
+        for (int k = 0; k < W; ++k) o.v[k] = fma(beta, dv.v[k], rv.v[k]);
+        st_pack<T, W>(d + i * W, o);
     }
     for (int64_t i = nw * W + tid; i < n; i += S) d[i] = fma(beta, d[i], r[i]);
 }
 
+// Blocks of the fused kernels: one 16-byte pack per thread where possible,
+// at most `per_sm` blocks per SM and kCgParts in all.  The reducing kernels
+// take 2 per SM (fewer same-address tickets, kU packs in flight per
+// thread), the plain update 8.
+unsigned cg_grid(int64_t units, int per_sm) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) ==
+                                                      cudaSuccess && v > 0)
+            sms = v;
+        else
+            sms = 152;
+    }
+    int64_t b = ceil_div(units, kThreads);
+    const int64_t cap = std::min<int64_t>((int64_t)sms * per_sm, kCgParts);
+    if (b > cap) b = cap;
+    return (unsigned)(b > 0 ? b : 1);
+}
+
 struct CgScratch {
     void *r, *d, *q;
-    double *scal;       // [rr0, rr1, dq, spare]
+    double *scal;       // [rr0, rr1, dq, alpha, beta]
     unsigned *count;    // the one-pass dot's block ticket (in the scalar block)
     double *partials;
 };
 
 size_t cg_bytes(int64_t n, int vt) {
     const size_t es = vt == RGCSR_F64 ? 8 : 4;
-    return 3 * align_up((size_t)n * es, 256) + 256 + align_up((size_t)kDotParts * 8, 256);
+    return 3 * align_up((size_t)n * es, 256) + 256 + align_up((size_t)std::max(kDotParts, kCgParts) * 8, 256);
 }
 
 CgScratch carve_cg(void *ws, int64_t n, int vt) {
@@ -123,20 +244,19 @@ int cg_run(const rgcsr_matrix *A, const void *b, void *x, double rel_tol, int ma
     auto iteration = [&](cudaStream_t st_, int cur_) -> int {
         int e;
         if ((e = rgcsr_spmv(A, c.d, c.q, (rgcsr_stream_t)st_)) != RGCSR_OK) return e;
-        if ((e = dot_device(n, c.d, c.q, &c.scal[2], c.partials, vt, st_, c.count)) != RGCSR_OK) return e;
         T *xt = static_cast<T *>(x), *rt = static_cast<T *>(c.r), *dt = static_cast<T *>(c.d);
         const T *qt = static_cast<const T *>(c.q);
-        if (vec)
-            cg_xr_kernel<T, kW><<<grid(ceil_div(n, kW)), kThreads, 0, st_>>>(n, &c.scal[cur_], &c.scal[2], xt, rt,
-                                                                            dt, qt);
-        else
-            cg_xr_kernel<T, 1><<<grid(n), kThreads, 0, st_>>>(n, &c.scal[cur_], &c.scal[2], xt, rt, dt, qt);
-        if ((e = dot_device(n, c.r, c.r, &c.scal[1 - cur_], c.partials, vt, st_, c.count)) != RGCSR_OK) return e;
-        if (vec)
-            cg_d_kernel<T, kW><<<grid(ceil_div(n, kW)), kThreads, 0, st_>>>(n, &c.scal[1 - cur_], &c.scal[cur_],
-                                                                           rt, dt);
-        else
-            cg_d_kernel<T, 1><<<grid(n), kThreads, 0, st_>>>(n, &c.scal[1 - cur_], &c.scal[cur_], rt, dt);
+        if (vec) {
+            const unsigned gr = cg_grid(ceil_div(n, kW), 2), gu = cg_grid(ceil_div(n, kW), 8);
+            cg_dq_kernel<T, kW><<<gr, kThreads, 0, st_>>>(n, dt, qt, c.scal, cur_, c.partials, c.count);
+            cg_xr_rr_kernel<T, kW><<<gr, kThreads, 0, st_>>>(n, xt, rt, dt, qt, c.scal, cur_, c.partials, c.count);
+            cg_d_kernel<T, kW><<<gu, kThreads, 0, st_>>>(n, c.scal, rt, dt);
+        } else {
+            const unsigned gr = cg_grid(n, 2), gu = cg_grid(n, 8);
+            cg_dq_kernel<T, 1><<<gr, kThreads, 0, st_>>>(n, dt, qt, c.scal, cur_, c.partials, c.count);
+            cg_xr_rr_kernel<T, 1><<<gr, kThreads, 0, st_>>>(n, xt, rt, dt, qt, c.scal, cur_, c.partials, c.count);
+            cg_d_kernel<T, 1><<<gu, kThreads, 0, st_>>>(n, c.scal, rt, dt);
+        }
         return launch_status();
     };
     // After the first round of iterations (which also runs any one-off kernel

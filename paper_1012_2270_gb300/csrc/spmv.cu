@@ -459,7 +459,8 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
                 n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
         return launch_status();
     }
-    if (kernel == RGCSR_KERNEL_LEAN && L && (L->variant == 1 || L->variant == 2 || L->variant == 4)) {
+    if (kernel == RGCSR_KERNEL_LEAN && L && (L->variant == 1 || L->variant == 2 || L->variant == 4 ||
+                                             L->variant == 8)) {
         auto aligned = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
         if (G != 32 || !aligned(val) || !aligned(M->columns)) return RGCSR_ERR_INVALID_ARG;
         // variant 1: 4 rows per lane (FP64: 2), 2 slot-rows in flight;
@@ -469,7 +470,10 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
         const int lpg = L->variant == 2 ? 16 : 32 / rpl1;
         const int64_t blocks = ceil_div(M->n_groups * lpg, (int64_t)kDefaultThreads);
         if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
-        if (L->variant == 1)
+        if (L->variant == 8)          // every slot-row of a short row in flight at once
+            rgcsr_spmv_vec<V, rpl1, 8, 2><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
+                n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
+        else if (L->variant == 1)
             rgcsr_spmv_vec<V, rpl1, 2, 5><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
                 n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
         else if (L->variant == 2)

@@ -39,7 +39,7 @@ def cg(A: RgCSRMatrix, b: torch.Tensor, rel_tol: float = 1e-8, max_iter: int = 1
 
 
 def ir_cg(A_hi: RgCSRMatrix, A_lo: RgCSRMatrix, b: torch.Tensor, outer_tol: float = 1e-10,
-          max_outer: int = 50, inner_tol: float = 1e-4, max_inner: int = 500):
+          max_outer: int = 50, inner_tol: float = 1e-6, max_inner: int = 2000):
     """Iterative refinement; returns (x, corrections, inner iterations, rel. residual)."""
     x = torch.empty_like(b)
     nb = L.lib().rgcsr_ir_cg_workspace_bytes(A_hi.shape[0])

@@ -18,8 +18,8 @@ NP = {"f32": np.float32, "f64": np.float64}
 TT = {"f32": torch.float32, "f64": torch.float64}
 VARIANTS = [dict(), dict(kernel=L.KERNEL_PAPER), dict(kernel=L.KERNEL_SPLIT, x_load=L.XLOAD_PLAIN),
             dict(kernel=L.KERNEL_SPLIT, block_threads=64, split_weight=4), dict(kernel=L.KERNEL_LEAN)]
-VARIANTS += [dict(kernel=L.KERNEL_TMA, variant=v) for v in range(0, 4)]
-VARIANTS += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4, 5, 6, 7)]   # vector loads, G = 32
+VARIANTS += [dict(kernel=L.KERNEL_TMA, variant=v) for v in range(0, 7)]
+VARIANTS += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4, 5, 6, 7, 8)]   # vector loads, G = 32
 # the x read paths: texture fetches and plain loads besides the read-only path
 VARIANTS += [dict(kernel=k, x_load=xl) for k in (L.KERNEL_PAPER, L.KERNEL_SPLIT, L.KERNEL_LEAN)
              for xl in (L.XLOAD_TEX, L.XLOAD_PLAIN)]
@@ -224,9 +224,9 @@ def test_full_size_spmv(name, dtype):
     if name != "b":
         check_spmv(M, A, dtype, x, kernel=L.KERNEL_SPLIT)
         check_spmv(M, A, dtype, x, kernel=L.KERNEL_LEAN)
-        for v in (1, 2, 4):                                 # vector loads
+        for v in (1, 2, 4, 5, 6, 7, 8):                     # vector loads (and pipelined)
             check_spmv(M, A, dtype, x, kernel=L.KERNEL_LEAN, variant=v)
-        for v in range(4):
+        for v in range(7):
             check_spmv(M, A, dtype, x, kernel=L.KERNEL_TMA, variant=v)
     check_spmv(M, A, dtype, x, kernel=L.KERNEL_TMA)
     assert device_status() == 0
@@ -317,12 +317,15 @@ def test_tma_sizes_and_partial_group(dtype, n):
     M = to_gpu_matrix(A, dtype, 32, slot_map=False)
     x = synth.uniform_vector(A.n_cols, seed=5)
     check_spmv(M, A, dtype, x, kernel=L.KERNEL_TMA)
+    for v in (4, 5, 6):                                    # several whole groups per copy
+        check_spmv(M, A, dtype, x, kernel=L.KERNEL_TMA, variant=v)
     check_spmv(M, A, dtype, x)
     assert device_status() == 0
 
 
+@pytest.mark.parametrize("variant", [0, 4])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-def test_tma_bounded_wait_runs_out_then_next_launch_is_correct(dtype):
+def test_tma_bounded_wait_runs_out_then_next_launch_is_correct(dtype, variant):
     # the TMA kernel's waits are bounded: with a limit of one probe the first
     # wait of (nearly) every warp runs out before its bulk copy lands, the
     # kernel records RGCSR_STATUS_TIMEOUT, waits for its own copies in flight
@@ -334,12 +337,12 @@ def test_tma_bounded_wait_runs_out_then_next_launch_is_correct(dtype):
     xd = torch.from_numpy(x.astype(NP[dtype])).cuda()
     assert device_status() == 0
     y = torch.full((A.n_rows,), float("nan"), dtype=TT[dtype], device="cuda")
-    M.spmv(xd, out=y, kernel=L.KERNEL_TMA, wait_limit=1)
+    M.spmv(xd, out=y, kernel=L.KERNEL_TMA, variant=variant, wait_limit=1)
     torch.cuda.synchronize()
     assert device_status() == L.STATUS_TIMEOUT
     assert torch.isnan(y).any()                    # rows of the abandoned groups stay unwritten
     assert device_status() == 0                    # the read cleared the bit
-    check_spmv(M, A, dtype, x, kernel=L.KERNEL_TMA)
+    check_spmv(M, A, dtype, x, kernel=L.KERNEL_TMA, variant=variant)
     assert device_status() == 0
     with pytest.raises(L.RgCSRError):
         M.spmv(xd, out=y, kernel=L.KERNEL_TMA, wait_limit=-1)
@@ -532,8 +535,8 @@ def test_unknown_kernel_variants_rejected():
     A = ragged(300, 200, seed=2)
     M = to_gpu_matrix(A, "f32", 32)
     x = torch.zeros(A.n_cols, dtype=torch.float32, device="cuda")
-    for kw in (dict(kernel=L.KERNEL_LEAN, variant=3), dict(kernel=L.KERNEL_LEAN, variant=8),
-               dict(kernel=L.KERNEL_TMA, variant=4),
+    for kw in (dict(kernel=L.KERNEL_LEAN, variant=3), dict(kernel=L.KERNEL_LEAN, variant=9),
+               dict(kernel=L.KERNEL_TMA, variant=7),
                dict(kernel=L.KERNEL_LEAN, variant=-1)):
         with pytest.raises(L.RgCSRError) as e:
             M.spmv(x, **kw)

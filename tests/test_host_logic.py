@@ -173,7 +173,9 @@ def test_bench_headline_is_short_and_parses():
              "batched_512_f32": {"gbs": big, "speedup_vs_plain": 10.123456},
              "backward_b_k8_f32": {"backward_over_forward": 2.123456},
              "hyb": {k: {"rgcsr_speedup": 1.123456} for k in cases},
-             "ir_cg_poisson128": {"fp64_cg_ms": 50.123, "ms": 40.123},
+             "ir_cg_poisson128": {"fp64_cg_ms": 50.123, "ms": 40.123,
+                                  "inner_tol_sweep": {"1e-06": {"final_rel_residual": 1e-12,
+                                                                "speedup_vs_fp64_cg": 1.23456}}},
              "spmm_b_f32": {"k8": {"gflops": big}}}
     line = bench.headline(value=big, world=8, steps=300, warmup=10, ms_per_step=0.351234567, gflops=big,
                           launches=2400, clocks=clocks, roof=roof, e2e=e2e, cpu=cpu, cases=cases,
