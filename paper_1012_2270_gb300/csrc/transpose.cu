@@ -13,6 +13,8 @@
 // matrix is an ordinary RgCSR matrix built with rgcsr_plan / rgcsr_convert.
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace rgcsr {
 namespace {
 
@@ -214,48 +216,86 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
+// One element's two hash terms, added to (h1, h2).
+__device__ __forceinline__ void hash_add(unsigned long long b, int64_t i, unsigned long long &h1,
+                                         unsigned long long &h2) {
+    const unsigned long long k = (unsigned long long)(i + 1);
+    h1 += mix64(b ^ (k * 0x9E3779B97F4A7C15ull));
+    h2 += mix64(b + k * 0xD1B54A32D192ED03ull);
+}
+
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor_u64(v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+    for (int w = 0; w < kHashThreads / 32; ++w) t += sh[w];
+    __syncthreads();
+    return t;
+}
+
+// W: the value word (unsigned for 4-byte values, unsigned long long for
+// 8-byte ones).  Each thread takes 16-byte packs (4 or 2 elements) in a
+// grid-stride loop with kHashU packs loaded before they are used, then the
+// elements past the last whole pack; with a misaligned base every element
+// goes through the scalar loop.
+constexpr int kHashU = 4;
+
 template <typename W>
 __global__ void __launch_bounds__(kHashThreads)
 values_hash_kernel(const W *__restrict__ v, int64_t n, unsigned long long *__restrict__ state) {
-    __shared__ unsigned long long sh[2][kHashThreads / 32];
+    constexpr int E = 16 / (int)sizeof(W);            // elements per pack
+    using P = uint4;
+    __shared__ unsigned long long sh[kHashThreads / 32];
     __shared__ bool last;
     unsigned long long h1 = 0, h2 = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long b = (unsigned long long)v[i], k = (unsigned long long)(i + 1);
-        h1 += mix64(b ^ (k * 0x9E3779B97F4A7C15ull));
-        h2 += mix64(b + k * 0xD1B54A32D192ED03ull);
-    }
+    const int64_t S = (int64_t)gridDim.x * blockDim.x, tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool vec = ((uintptr_t)v & 15) == 0;
+    const int64_t np = vec ? n / E : 0;
+#pragma unroll 1
+    for (int64_t p0 = tid; p0 < np; p0 += kHashU * S) {
+        P pk[kHashU];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        h1 += shfl_xor_u64(h1, o);
-        h2 += shfl_xor_u64(h2, o);
+        for (int u = 0; u < kHashU; ++u)
+            if (p0 + u * S < np) pk[u] = __ldcs(reinterpret_cast<const P *>(v) + p0 + u * S);
+#pragma unroll
+        for (int u = 0; u < kHashU; ++u)
+            if (p0 + u * S < np) {
+                const int64_t e0 = (p0 + u * S) * E;
+                if constexpr (E == 4) {
+                    hash_add(pk[u].x, e0, h1, h2);
+                    hash_add(pk[u].y, e0 + 1, h1, h2);
+                    hash_add(pk[u].z, e0 + 2, h1, h2);
+                    hash_add(pk[u].w, e0 + 3, h1, h2);
+                } else {
+                    hash_add(((unsigned long long)pk[u].y << 32) | pk[u].x, e0, h1, h2);
+                    hash_add(((unsigned long long)pk[u].w << 32) | pk[u].z, e0 + 1, h1, h2);
+                }
+            }
     }
-    if ((threadIdx.x & 31) == 0) {
-        sh[0][threadIdx.x >> 5] = h1;
-        sh[1][threadIdx.x >> 5] = h2;
-    }
-    __syncthreads();
+    for (int64_t i = np * E + tid; i < n; i += S) hash_add((unsigned long long)v[i], i, h1, h2);
+    h1 = block_sum_u64(h1, sh);
+    h2 = block_sum_u64(h2, sh);
     unsigned long long *part = state + 8;               // [kHashParts] h1, then [kHashParts] h2
     unsigned *ticket = reinterpret_cast<unsigned *>(state + 2);
     if (threadIdx.x == 0) {
-        unsigned long long b1 = 0, b2 = 0;
-        for (int w = 0; w < kHashThreads / 32; ++w) {
-            b1 += sh[0][w];
-            b2 += sh[1][w];
-        }
-        part[blockIdx.x] = b1;
-        part[kHashParts + blockIdx.x] = b2;
+        part[blockIdx.x] = h1;
+        part[kHashParts + blockIdx.x] = h2;
         __threadfence();
         last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
     __threadfence();
     unsigned long long t1 = 0, t2 = 0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
         t1 += __ldcg(part + b);
         t2 += __ldcg(part + kHashParts + b);
     }
+    t1 = block_sum_u64(t1, sh);
+    t2 = block_sum_u64(t2, sh);
+    if (threadIdx.x != 0) return;
     const bool held = (state[1] & 1ull) != 0;
     const bool changed = !held || state[0] != t1 || state[3] != t2;
     state[0] = t1;
@@ -282,6 +322,24 @@ __global__ void sampled_dot_kernel(int64_t nnz, int k, const int32_t *__restrict
         const T *x = X + (int64_t)col[p] * ldx;
         T s = 0;
         for (int b = 0; b < k; ++b) s = fma(__ldg(g + b), __ldg(x + b), s);
+        out[p] = s;
+    }
+}
+
+// The same for k == KC with 16-byte aligned rows of G and X: each row is
+// read with KC * sizeof(T) / 16 vector loads (load_xrow), and the products
+// are added in increasing b as above.
+template <typename T, int KC>
+__global__ void sampled_dot_vec_kernel(int64_t nnz, const int32_t *__restrict__ row_index,
+                                       const int32_t *__restrict__ col, const T *__restrict__ G, int64_t ldg,
+                                       const T *__restrict__ X, int64_t ldx, T *__restrict__ out) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        T g[KC], x[KC];
+        load_xrow<T, KC, true>(G + (int64_t)row_index[p] * ldg, g);
+        load_xrow<T, KC, true>(X + (int64_t)col[p] * ldx, x);
+        T s = 0;
+#pragma unroll
+        for (int b = 0; b < KC; ++b) s = fma(g[b], x[b], s);
         out[p] = s;
     }
 }
@@ -421,7 +479,9 @@ RGCSR_API int rgcsr_gather_values_if_changed(const rgcsr_matrix *M, const void *
     if (((uintptr_t)state & 7) != 0) return RGCSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     auto *st = static_cast<unsigned long long *>(state);
-    const unsigned g = grid_for(M->n_stored, 256);
+    // a grid-stride gather on a bounded grid: when nothing changed, each of
+    // its blocks only reads the flag and exits
+    const unsigned g = std::min<unsigned>(grid_for(M->n_stored, 256), 152u * 8u);
     if (M->value_type == RGCSR_F64) {
         values_hash_kernel<unsigned long long><<<kHashParts, kHashThreads, 0, s>>>(
             static_cast<const unsigned long long *>(src), n_src, st);
@@ -455,6 +515,24 @@ RGCSR_API int rgcsr_sampled_dot(int64_t nnz, int32_t k, const int32_t *row_index
     if (!row_index || !col_idx || !out || (k > 0 && (!G || !X))) return RGCSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned g = grid_for(nnz, 256);
+    const size_t es = value_type == RGCSR_F64 ? 8 : 4;
+    const bool vec = all_aligned16(G, X) && (ldg * es) % 16 == 0 && (ldx * es) % 16 == 0 &&
+                     (k == 8 || k == 4 || (k == 2 && es == 8));
+    if (vec && value_type == RGCSR_F32) {
+        const float *Gf = static_cast<const float *>(G), *Xf = static_cast<const float *>(X);
+        float *of = static_cast<float *>(out);
+        if (k == 8) sampled_dot_vec_kernel<float, 8><<<g, 256, 0, s>>>(nnz, row_index, col_idx, Gf, ldg, Xf, ldx, of);
+        else sampled_dot_vec_kernel<float, 4><<<g, 256, 0, s>>>(nnz, row_index, col_idx, Gf, ldg, Xf, ldx, of);
+        return launch_status();
+    }
+    if (vec && value_type == RGCSR_F64) {
+        const double *Gd = static_cast<const double *>(G), *Xd = static_cast<const double *>(X);
+        double *od = static_cast<double *>(out);
+        if (k == 8) sampled_dot_vec_kernel<double, 8><<<g, 256, 0, s>>>(nnz, row_index, col_idx, Gd, ldg, Xd, ldx, od);
+        else if (k == 4) sampled_dot_vec_kernel<double, 4><<<g, 256, 0, s>>>(nnz, row_index, col_idx, Gd, ldg, Xd, ldx, od);
+        else sampled_dot_vec_kernel<double, 2><<<g, 256, 0, s>>>(nnz, row_index, col_idx, Gd, ldg, Xd, ldx, od);
+        return launch_status();
+    }
     if (value_type == RGCSR_F64)
         sampled_dot_kernel<double><<<g, 256, 0, s>>>(nnz, k, row_index, col_idx, static_cast<const double *>(G),
                                                      ldg, static_cast<const double *>(X), ldx,

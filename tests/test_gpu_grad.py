@@ -238,3 +238,26 @@ def test_values_reloaded_only_when_they_change(dtype):
     trp, tc, perm = oracle.csr_transpose(A.rowptr, A.col, A.n_cols)
     dX_ref, dX_abs = oracle.csr_spmm(trp, tc, vals2[perm], np.ones((A.n_rows, 3)))
     assert_within_bound(Xg.grad.cpu().numpy(), dX_ref, dX_abs, TAU[dtype], "dX after other values")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("k,ld", [(2, 2), (4, 4), (8, 8), (8, 12), (4, 5), (3, 3)])
+def test_sampled_dot_against_oracle(dtype, k, ld):
+    # rgcsr_sampled_dot with 16-byte row loads (k = 2 for FP64, 4, 8 with
+    # aligned rows) and the scalar path (odd strides, k = 3): the same sums,
+    # in increasing b, as the oracle's value gradient
+    rng = np.random.default_rng(k * 10 + ld)
+    A = synth.random_csr(500, 400, rng.integers(0, 30, 500), seed=k)
+    rows = torch.tensor(np.repeat(np.arange(A.n_rows), np.diff(A.rowptr)).astype(np.int32), device="cuda")
+    cols = torch.tensor(A.col, device="cuda")
+    Gm = synth.uniform_matrix(A.n_rows, ld, seed=1).astype(NP[dtype])
+    Xm = synth.uniform_matrix(A.n_cols, ld, seed=2).astype(NP[dtype])
+    Gt, Xt = torch.tensor(Gm, device="cuda"), torch.tensor(Xm, device="cuda")
+    out = torch.empty(A.nnz, dtype=TT[dtype], device="cuda")
+    L.call("rgcsr_sampled_dot", A.nnz, k, _ptr(rows), _ptr(cols), _ptr(Gt), ld, _ptr(Xt), ld, _ptr(out),
+           L.F64 if dtype == "f64" else L.F32, _stream_ptr())
+    _, ref = oracle.spmm_grads(A.rowptr, A.col, A.val, Xm[:, :k].astype(np.float64),
+                               Gm[:, :k].astype(np.float64), A.n_cols)
+    _, absref = oracle.spmm_grads(A.rowptr, A.col, A.val, np.abs(Xm[:, :k]).astype(np.float64),
+                                  np.abs(Gm[:, :k]).astype(np.float64), A.n_cols)
+    assert_within_bound(out.cpu().numpy(), ref, absref, TAU[dtype], f"sampled dot k={k} ld={ld}")
