@@ -118,7 +118,7 @@ def kernel_name(cfg, M, A, dt):
     """The kernel that a configuration runs (the library's dispatch rules)."""
     t = "float" if dt == "f32" else "double"
     if "tiles" in cfg:
-        pipe = len(cfg["tiles"]) > 1 and cfg["tiles"][1] in (3, 4)
+        pipe = len(cfg["tiles"]) > 1 and cfg["tiles"][1] in (3, 4, 5)
         return f"rgcsr_spmv_tiles{'_pipe' if pipe else ''}_kernel<{t}>"
     if "long_rows" in cfg:
         return f"rgcsr_spmv_split+segments<{t}>"
@@ -966,7 +966,9 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None,
         for o in ops:
             o[0]._bench_y = torch.empty(b.n_rows, 8, device=dev)
         t_mm = per_call_us(spmm_only)
+        torch.cuda.nvtx.range_push("autograd_forward")            # a profiler can pick it out
         t_f = per_call_us(fwd)
+        torch.cuda.nvtx.range_pop()
         t_fb = per_call_us(fwd_bwd)
         forms["backward_b_k8_f32"] = {"group_size": G, "schedule": "descending row order, group tiles C=64",
                                       "spmm_us": t_mm, "forward_us": t_f, "forward_backward_us": t_fb,

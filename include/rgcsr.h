@@ -44,6 +44,7 @@ typedef struct CUstream_st *rgcsr_stream_t;   /* identical to cudaStream_t */
 #define RGCSR_ERR_CUDA              -6   /* a CUDA runtime call failed         */
 #define RGCSR_ERR_WORKSPACE         -7   /* workspace missing or too small     */
 #define RGCSR_ERR_BAD_PERM          -8   /* row_perm not a permutation of [0, n_rows) */
+#define RGCSR_ERR_CORRUPT           -9   /* an RgCSR matrix fails rgcsr_check_matrix */
 
 /* element types */
 #define RGCSR_F64  0
@@ -327,8 +328,9 @@ int rgcsr_spmv_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *S, const 
 typedef struct {
     int32_t tile;               /* slot-rows per task, >= 1                   */
     int32_t variant;            /* 0 = default; 1, 2: fewer / more slot-rows
-                                   in flight per lane; 3, 4: software-
-                                   pipelined across a warp's tiles (tuning)   */
+                                   in flight per lane; 3, 4, 5: software-
+                                   pipelined across a warp's tiles, 5 with
+                                   twice the slot-rows per step (tuning)      */
     int64_t n_groups;           /* (plan) the matrix's group count            */
     int64_t n_extra;            /* (plan) tasks beyond one per group          */
     int64_t n_split;            /* (plan) groups cut into more than one task  */
@@ -480,16 +482,15 @@ int rgcsr_gather_values(const rgcsr_matrix *M, const void *src, const int64_t *s
 /* rgcsr_gather_values, skipped when M already holds these values: `state`
  * is a caller-allocated device record of RGCSR_VALUES_STATE_BYTES bytes
  * (8-byte aligned), zero-filled before its first use ("holds nothing"),
- * one per matrix.  The call hashes src[0, n_src) -- two 64-bit sums over
- * the elements of a bijective mix (the SplitMix64 finalizer) of the
- * element's bits combined with its position, so any single changed element
- * changes the hash -- compares the hash with the one the record holds,
- * stores the new one, and gathers only if they differ or the record held
- * nothing; the decision is taken on the device (two launches, no host
+ * one per matrix.  The call hashes src[0, n_src) -- a 64-bit sum, over the
+ * 8-byte words of src's bytes, of a bijective mix (the SplitMix64
+ * finalizer) of each word combined with its position, so any single changed
+ * element changes the hash -- compares the hash with the one the record
+ * holds, stores the new one, and gathers only if they differ or the record
+ * held nothing; the decision is taken on the device (two launches, no host
  * synchronisation).  Several elements changed at once leave the hash
- * unchanged only by chance (both sums equal, about 2^-128); zero the
- * record to force a refresh.  One call per record in flight.  F64 or F32.
- * Async. */
+ * unchanged only by chance (about 2^-64); zero the record to force a
+ * refresh.  One call per record in flight.  F64 or F32.  Async. */
 #define RGCSR_VALUES_STATE_BYTES 8192
 int rgcsr_gather_values_if_changed(const rgcsr_matrix *M, const void *src, int64_t n_src,
                                    const int64_t *src_index, void *state, rgcsr_stream_t stream);
@@ -630,6 +631,50 @@ int hyb_spmm(const hyb_matrix *H, int32_t k, const void *X, int64_t ldx, void *Y
              rgcsr_stream_t stream);
 
 /* ----------------------------------------------------------------------- */
+/* Structural checks (a stand-in for a device memory checker)               */
+/* ----------------------------------------------------------------------- */
+/* rgcsr_check_matrix verifies on the device that M's arrays form the layout
+ * of Sec. 3.4 (see rgcsr_matrix), so that no kernel can index outside them.
+ * Each failed check sets its bit in report->flags:                          */
+#define RGCSR_CHECK_GROUP_PTR   1   /* group_ptr[0] != 0, group_ptr[n_groups] != n_stored, or a
+                                       group whose slab is not R_g * K_g slots (K_g: its longest row) */
+#define RGCSR_CHECK_ROW_LENGTHS 2   /* a row length < 0 or > max_row_len, or lengths not summing to nnz */
+#define RGCSR_CHECK_COLUMN      4   /* a slot inside its row's length with a column outside [0, n_cols) */
+#define RGCSR_CHECK_PADDING     8   /* a padding slot (past its row's length) whose value bits or
+                                       column are not 0 */
+#define RGCSR_CHECK_PERM       16   /* a row_perm entry outside [0, n_rows), or entries that are not a
+                                       permutation (a sum of hashed entries: a non-permutation passes
+                                       only by a 2^-64 chance) */
+#define RGCSR_CHECK_SCALE      32   /* BF16/F16 storage: row_scale NULL, or an entry not finite and > 0 */
+#define RGCSR_CHECK_SLOT_MAP   64   /* slot_to_csr (when not NULL): not -1 on a padding slot, or outside
+                                       [0, nnz) on a valid one */
+typedef struct {
+    int32_t flags;              /* RGCSR_CHECK_* bits of the failed checks, 0 = none */
+    int32_t reserved;
+    int64_t group;              /* lowest group failing RGCSR_CHECK_GROUP_PTR, else -1 */
+    int64_t row;                /* lowest stored row failing a length, scale or permutation check, else -1 */
+    int64_t slot;               /* lowest slot failing a column, padding or slot-map check, else -1 */
+} rgcsr_check_report;
+/* Every load of the check stays inside the sizes M declares (n_groups + 1,
+ * n_rows, n_stored), whatever the arrays hold.  Returns RGCSR_OK
+ * (report->flags == 0), RGCSR_ERR_CORRUPT, or RGCSR_ERR_INVALID_ARG /
+ * RGCSR_ERR_UNSUPPORTED_DTYPE for a malformed descriptor.  Synchronises
+ * `stream`; calls from several host threads are serialised (the library keeps
+ * one device record). */
+int rgcsr_check_matrix(const rgcsr_matrix *M, rgcsr_check_report *report, rgcsr_stream_t stream);
+/* Checks mode, on with rgcsr_set_checks(1) or RGCSR_CHECKS=1 in the
+ * environment when the library loads: every product on an rgcsr_matrix
+ * (rgcsr_spmv, rgcsr_spmv_ex, rgcsr_spmv_host, rgcsr_spmv_long_rows,
+ * rgcsr_spmv_tiles, rgcsr_spmv_xwindow, rgcsr_spmm, rgcsr_spmm_long_rows,
+ * rgcsr_spmm_tiles, rgcsr_spmv_bwd_values, rgcsr_cg, rgcsr_ir_cg) first runs
+ * rgcsr_check_matrix on it; if that fails, the product returns
+ * RGCSR_ERR_CORRUPT without launching anything and RGCSR_STATUS_CORRUPT joins
+ * the status bits.  The check synchronises the stream, so the mode is for
+ * debugging; on a stream being captured into a CUDA graph it is skipped.
+ * Returns the previous setting. */
+int rgcsr_set_checks(int on);
+
+/* ----------------------------------------------------------------------- */
 /* Misc                                                                     */
 /* ----------------------------------------------------------------------- */
 /* Device-side error bits, sticky until read: RGCSR_STATUS_TIMEOUT means a
@@ -637,6 +682,9 @@ int hyb_spmm(const hyb_matrix *H, int32_t k, const void *X, int64_t ldx, void *Y
  * its output unwritten.  rgcsr_get_status copies the bits of the current
  * device to *status_out and clears them; synchronises `stream`. */
 #define RGCSR_STATUS_TIMEOUT 1
+/* RGCSR_STATUS_CORRUPT: in checks mode (below) a product refused a matrix
+ * that failed rgcsr_check_matrix. */
+#define RGCSR_STATUS_CORRUPT 2
 int rgcsr_get_status(int *status_out, rgcsr_stream_t stream);
 const char *rgcsr_status_string(int status);
 /* Library version as major*10000 + minor*100 + patch. */

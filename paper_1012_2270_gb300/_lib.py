@@ -20,11 +20,14 @@ RGCSR_ERR_UNSUPPORTED_DTYPE = -5
 RGCSR_ERR_CUDA = -6
 RGCSR_ERR_WORKSPACE = -7
 RGCSR_ERR_BAD_PERM = -8
+RGCSR_ERR_CORRUPT = -9
 
 F64, F32, BF16, F16, I32T, I64T = 0, 1, 2, 3, 4, 5
 
 KERNEL_AUTO, KERNEL_PAPER, KERNEL_SPLIT, KERNEL_TMA, KERNEL_LEAN, KERNEL_SELL = 0, 1, 2, 3, 4, 5
-STATUS_TIMEOUT = 1
+STATUS_TIMEOUT, STATUS_CORRUPT = 1, 2
+CHECK_GROUP_PTR, CHECK_ROW_LENGTHS, CHECK_COLUMN, CHECK_PADDING = 1, 2, 4, 8
+CHECK_PERM, CHECK_SCALE, CHECK_SLOT_MAP = 16, 32, 64
 XLOAD_NC, XLOAD_PLAIN, XLOAD_TEX = 0, 1, 2
 XWINDOW_ROWS, XWINDOW_MAX_RANGES, XWINDOW_GAP, XWINDOW_CAP_BYTES = 256, 4, 64, 32768
 VALUES_STATE_BYTES = 8192
@@ -69,6 +72,10 @@ class Tiles(ctypes.Structure):
 
 class XWindow(ctypes.Structure):
     _fields_ = [("n_ranges", I32), ("total", I32), ("lo", I32 * 4), ("len", I32 * 4)]
+
+
+class CheckReport(ctypes.Structure):
+    _fields_ = [("flags", I32), ("reserved", I32), ("group", I64), ("row", I64), ("slot", I64)]
 
 
 class BatchDesc(ctypes.Structure):
@@ -142,6 +149,8 @@ SIGNATURES = {
     "hyb_convert": (ctypes.c_int, [_PCSR, _PH, P, SZ, P]),
     "hyb_spmv": (ctypes.c_int, [_PH, P, P, P]),
     "hyb_spmm": (ctypes.c_int, [_PH, I32, P, I64, P, I64, P]),
+    "rgcsr_check_matrix": (ctypes.c_int, [_PM, ctypes.POINTER(CheckReport), P]),
+    "rgcsr_set_checks": (ctypes.c_int, [ctypes.c_int]),
     "rgcsr_get_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), P]),
     "rgcsr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rgcsr_version": (ctypes.c_int, []),

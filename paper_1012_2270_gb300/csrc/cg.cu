@@ -326,6 +326,7 @@ RGCSR_API int rgcsr_cg(const rgcsr_matrix *A, const void *b, void *x, double rel
     const int vt = vector_type(A);
     if (!workspace || workspace_bytes < cg_bytes(A->n_rows, vt)) return RGCSR_ERR_WORKSPACE;
     CgScratch c = carve_cg(workspace, A->n_rows, vt);
+    if (const int cst = debug_check(A, (cudaStream_t)stream)) return cst;   // checks mode
     int its = 0;
     double rel = 0.0;
     const int st = vt == RGCSR_F64
@@ -359,6 +360,8 @@ RGCSR_API int rgcsr_ir_cg(const rgcsr_matrix *A_hi, const rgcsr_matrix *A_lo, co
     if (!b || !x) return RGCSR_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < rgcsr_ir_cg_workspace_bytes(n)) return RGCSR_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
+    if (const int cst = debug_check(A_hi, s)) return cst;   // checks mode
+    if (const int cst = debug_check(A_lo, s)) return cst;
     char *p = static_cast<char *>(workspace);
     double *r64 = reinterpret_cast<double *>(p); p += align_up((size_t)n * 8, 256);
     double *d64 = reinterpret_cast<double *>(p); p += align_up((size_t)n * 8, 256);

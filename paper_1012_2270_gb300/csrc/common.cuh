@@ -55,6 +55,14 @@ inline bool all_aligned16() { return true; }
 template <typename P, typename... R>
 inline bool all_aligned16(P p, R... r) { return ((uintptr_t)p & 15) == 0 && all_aligned16(r...); }
 
+// The SplitMix64 finalizer (Steele, Lea and Flood 2014; constants as
+// published): a bijection of 64-bit words that scatters every input bit.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 __device__ __forceinline__ int warp_max_i(int v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
@@ -184,6 +192,13 @@ int launch_validate_csr(const rgcsr_csr *A, int *flags, int64_t *max_len, cudaSt
 int launch_row_lengths(const rgcsr_csr *A, const int32_t *perm, int32_t *row_lengths, cudaStream_t s);
 // sets bit 4 of *flags unless perm is a permutation of [0, n); seen: n ints of scratch
 int launch_check_perm(const int32_t *perm, int64_t n, int32_t *seen, int *flags, cudaStream_t s);
+
+// Checks mode (check.cu): RGCSR_OK when it is off, when `s` is being
+// captured, or when M passes rgcsr_check_matrix; else RGCSR_ERR_CORRUPT
+// (and RGCSR_STATUS_CORRUPT is raised).  Products call it before any launch.
+int debug_check(const rgcsr_matrix *M, cudaStream_t s);
+// Status bits raised on the host since the last call (rgcsr_get_status).
+int take_host_status();
 
 // Sum of v over the block (blockDim.x a multiple of 32, <= 1024); sh: 32
 // doubles of shared memory.  Every thread returns the total.

@@ -173,6 +173,7 @@ RGCSR_API int rgcsr_spmm(const rgcsr_matrix *M, int32_t k, const void *X, int64_
     if (!M->group_ptr || !M->row_lengths || (M->n_stored > 0 && (!M->values || !M->columns)))
         return RGCSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    if (const int cst = debug_check(M, s)) return cst;   // checks mode
     switch (M->value_type) {
         case RGCSR_F64:
             return spmm_t<double>(M, k, static_cast<const double *>(X), ldx, static_cast<double *>(Y), ldy, s);

@@ -240,6 +240,7 @@ RGCSR_API int rgcsr_spmm_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows 
     if (k == 1 && ldx == 1 && ldy == 1)      // one right-hand side: the SpMV path
         return L ? rgcsr_spmv_long_rows(M, L, X, Y, stream) : rgcsr_spmv(M, X, Y, stream);
     cudaStream_t s = (cudaStream_t)stream;
+    if (const int cst = debug_check(M, s)) return cst;   // checks mode
     switch (M->value_type) {
         case RGCSR_F64:
             return spmm_rows_t<double>(M, L, k, static_cast<const double *>(X), ldx, static_cast<double *>(Y), ldy,

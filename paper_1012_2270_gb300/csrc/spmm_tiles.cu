@@ -185,6 +185,7 @@ RGCSR_API int rgcsr_spmm_tiles(const rgcsr_matrix *M, const rgcsr_tiles *T, int3
     }
     if (k == 1 && ldx == 1 && ldy == 1) return rgcsr_spmv_tiles(M, T, X, Y, stream);   // the SpMV
     cudaStream_t s = (cudaStream_t)stream;
+    if (const int cst = debug_check(M, s)) return cst;   // checks mode
     switch (M->value_type) {
         case RGCSR_F64:
             return spmm_tiles_t<double>(M, T, k, static_cast<const double *>(X), ldx, static_cast<double *>(Y), ldy,

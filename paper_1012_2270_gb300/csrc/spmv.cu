@@ -686,6 +686,7 @@ RGCSR_API int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
     if (M->n_rows == 0) return RGCSR_OK;
     if (!y || (M->n_cols > 0 && !x)) return RGCSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    if (const int cst = debug_check(M, s)) return cst;   // checks mode
     int kernel = launch ? launch->kernel : RGCSR_KERNEL_AUTO;
     int variant = launch ? launch->variant : 0;
     // x read paths other than the read-only one are an ablation of the
@@ -827,6 +828,7 @@ RGCSR_API int rgcsr_spmv_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows 
                               !S->long_count || !S->partials || !S->arrivals))
         return RGCSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    if (const int cst = debug_check(M, s)) return cst;   // checks mode
     switch (M->value_type) {
         case RGCSR_F64:
             return launch_long_rows<double>(M, S, static_cast<const double *>(x), static_cast<double *>(y), s);

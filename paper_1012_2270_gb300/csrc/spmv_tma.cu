@@ -607,5 +607,6 @@ RGCSR_API int rgcsr_get_status(int *status_out, rgcsr_stream_t stream) {
     RGCSR_CUDA_TRY(cudaMemcpyToSymbolAsync(g_spmv_status, &zero, sizeof(int), 0,
                                            cudaMemcpyHostToDevice, s));
     RGCSR_CUDA_TRY(cudaStreamSynchronize(s));
+    *status_out |= take_host_status();
     return RGCSR_OK;
 }

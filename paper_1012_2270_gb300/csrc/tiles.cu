@@ -311,12 +311,13 @@ int launch_tiles(const rgcsr_matrix *M, const rgcsr_tiles *T, const typename VT<
     const int64_t n_tasks = M->n_groups + T->n_extra;
     // slot-rows in flight per lane (U) and CTAs per SM by variant:
     // 0: U = 8 (FP64: 4), 5 CTAs;  1: U = 4 (FP64: 2), 6 CTAs;  2: U = 16 (FP64: 8), 4 CTAs;
-    // 3, 4: software-pipelined, U = 4 (FP64: 2) with 4 CTAs, U = 8 (FP64: 4) with 3 CTAs
+    // 3, 4: software-pipelined, U = 4 (FP64: 2) with 4 CTAs, U = 8 (FP64: 4) with 3 CTAs;
+    // 5: software-pipelined, U = 16 (FP64: 8) with 2 CTAs
     constexpr int U0 = sizeof(A) == 8 ? 4 : 8;
     void (*kern)(int64_t, int32_t, int32_t, int64_t, int64_t, const V *, const int32_t *, const int64_t *,
                  const int32_t *, const float *, const int64_t *, const int64_t *, const int32_t *, int32_t *,
                  A *, const A *, A *, const int32_t *);
-    static int cache[5][64];
+    static int cache[6][64];
     int *cc;
     switch (T->variant) {
         case 0: kern = rgcsr_spmv_tiles_kernel<V, U0, 5>; cc = cache[0]; break;
@@ -324,6 +325,7 @@ int launch_tiles(const rgcsr_matrix *M, const rgcsr_tiles *T, const typename VT<
         case 2: kern = rgcsr_spmv_tiles_kernel<V, 2 * U0, 4>; cc = cache[2]; break;
         case 3: kern = rgcsr_spmv_tiles_pipe_kernel<V, U0 / 2, 4>; cc = cache[3]; break;
         case 4: kern = rgcsr_spmv_tiles_pipe_kernel<V, U0, 3>; cc = cache[4]; break;
+        case 5: kern = rgcsr_spmv_tiles_pipe_kernel<V, 2 * U0, 2>; cc = cache[5]; break;
         default: return RGCSR_ERR_INVALID_ARG;
     }
     int64_t grid = resident_ctas(kern, cc);                                 // persistent
@@ -407,6 +409,7 @@ RGCSR_API int rgcsr_spmv_tiles(const rgcsr_matrix *M, const rgcsr_tiles *T, cons
     if (T->n_extra > 0 && (!T->first_extra || !T->part_base || !T->extra_group || !T->arrivals || !T->partials))
         return RGCSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    if (const int cst = debug_check(M, s)) return cst;   // checks mode
     switch (M->value_type) {
         case RGCSR_F64:
             return launch_tiles<double>(M, T, static_cast<const double *>(x), static_cast<double *>(y), s);

@@ -190,38 +190,27 @@ __global__ void gather_if_kernel(const V *__restrict__ src, const int64_t *__res
     }
 }
 
-// Hash of n value words, two 64-bit sums
-//   h1 = sum_i mix(b_i ^ ((i + 1) K1)),  h2 = sum_i mix(b_i + (i + 1) K2)  (mod 2^64)
-// with b_i the bits of element i and mix the SplitMix64 finalizer (Steele,
-// Lea and Flood 2014; constants as published), a bijection of 64-bit words.
-// Because mix is a bijection, changing any one element always changes both
-// sums; several elements changed at once leave a sum unchanged only by
-// chance, since mix destroys the structure a common change of bits (e.g.
-// every value scaled by one factor) would otherwise carry into the sums.
-// The sums are exact modular arithmetic, so they do not depend on the order
-// of the additions.  The last block to finish (a ticket after a fence) adds
-// the block sums and updates the state record: words 0 and 3 the hash,
-// word 1 bit 0 "holds values", bit 1 "changed by this call".
-constexpr int kHashParts = 304;
+// Hash of n values of ES bytes (2, 4 or 8), one 64-bit sum over the 64-bit
+// words of their bytes (little-endian; the last word zero-filled past the
+// end):
+//     h = sum_j mix(w_j ^ ((j + 1) K))   (mod 2^64),   K = 0x9E3779B97F4A7C15
+// with mix the SplitMix64 finalizer (Steele, Lea and Flood 2014; constants
+// as published), a bijection of 64-bit words, so changing any one value
+// always changes h; several values changed at once leave it unchanged only
+// by chance (about 2^-64), since mix destroys the structure a common change
+// of bits (e.g. every value scaled by one factor) would otherwise carry into
+// the sum.  One mix per 8 bytes keeps the kernel at the read rate.  The sum
+// is exact modular arithmetic, so it does not depend on the order of the
+// additions.  The last block to finish (a ticket after a fence) adds the
+// block sums and updates the state record: word 0 the hash, word 1 bit 0
+// "holds values", bit 1 "changed by this call".
+constexpr int kHashParts = 608;          // 4 blocks per SM
 constexpr int kHashThreads = 256;
+constexpr unsigned long long kHashK = 0x9E3779B97F4A7C15ull;
 
 __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int o) {
     const unsigned lo = __shfl_xor_sync(kFull, (unsigned)v, o), hi = __shfl_xor_sync(kFull, (unsigned)(v >> 32), o);
     return ((unsigned long long)hi << 32) | lo;
-}
-
-__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-// One element's two hash terms, added to (h1, h2).
-__device__ __forceinline__ void hash_add(unsigned long long b, int64_t i, unsigned long long &h1,
-                                         unsigned long long &h2) {
-    const unsigned long long k = (unsigned long long)(i + 1);
-    h1 += mix64(b ^ (k * 0x9E3779B97F4A7C15ull));
-    h2 += mix64(b + k * 0xD1B54A32D192ED03ull);
 }
 
 __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long *sh) {
@@ -235,71 +224,74 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
     return t;
 }
 
-// W: the value word (unsigned for 4-byte values, unsigned long long for
-// 8-byte ones).  Each thread takes 16-byte packs (4 or 2 elements) in a
-// grid-stride loop with kHashU packs loaded before they are used, then the
-// elements past the last whole pack; with a misaligned base every element
-// goes through the scalar loop.
+// Word j assembled from its values (each loaded at its own alignment).
+template <int ES>
+__device__ __forceinline__ unsigned long long hash_word(const void *v, int64_t n, int64_t j) {
+    constexpr int PER = 8 / ES;
+    unsigned long long w = 0;
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+        const int64_t i = j * PER + e;
+        if (i < n) {
+            unsigned long long b;
+            if constexpr (ES == 8) b = static_cast<const unsigned long long *>(v)[i];
+            else if constexpr (ES == 4) b = static_cast<const unsigned *>(v)[i];
+            else b = static_cast<const unsigned short *>(v)[i];
+            w |= b << (8 * ES * e);
+        }
+    }
+    return w;
+}
+
+// Each thread takes 16-byte packs (words 2p, 2p + 1) in a grid-stride loop
+// with kHashU packs loaded before they are used, then the words past the
+// last whole pack; with a base that is not 16-byte aligned every word is
+// assembled from its values.
 constexpr int kHashU = 4;
 
-template <typename W>
+template <int ES>
 __global__ void __launch_bounds__(kHashThreads)
-values_hash_kernel(const W *__restrict__ v, int64_t n, unsigned long long *__restrict__ state) {
-    constexpr int E = 16 / (int)sizeof(W);            // elements per pack
-    using P = uint4;
+values_hash_kernel(const void *__restrict__ v, int64_t n, unsigned long long *__restrict__ state) {
     __shared__ unsigned long long sh[kHashThreads / 32];
     __shared__ bool last;
-    unsigned long long h1 = 0, h2 = 0;
+    unsigned long long h = 0;
     const int64_t S = (int64_t)gridDim.x * blockDim.x, tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool vec = ((uintptr_t)v & 15) == 0;
-    const int64_t np = vec ? n / E : 0;
+    const int64_t bytes = n * ES, words = (bytes + 7) / 8;
+    const int64_t np = ((uintptr_t)v & 15) == 0 ? bytes / 16 : 0;
 #pragma unroll 1
     for (int64_t p0 = tid; p0 < np; p0 += kHashU * S) {
-        P pk[kHashU];
+        uint4 pk[kHashU];
 #pragma unroll
         for (int u = 0; u < kHashU; ++u)
-            if (p0 + u * S < np) pk[u] = __ldcs(reinterpret_cast<const P *>(v) + p0 + u * S);
+            if (p0 + u * S < np) pk[u] = __ldcs(static_cast<const uint4 *>(v) + p0 + u * S);
 #pragma unroll
         for (int u = 0; u < kHashU; ++u)
             if (p0 + u * S < np) {
-                const int64_t e0 = (p0 + u * S) * E;
-                if constexpr (E == 4) {
-                    hash_add(pk[u].x, e0, h1, h2);
-                    hash_add(pk[u].y, e0 + 1, h1, h2);
-                    hash_add(pk[u].z, e0 + 2, h1, h2);
-                    hash_add(pk[u].w, e0 + 3, h1, h2);
-                } else {
-                    hash_add(((unsigned long long)pk[u].y << 32) | pk[u].x, e0, h1, h2);
-                    hash_add(((unsigned long long)pk[u].w << 32) | pk[u].z, e0 + 1, h1, h2);
-                }
+                const unsigned long long k0 = (unsigned long long)(2 * (p0 + u * S) + 1) * kHashK;
+                h += mix64((((unsigned long long)pk[u].y << 32) | pk[u].x) ^ k0);
+                h += mix64((((unsigned long long)pk[u].w << 32) | pk[u].z) ^ (k0 + kHashK));
             }
     }
-    for (int64_t i = np * E + tid; i < n; i += S) hash_add((unsigned long long)v[i], i, h1, h2);
-    h1 = block_sum_u64(h1, sh);
-    h2 = block_sum_u64(h2, sh);
-    unsigned long long *part = state + 8;               // [kHashParts] h1, then [kHashParts] h2
+    for (int64_t j = 2 * np + tid; j < words; j += S)
+        h += mix64(hash_word<ES>(v, n, j) ^ ((unsigned long long)(j + 1) * kHashK));
+    h = block_sum_u64(h, sh);
+    unsigned long long *part = state + 8;               // [kHashParts] block sums
     unsigned *ticket = reinterpret_cast<unsigned *>(state + 2);
     if (threadIdx.x == 0) {
-        part[blockIdx.x] = h1;
-        part[kHashParts + blockIdx.x] = h2;
+        part[blockIdx.x] = h;
         __threadfence();
         last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    unsigned long long t1 = 0, t2 = 0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-        t1 += __ldcg(part + b);
-        t2 += __ldcg(part + kHashParts + b);
-    }
-    t1 = block_sum_u64(t1, sh);
-    t2 = block_sum_u64(t2, sh);
+    unsigned long long t = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(part + b);
+    t = block_sum_u64(t, sh);
     if (threadIdx.x != 0) return;
     const bool held = (state[1] & 1ull) != 0;
-    const bool changed = !held || state[0] != t1 || state[3] != t2;
-    state[0] = t1;
-    state[3] = t2;
+    const bool changed = !held || state[0] != t;
+    state[0] = t;
     state[1] = 1ull | (changed ? 2ull : 0ull);
     *ticket = 0u;
 }
@@ -472,7 +464,7 @@ RGCSR_API int rgcsr_gather_values(const rgcsr_matrix *M, const void *src, const 
 
 RGCSR_API int rgcsr_gather_values_if_changed(const rgcsr_matrix *M, const void *src, int64_t n_src,
                                              const int64_t *src_index, void *state, rgcsr_stream_t stream) {
-    static_assert(8 * (8 + 2 * kHashParts) <= RGCSR_VALUES_STATE_BYTES, "state record too small");
+    static_assert(8 * (8 + kHashParts) <= RGCSR_VALUES_STATE_BYTES, "state record too small");
     if (!M || M->n_stored < 0 || n_src < 0 || !state) return RGCSR_ERR_INVALID_ARG;
     if (M->value_type != RGCSR_F64 && M->value_type != RGCSR_F32) return RGCSR_ERR_UNSUPPORTED_DTYPE;
     if ((n_src > 0 && !src) || (M->n_stored > 0 && (!M->values || !src_index))) return RGCSR_ERR_INVALID_ARG;
@@ -483,14 +475,12 @@ RGCSR_API int rgcsr_gather_values_if_changed(const rgcsr_matrix *M, const void *
     // its blocks only reads the flag and exits
     const unsigned g = std::min<unsigned>(grid_for(M->n_stored, 256), 152u * 8u);
     if (M->value_type == RGCSR_F64) {
-        values_hash_kernel<unsigned long long><<<kHashParts, kHashThreads, 0, s>>>(
-            static_cast<const unsigned long long *>(src), n_src, st);
+        values_hash_kernel<8><<<kHashParts, kHashThreads, 0, s>>>(src, n_src, st);
         if (M->n_stored > 0)
             gather_if_kernel<double><<<g, 256, 0, s>>>(static_cast<const double *>(src), src_index, M->n_stored,
                                                        static_cast<double *>(M->values), st + 1);
     } else {
-        values_hash_kernel<unsigned><<<kHashParts, kHashThreads, 0, s>>>(static_cast<const unsigned *>(src),
-                                                                       n_src, st);
+        values_hash_kernel<4><<<kHashParts, kHashThreads, 0, s>>>(src, n_src, st);
         if (M->n_stored > 0)
             gather_if_kernel<float><<<g, 256, 0, s>>>(static_cast<const float *>(src), src_index, M->n_stored,
                                                       static_cast<float *>(M->values), st + 1);
@@ -585,6 +575,7 @@ RGCSR_API int rgcsr_spmv_bwd_values(const rgcsr_matrix *M, int32_t k, const void
     if (!M->group_ptr || !M->columns || !M->slot_to_csr || !dval || (k > 0 && (!G || !X)))
         return RGCSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    if (const int cst = debug_check(M, s)) return cst;   // checks mode
     const unsigned g = grid_for(M->n_groups * 32, 256);
     if (M->value_type == RGCSR_F64)
         bwd_values_kernel<double><<<g, 256, 0, s>>>(M->n_rows, M->group_size, M->n_groups, M->group_ptr, M->columns,

@@ -304,6 +304,7 @@ RGCSR_API int rgcsr_spmv_xwindow(const rgcsr_matrix *M, const rgcsr_xwindow *win
     if (M->n_rows == 0) return RGCSR_OK;
     if (!windows || !y || (M->n_cols > 0 && !x)) return RGCSR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    if (const int cst = debug_check(M, s)) return cst;   // checks mode
     switch (M->value_type) {
         case RGCSR_F64: return launch_xwindow<double>(M, windows, x, y, s);
         case RGCSR_F32: return launch_xwindow<float>(M, windows, x, y, s);

@@ -17,6 +17,25 @@ from . import _lib as L
 _VT = {torch.float64: L.F64, torch.float32: L.F32}
 
 
+# rgcsr_check_matrix's checks: (name, RGCSR_CHECK_* bit)
+CHECKS = (("group_ptr", L.CHECK_GROUP_PTR), ("row_lengths", L.CHECK_ROW_LENGTHS), ("column", L.CHECK_COLUMN),
+          ("padding", L.CHECK_PADDING), ("perm", L.CHECK_PERM), ("scale", L.CHECK_SCALE),
+          ("slot_map", L.CHECK_SLOT_MAP))
+
+
+def set_checks(on: bool) -> bool:
+    """Checks mode (rgcsr_set_checks): every product checks its matrix
+    first and refuses a corrupt one.  Returns the previous setting."""
+    return bool(L.lib().rgcsr_set_checks(1 if on else 0))
+
+
+def get_status(stream=None) -> int:
+    """The library's sticky status bits (rgcsr_get_status), cleared by the read."""
+    st = ctypes.c_int(0)
+    L.call("rgcsr_get_status", ctypes.byref(st), _stream_ptr(stream))
+    return st.value
+
+
 def _stream_ptr(stream=None) -> ctypes.c_void_p:
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -231,6 +250,17 @@ class RgCSRMatrix:
         elif other._long is not None:
             self.split_long_rows(other._long[0].threshold, other._long[0].segment)
         return self
+
+    def check(self, stream=None) -> dict:
+        """The library's structural checks of the stored layout
+        (rgcsr_check_matrix): {"ok", "flags" (names of the failed checks),
+        "group", "row", "slot" (the lowest failing ones, -1 = none)}."""
+        rep = L.CheckReport()
+        st = L.lib().rgcsr_check_matrix(ctypes.byref(self.s), ctypes.byref(rep), _stream_ptr(stream))
+        if st not in (L.RGCSR_OK, L.RGCSR_ERR_CORRUPT):
+            raise L.RgCSRError("rgcsr_check_matrix", st)
+        return {"ok": st == L.RGCSR_OK, "flags": [n for n, b in CHECKS if rep.flags & b],
+                "group": rep.group, "row": rep.row, "slot": rep.slot}
 
     def plan_x_window(self, stream=None) -> "RgCSRMatrix":
         """Plans the shared-memory x window of every block of 256 stored rows

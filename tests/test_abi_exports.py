@@ -111,6 +111,20 @@ def _argument_checks():
     M64 = L.Matrix(n_rows=4, n_cols=4, group_size=64, n_groups=1, value_type=L.F32, group_ptr=8, row_lengths=8)
     T = L.Tiles(**full)
     assert lib.rgcsr_spmv_tiles(ctypes.byref(M64), ctypes.byref(T), 8, 8, None) == L.RGCSR_ERR_INVALID_ARG
+    # structural checks: descriptor errors come before any device work
+    rep = L.CheckReport(flags=99)
+    assert lib.rgcsr_check_matrix(None, ctypes.byref(rep), None) == L.RGCSR_ERR_INVALID_ARG
+    assert lib.rgcsr_check_matrix(ctypes.byref(M2), None, None) == L.RGCSR_ERR_INVALID_ARG
+    M3 = L.Matrix(n_rows=4, n_cols=4, group_size=32, n_groups=2, value_type=L.F32, group_ptr=8, row_lengths=8)
+    assert lib.rgcsr_check_matrix(ctypes.byref(M3), ctypes.byref(rep), None) == L.RGCSR_ERR_INVALID_ARG
+    M4 = L.Matrix(n_rows=4, n_cols=4, group_size=32, n_groups=1, value_type=L.I32T, group_ptr=8, row_lengths=8)
+    assert lib.rgcsr_check_matrix(ctypes.byref(M4), ctypes.byref(rep), None) == L.RGCSR_ERR_UNSUPPORTED_DTYPE
+    assert lib.rgcsr_check_matrix(ctypes.byref(M0), ctypes.byref(rep), None) == L.RGCSR_OK
+    assert (rep.flags, rep.group, rep.row, rep.slot) == (0, -1, -1, -1)
+    # checks mode: the switch returns the previous setting
+    prev = lib.rgcsr_set_checks(1)
+    assert lib.rgcsr_set_checks(0) == 1
+    assert lib.rgcsr_set_checks(prev) == 0
 
 
 def test_argument_errors_without_gpu():
@@ -134,7 +148,7 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
 # ctypes mirror -> C typedef of include/rgcsr.h
 STRUCTS = {"CSR": "rgcsr_csr", "Matrix": "rgcsr_matrix", "Launch": "rgcsr_launch", "Hyb": "hyb_matrix",
            "LongRows": "rgcsr_long_rows", "Tiles": "rgcsr_tiles", "BatchDesc": "rgcsr_batch_desc",
-           "Batch": "rgcsr_batch", "XWindow": "rgcsr_xwindow"}
+           "Batch": "rgcsr_batch", "XWindow": "rgcsr_xwindow", "CheckReport": "rgcsr_check_report"}
 
 
 def declared_structs():

@@ -241,6 +241,54 @@ def test_values_reloaded_only_when_they_change(dtype):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_value_hash_sees_every_change(dtype, offset):
+    # the refresh decision itself (rgcsr_gather_values_if_changed's state
+    # record, word 1 bit 1 = changed by this call): a change of one element
+    # anywhere -- first, last (in the zero-filled last word when n is odd),
+    # an interior one, a sign, a single low bit -- and a swap of two unequal
+    # elements are all seen; an unchanged tensor is not.  offset = 1 starts
+    # the values off a 16-byte boundary (the word-by-word path).
+    rng = np.random.default_rng(21)
+    lengths = rng.integers(1, 9, 301)
+    lengths[0] += 1 - lengths.sum() % 2      # an odd count of values
+    A = synth.random_csr(301, 250, lengths, seed=21)
+    assert A.nnz % 2 == 1
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dtype]), A.n_cols, dtype=TT[dtype],
+                             keep_slot_map=True)
+    buf = torch.tensor(np.r_[np.zeros(offset), A.val].astype(NP[dtype]), device="cuda")
+    v = buf[offset:]
+    n = v.numel()
+    state = torch.zeros(L.VALUES_STATE_BYTES // 8, dtype=torch.int64, device="cuda")
+
+    def changed():
+        L.call("rgcsr_gather_values_if_changed", ctypes.byref(M.s), _ptr(v), n, _ptr(M.slot_to_csr),
+               _ptr(state), _stream_ptr())
+        return bool(state[1].item() & 2)
+
+    assert changed()                         # first call: the record held nothing
+    assert not changed()
+    ints = v.view(torch.int32 if dtype == "f32" else torch.int64)
+    for i in (0, 1, n // 2, n - 2, n - 1):
+        old = v[i].item()
+        v[i] = -old
+        assert changed(), i
+        assert not changed(), i
+        ints[i] ^= 1                         # the lowest bit
+        assert changed(), i
+        v[i] = old
+        assert changed(), i
+    i, j = 3, n - 4
+    assert v[i].item() != v[j].item()
+    vi, vj = v[i].item(), v[j].item()
+    v[i], v[j] = vj, vi
+    assert changed()
+    assert not changed()
+    v.mul_(2.0)                              # every element at once
+    assert changed()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
 @pytest.mark.parametrize("k,ld", [(2, 2), (4, 4), (8, 8), (8, 12), (4, 5), (3, 3)])
 def test_sampled_dot_against_oracle(dtype, k, ld):
     # rgcsr_sampled_dot with 16-byte row loads (k = 2 for FP64, 4, 8 with
