@@ -122,22 +122,14 @@ def kernel_name(cfg, M, A, dt):
         return f"rgcsr_spmv_tiles{'_pipe' if pipe else ''}_kernel<{t}>"
     if "long_rows" in cfg:
         return f"rgcsr_spmv_split+segments<{t}>"
-    k = cfg.get("kernel", 0)
-    if k == 4 and cfg.get("variant", 0) in (1, 2, 4, 8):
-        return f"rgcsr_spmv_vec<{t}>"
-    if k == 4 and cfg.get("variant", 0) in (5, 6, 7):
-        return f"rgcsr_spmv_vecp<{t}>"
+    k, v = cfg.get("kernel", 0), cfg.get("variant", 0)
     if k == 0:
-        n = A.n_rows
-        dense = (M.n_stored * 4 <= M.nnz * 5 and
-                 not (M.max_row_len > 64 and M.max_row_len * n > 8 * M.nnz))
-        if dense and M.group_size == 32 and A.nnz <= 8 * n:       # (device allocations are aligned)
-            return f"rgcsr_spmv_vec<{t}>"
-        if dense and M.group_size == 32 and n >= 32 and dt == "f32":
-            k = 3
-        else:
-            k = 4 if dense else 2
-    if k == 3 and cfg.get("variant", 0) >= 4:
+        k, v = M.auto_kernel()                  # the library's own rule
+    if k == 4 and v in (1, 2, 4, 8):
+        return f"rgcsr_spmv_vec<{t}>"
+    if k == 4 and v in (5, 6, 7):
+        return f"rgcsr_spmv_vecp<{t}>"
+    if k == 3 and v >= 4:
         return f"rgcsr_spmv_tma_multi<{t}>"
     return {1: "rgcsr_spmv_paper", 2: "rgcsr_spmv_split", 3: "rgcsr_spmv_tma", 4: "rgcsr_spmv_lean"}[k] + f"<{t}>"
 
@@ -833,7 +825,7 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None,
                 # kernel: the default, or (G = 32, no schedule) 16-byte loads, whichever is faster here
                 kws = [{}]
                 if Qs[0].group_size == 32 and Qs[0]._tiles is None and Qs[0]._long is None:
-                    kws += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4, 5, 6, 7, 8)]
+                    kws += [dict(kernel=L.KERNEL_LEAN, variant=v) for v in (1, 2, 4, 5, 6, 7, 8, 9)]
                     kws += [dict(kernel=L.KERNEL_TMA, variant=v) for v in (4, 5, 6)]
                 ts = {i: rotating_us([lambda Q=Q, xj=xj, y=y, k=k: Q.spmv(xj, out=y, **k)
                                       for Q, xj, y in zip(Qs, xs, ys)], stream)

@@ -45,6 +45,7 @@ typedef struct CUstream_st *rgcsr_stream_t;   /* identical to cudaStream_t */
 #define RGCSR_ERR_WORKSPACE         -7   /* workspace missing or too small     */
 #define RGCSR_ERR_BAD_PERM          -8   /* row_perm not a permutation of [0, n_rows) */
 #define RGCSR_ERR_CORRUPT           -9   /* an RgCSR matrix fails rgcsr_check_matrix */
+#define RGCSR_ERR_TIMEOUT          -10   /* a bounded device wait gave up (results invalid) */
 
 /* element types */
 #define RGCSR_F64  0
@@ -153,7 +154,9 @@ typedef struct {
                                    (a lane owns 16 / value size rows: F64 2,
                                    F32 4, BF16/F16 8), 2, 1 or 4 slot-rows per
                                    stage; 8 = as 1 with 8 slot-rows in flight
-                                   (a short row's whole slab at once);
+                                   (a short row's whole slab at once); 9 =
+                                   BF16/FP16 storage only: as 1 with six
+                                   blocks per SM;
                                    16-byte aligned values and columns; other
                                    kernels: 0                                     */
     int32_t wait_limit;         /* TMA kernel: non-blocking probes of a stage's
@@ -230,6 +233,11 @@ int rgcsr_plan_noalloc(const rgcsr_csr *A, rgcsr_matrix *M, rgcsr_stream_t strea
 int rgcsr_spmv(const rgcsr_matrix *M, const void *x, void *y, rgcsr_stream_t stream);
 int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
                   const rgcsr_launch *launch, rgcsr_stream_t stream);
+/* The kernel and variant that RGCSR_KERNEL_AUTO (and so rgcsr_spmv) runs
+ * for M, by the rule given at RGCSR_KERNEL_AUTO.  Host only: reads M's
+ * fields, not its arrays (whose addresses decide the 16-byte alignment
+ * condition).  RGCSR_ERR_INVALID_ARG for a malformed descriptor. */
+int rgcsr_auto_kernel(const rgcsr_matrix *M, int32_t *kernel, int32_t *variant);
 
 /* x staged in shared memory (the x read-path study of Sec. 4.3, not the
  * paper's kernel).  For every block of RGCSR_XWINDOW_ROWS consecutive stored
@@ -491,7 +499,7 @@ int rgcsr_gather_values(const rgcsr_matrix *M, const void *src, const int64_t *s
  * synchronisation).  Several elements changed at once leave the hash
  * unchanged only by chance (about 2^-64); zero the record to force a
  * refresh.  One call per record in flight.  F64 or F32.  Async. */
-#define RGCSR_VALUES_STATE_BYTES 8192
+#define RGCSR_VALUES_STATE_BYTES 16384
 int rgcsr_gather_values_if_changed(const rgcsr_matrix *M, const void *src, int64_t n_src,
                                    const int64_t *src_index, void *state, rgcsr_stream_t stream);
 /* out[s] = inner[outer[s]], or -1 where outer[s] < 0 (n entries).  Async. */
@@ -567,11 +575,21 @@ int rgcsr_fp64_fma_probe(int32_t iters, void *sink, int64_t *fmas, rgcsr_stream_
  * x = 0, stopping when ||r|| <= rel_tol ||b|| (the recurrence residual,
  * checked on the host every check_every iterations) or after max_iter
  * iterations.  Vectors are double for F64 storage, float otherwise.
+ * An iteration is the SpMV q = A d and one cooperative kernel (every block
+ * resident) for dq, alpha, x, r, rr', beta and d, with two grid barriers;
+ * where a cooperative launch is not possible, three kernels instead.  A
+ * barrier wait is bounded (rgcsr_set_wait_limit); one that gives up makes
+ * the call return RGCSR_ERR_TIMEOUT at its next check, with x invalid.
  * Writes *iterations and *rel_residual (host); synchronises `stream`. */
 size_t rgcsr_cg_workspace_bytes(int64_t n, int32_t value_type);
 int rgcsr_cg(const rgcsr_matrix *A, const void *b, void *x, double rel_tol, int32_t max_iter,
              int32_t check_every, void *workspace, size_t workspace_bytes, int32_t *iterations,
              double *rel_residual, rgcsr_stream_t stream);
+/* Polls before a grid barrier of rgcsr_cg / rgcsr_ir_cg gives up; 0 restores
+ * the default (about a second).  For tests of the timeout path: a barrier
+ * whose blocks are all resident ends in microseconds.  RGCSR_ERR_INVALID_ARG
+ * if polls < 0. */
+int rgcsr_set_wait_limit(int32_t polls);
 /* Mixed-precision iterative refinement: outer loop in FP64 (r = b - A_hi x
  * with the F64 matrix A_hi, stop when ||r|| <= outer_tol ||b|| or after
  * max_outer corrections), inner CG in float on A_lo (F32, BF16 or F16

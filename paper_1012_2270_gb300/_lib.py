@@ -21,6 +21,7 @@ RGCSR_ERR_CUDA = -6
 RGCSR_ERR_WORKSPACE = -7
 RGCSR_ERR_BAD_PERM = -8
 RGCSR_ERR_CORRUPT = -9
+RGCSR_ERR_TIMEOUT = -10
 
 F64, F32, BF16, F16, I32T, I64T = 0, 1, 2, 3, 4, 5
 
@@ -30,7 +31,7 @@ CHECK_GROUP_PTR, CHECK_ROW_LENGTHS, CHECK_COLUMN, CHECK_PADDING = 1, 2, 4, 8
 CHECK_PERM, CHECK_SCALE, CHECK_SLOT_MAP = 16, 32, 64
 XLOAD_NC, XLOAD_PLAIN, XLOAD_TEX = 0, 1, 2
 XWINDOW_ROWS, XWINDOW_MAX_RANGES, XWINDOW_GAP, XWINDOW_CAP_BYTES = 256, 4, 64, 32768
-VALUES_STATE_BYTES = 8192
+VALUES_STATE_BYTES = 16384
 
 
 class CSR(ctypes.Structure):
@@ -104,6 +105,7 @@ SIGNATURES = {
     "rgcsr_descending_order": (ctypes.c_int, [_PCSR, P, P, SZ, P]),
     "rgcsr_spmv": (ctypes.c_int, [_PM, P, P, P]),
     "rgcsr_spmv_ex": (ctypes.c_int, [_PM, P, P, _PL, P]),
+    "rgcsr_auto_kernel": (ctypes.c_int, [_PM, PI32, PI32]),
     "rgcsr_spmv_host": (ctypes.c_int, [_PM, P, P, P, P, _PL, ctypes.POINTER(LongRows),
                                        ctypes.POINTER(Tiles), P]),
     "rgcsr_tiles_workspace_bytes": (SZ, [I64]),
@@ -151,6 +153,7 @@ SIGNATURES = {
     "hyb_spmm": (ctypes.c_int, [_PH, I32, P, I64, P, I64, P]),
     "rgcsr_check_matrix": (ctypes.c_int, [_PM, ctypes.POINTER(CheckReport), P]),
     "rgcsr_set_checks": (ctypes.c_int, [ctypes.c_int]),
+    "rgcsr_set_wait_limit": (ctypes.c_int, [I32]),
     "rgcsr_get_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), P]),
     "rgcsr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rgcsr_version": (ctypes.c_int, []),

@@ -13,6 +13,7 @@ RGCSR_API const char *rgcsr_status_string(int status) {
         case RGCSR_ERR_WORKSPACE: return "workspace missing or too small";
         case RGCSR_ERR_BAD_PERM: return "row_perm is not a permutation of the rows";
         case RGCSR_ERR_CORRUPT: return "RgCSR matrix failed its structural checks";
+        case RGCSR_ERR_TIMEOUT: return "a bounded device wait gave up";
         default: return "unknown status";
     }
 }

@@ -14,6 +14,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 namespace rgcsr {
@@ -42,25 +43,6 @@ template <typename T>
 __device__ __forceinline__ void acc_dot(T a, T b, float &s, float &c, double &sd) {
     if constexpr (sizeof(T) == 4) dot2_step(a, b, s, c);
     else sd = fma((double)a, (double)b, sd);
-}
-
-// The block's partial (every thread passes its own) goes to parts; true in
-// the block that finishes last, whose threads then get the grand total.
-__device__ __forceinline__ bool reduce_last(double v, double *parts, unsigned *ticket, double *sh, double &total) {
-    __shared__ bool last;
-    const double b = block_sum(v, sh);
-    if (threadIdx.x == 0) {
-        parts[blockIdx.x] = b;
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    double t = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(parts + i);
-    total = block_sum(t, sh);
-    return true;
 }
 
 template <typename T, int W>
@@ -168,6 +150,180 @@ cg_d_kernel(int64_t n, const double *__restrict__ scal, const T *__restrict__ r,
     for (int64_t i = nw * W + tid; i < n; i += S) d[i] = fma(beta, d[i], r[i]);
 }
 
+// The same three steps as one cooperative kernel (every block resident),
+// with two grid barriers in place of the kernel boundaries:
+//   1. dq = d . q, block sums to parts[0, G);  barrier;  every block adds
+//      parts[0, G) in block order with the same tree, so all blocks hold the
+//      same dq, and alpha = rr / dq;
+//   2. x += alpha d, r -= alpha q, rr' = r . r, block sums to parts[G, 2G);
+//      barrier;  rr' and beta = rr' / rr likewise;
+//   3. d = r + beta d.
+// Each thread visits the same elements in every step (a grid-stride loop
+// over 16-byte packs), so what step 2 writes, step 3 reads back from its own
+// thread; the vectors are re-read from L2 rather than held.  Block 0 records
+// dq, alpha, rr' and beta in the scalar block as the three kernels do.  A
+// barrier is a counter in the scalar block: each block adds one and polls
+// (acquire loads, a short sleep between polls) until all have; a wait gives
+// up after wait_limit polls, sets the error word and its block returns, so
+// the caller sees RGCSR_ERR_TIMEOUT instead of a hang.  The last block to
+// leave resets the counters for the next launch.
+struct CoopWords {                  // in the scalar block at byte 72
+    unsigned arrive, leave;
+    int error;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// false (in every thread of the block) when the wait ran out
+__device__ __forceinline__ bool grid_barrier(CoopWords *w, unsigned target, unsigned limit) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&w->arrive, 1u);
+        int done = 0;
+        for (unsigned p = 0; p < limit; ++p) {
+            if (ld_acquire_gpu(&w->arrive) >= target) { done = 1; break; }
+            __nanosleep(32);
+        }
+        if (!done) atomicExch(&w->error, 1);
+        ok = done;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// the sum of parts[0, G) in block order, the same in every block
+__device__ __forceinline__ double sum_parts(const double *parts, double *sh) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(parts + b);
+    return block_sum(t, sh);
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads)
+cg_update_coop_kernel(int64_t n, T *__restrict__ x, T *__restrict__ r, T *__restrict__ d, const T *__restrict__ q,
+                      double *scal, int cur, double *parts, CoopWords *w, unsigned limit) {
+    __shared__ double sh[32];
+    const int64_t S = (int64_t)gridDim.x * blockDim.x, tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nw = n / W;
+    const unsigned G = gridDim.x;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    // 1. dq
+    float s = 0.0f, c = 0.0f;
+    double sd = 0.0;
+#pragma unroll 1
+    for (int64_t i0 = tid; i0 < nw; i0 += kU * S) {
+        Pack<T, W> dv[kU], qv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (i0 + u * S < nw) {
+                dv[u] = ld_pack<T, W>(d + (i0 + u * S) * W);
+                qv[u] = ld_pack<T, W>(q + (i0 + u * S) * W);
+            }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (i0 + u * S < nw) {
+#pragma unroll
+                for (int k = 0; k < W; ++k) acc_dot(dv[u].v[k], qv[u].v[k], s, c, sd);
+            }
+    }
+    for (int64_t i = nw * W + tid; i < n; i += S) acc_dot(d[i], q[i], s, c, sd);
+    double b = block_sum(sizeof(T) == 4 ? (double)s + (double)c : sd, sh);
+    if (threadIdx.x == 0) parts[blockIdx.x] = b;
+    if (!grid_barrier(w, G, limit)) return;
+    const double dq = sum_parts(parts, sh);
+    const double rr = scal[cur];
+    const T alpha = (T)(rr / dq);
+    if (lead) {
+        scal[2] = dq;
+        scal[3] = rr / dq;
+    }
+    // 2. x, r and rr'
+    s = c = 0.0f;
+    sd = 0.0;
+#pragma unroll 1
+    for (int64_t i0 = tid; i0 < nw; i0 += kU * S) {
+        Pack<T, W> xv[kU], rv[kU], dv[kU], qv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (i0 + u * S < nw) {
+                const int64_t i = i0 + u * S;
+                xv[u] = ld_pack<T, W>(x + i * W);
+                rv[u] = ld_pack<T, W>(r + i * W);
+                dv[u] = ld_pack<T, W>(d + i * W);
+                qv[u] = ld_pack<T, W>(q + i * W);
+            }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (i0 + u * S < nw) {
+                const int64_t i = i0 + u * S;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    xv[u].v[k] = fma(alpha, dv[u].v[k], xv[u].v[k]);
+                    rv[u].v[k] = fma(-alpha, qv[u].v[k], rv[u].v[k]);
+                    acc_dot(rv[u].v[k], rv[u].v[k], s, c, sd);
+                }
+                st_pack<T, W>(x + i * W, xv[u]);
+                st_pack<T, W>(r + i * W, rv[u]);
+            }
+    }
+    for (int64_t i = nw * W + tid; i < n; i += S) {
+        x[i] = fma(alpha, d[i], x[i]);
+        const T ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        acc_dot(ri, ri, s, c, sd);
+    }
+    b = block_sum(sizeof(T) == 4 ? (double)s + (double)c : sd, sh);
+    if (threadIdx.x == 0) parts[G + blockIdx.x] = b;
+    if (!grid_barrier(w, 2 * G, limit)) return;
+    const double rr1 = sum_parts(parts + G, sh);
+    const T beta = (T)(rr1 / rr);
+    if (lead) {
+        scal[1 - cur] = rr1;
+        scal[4] = rr1 / rr;
+    }
+    // 3. d
+#pragma unroll 1
+    for (int64_t i0 = tid; i0 < nw; i0 += kU * S) {
+        Pack<T, W> rv[kU], dv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (i0 + u * S < nw) {
+                rv[u] = ld_pack<T, W>(r + (i0 + u * S) * W);
+                dv[u] = ld_pack<T, W>(d + (i0 + u * S) * W);
+            }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (i0 + u * S < nw) {
+#pragma unroll
+                for (int k = 0; k < W; ++k) dv[u].v[k] = fma(beta, dv[u].v[k], rv[u].v[k]);
+                st_pack<T, W>(d + (i0 + u * S) * W, dv[u]);
+            }
+    }
+    for (int64_t i = nw * W + tid; i < n; i += S) d[i] = fma(beta, d[i], r[i]);
+    // the last block to leave resets the counters (all others are past both barriers)
+    if (threadIdx.x == 0 && atomicAdd(&w->leave, 1u) == G - 1) {
+        w->arrive = 0u;
+        w->leave = 0u;
+        __threadfence();
+    }
+}
+
+// Polls before a grid barrier of the cooperative update gives up (each poll
+// is an L2 round trip plus a short sleep: the default is on the order of a
+// second); rgcsr_set_wait_limit changes it, for tests of the timeout path.
+constexpr unsigned kDefaultWaitLimit = 1u << 21;
+std::atomic<unsigned> g_wait_limit{0};
+unsigned cg_wait_limit() {
+    const unsigned v = g_wait_limit.load(std::memory_order_relaxed);
+    return v ? v : kDefaultWaitLimit;
+}
+
 // Blocks of the fused kernels: one 16-byte pack per thread where possible,
 // at most `per_sm` blocks per SM and kCgParts in all.  The reducing kernels
 // take 2 per SM (fewer same-address tickets, kU packs in flight per
@@ -197,7 +353,7 @@ struct CgScratch {
 
 size_t cg_bytes(int64_t n, int vt) {
     const size_t es = vt == RGCSR_F64 ? 8 : 4;
-    return 3 * align_up((size_t)n * es, 256) + 256 + align_up((size_t)std::max(kDotParts, kCgParts) * 8, 256);
+    return 3 * align_up((size_t)n * es, 256) + 256 + align_up((size_t)std::max(kDotParts, 2 * kCgParts) * 8, 256);
 }
 
 CgScratch carve_cg(void *ws, int64_t n, int vt) {
@@ -227,7 +383,7 @@ int cg_run(const rgcsr_matrix *A, const void *b, void *x, double rel_tol, int ma
     RGCSR_CUDA_TRY(cudaMemsetAsync(x, 0, bytes, s));
     RGCSR_CUDA_TRY(cudaMemcpyAsync(c.r, b, bytes, cudaMemcpyDeviceToDevice, s));
     RGCSR_CUDA_TRY(cudaMemcpyAsync(c.d, b, bytes, cudaMemcpyDeviceToDevice, s));
-    RGCSR_CUDA_TRY(cudaMemsetAsync(c.count, 0, sizeof(unsigned), s));
+    RGCSR_CUDA_TRY(cudaMemsetAsync(c.count, 0, 32, s));            // the ticket and the barrier words
     if ((st = dot_device(n, c.r, c.r, &c.scal[0], c.partials, vt, s, c.count)) != RGCSR_OK) return st;
     double bb = 0.0;
     RGCSR_CUDA_TRY(cudaMemcpyAsync(&bb, &c.scal[0], sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -241,11 +397,49 @@ int cg_run(const rgcsr_matrix *A, const void *b, void *x, double rel_tol, int ma
     // rr' = r.r; d = r + (rr' / rr) d.  `cur` selects which scalar slot holds rr.
     constexpr int kW = 16 / (int)sizeof(T);                 // 16-byte accesses when x is aligned
     const bool vec = all_aligned16(x, c.r, c.d, c.q);
+    CoopWords *words = reinterpret_cast<CoopWords *>(reinterpret_cast<char *>(c.scal) + 72);
+    // the update as one cooperative kernel when every block of its grid can
+    // be resident (up to 4 per SM); else, or if the launch is refused, the
+    // three kernels
+    auto coop_kernel = vec ? cg_update_coop_kernel<T, kW> : cg_update_coop_kernel<T, 1>;
+    unsigned coop_grid = 0;
+    {
+        int per_sm = 0, sms = 0, dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel, kThreads, 0) == cudaSuccess &&
+            per_sm > 0 && sms > 0) {
+            const int64_t want = ceil_div(ceil_div(n, vec ? kW : 1), kThreads);
+            coop_grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)std::min(per_sm, 4) * sms,
+                                                                           (int64_t)kCgParts}));
+        }
+        cudaGetLastError();
+    }
+    const unsigned limit = cg_wait_limit();
     auto iteration = [&](cudaStream_t st_, int cur_) -> int {
         int e;
         if ((e = rgcsr_spmv(A, c.d, c.q, (rgcsr_stream_t)st_)) != RGCSR_OK) return e;
         T *xt = static_cast<T *>(x), *rt = static_cast<T *>(c.r), *dt = static_cast<T *>(c.d);
         const T *qt = static_cast<const T *>(c.q);
+        if (coop_grid) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(coop_grid);
+            cfg.blockDim = dim3(kThreads);
+            cfg.stream = st_;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            if (cudaLaunchKernelEx(&cfg, coop_kernel, n, xt, rt, dt, qt, c.scal, cur_, c.partials, words, limit) ==
+                cudaSuccess)
+                return RGCSR_OK;
+            cudaGetLastError();
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(st_, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+                return RGCSR_ERR_CUDA;                  // not recordable: the round runs without a graph
+            coop_grid = 0;                              // refused: the three kernels from now on
+        }
         if (vec) {
             const unsigned gr = cg_grid(ceil_div(n, kW), 2), gu = cg_grid(ceil_div(n, kW), 8);
             cg_dq_kernel<T, kW><<<gr, kThreads, 0, st_>>>(n, dt, qt, c.scal, cur_, c.partials, c.count);
@@ -278,8 +472,11 @@ int cg_run(const rgcsr_matrix *A, const void *b, void *x, double rel_tol, int ma
             }
         }
         it += chunk;
+        CoopWords cw;
         RGCSR_CUDA_TRY(cudaMemcpyAsync(&rr, &c.scal[cur], sizeof(double), cudaMemcpyDeviceToHost, s));
+        RGCSR_CUDA_TRY(cudaMemcpyAsync(&cw, words, sizeof(cw), cudaMemcpyDeviceToHost, s));
         RGCSR_CUDA_TRY(cudaStreamSynchronize(s));
+        if (cw.error) { if (round) cudaGraphExecDestroy(round); return RGCSR_ERR_TIMEOUT; }
         if (!(rr == rr) || std::sqrt(rr) <= rel_tol * std::sqrt(bb)) break;   // converged (or NaN)
         if (!tried && check_every % 2 == 0 && max_iter - it >= 2 * check_every) {
             tried = true;
@@ -403,5 +600,11 @@ RGCSR_API int rgcsr_ir_cg(const rgcsr_matrix *A_hi, const rgcsr_matrix *A_lo, co
     }
     *inner_iters = total_inner;
     *rel_residual = rel;
+    return RGCSR_OK;
+}
+
+RGCSR_API int rgcsr_set_wait_limit(int32_t polls) {
+    if (polls < 0) return RGCSR_ERR_INVALID_ARG;
+    g_wait_limit.store((unsigned)polls);
     return RGCSR_OK;
 }

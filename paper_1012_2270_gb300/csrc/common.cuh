@@ -193,6 +193,9 @@ int launch_row_lengths(const rgcsr_csr *A, const int32_t *perm, int32_t *row_len
 // sets bit 4 of *flags unless perm is a permutation of [0, n); seen: n ints of scratch
 int launch_check_perm(const int32_t *perm, int64_t n, int32_t *seen, int *flags, cudaStream_t s);
 
+// The kernel and variant RGCSR_KERNEL_AUTO runs for M (spmv.cu).
+int auto_kernel(const rgcsr_matrix *M, int *variant);
+
 // Checks mode (check.cu): RGCSR_OK when it is off, when `s` is being
 // captured, or when M passes rgcsr_check_matrix; else RGCSR_ERR_CORRUPT
 // (and RGCSR_STATUS_CORRUPT is raised).  Products call it before any launch.
@@ -236,6 +239,25 @@ __device__ __forceinline__ void dot2_step(float a, float b, float &s, float &c) 
     const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));   // s + p = t + q exactly
     s = t;
     c = __fadd_rn(c, __fadd_rn(q, e));
+}
+
+// The block's partial (every thread passes its own) goes to parts; true in
+// the block that finishes last, whose threads then get the grand total.
+__device__ __forceinline__ bool reduce_last(double v, double *parts, unsigned *ticket, double *sh, double &total) {
+    __shared__ bool last;
+    const double b = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        parts[blockIdx.x] = b;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double t = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(parts + i);
+    total = block_sum(t, sh);
+    return true;
 }
 
 // Vector kernels (blas1.cu).  dot_device writes the dot product of x and y

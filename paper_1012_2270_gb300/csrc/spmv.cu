@@ -216,19 +216,20 @@ __device__ __forceinline__ void vec_get(const V *p, const int32_t *c, typename V
     }
 }
 
-template <typename V, int RPL, int U, int MIN_BLOCKS>
-__global__ void __launch_bounds__(kDefaultThreads, MIN_BLOCKS)
-rgcsr_spmv_vec(int64_t n, const V *__restrict__ val, const int32_t *__restrict__ col,
-               const int64_t *__restrict__ gp, const int32_t *__restrict__ rl, const float *__restrict__ scale,
-               const typename VT<V>::A *__restrict__ x, typename VT<V>::A *__restrict__ y,
-               const int32_t *__restrict__ perm) {
+// The row sums of thread `tid` under that mapping: acc[r] for row
+// first + t0 + r of group g = tid / (32 / RPL).  Returns R_g, or 0 when the
+// thread is past the last group (nothing loaded).
+template <typename V, int RPL, int U>
+__device__ __forceinline__ int vec_rows(int64_t n, const V *__restrict__ val, const int32_t *__restrict__ col,
+                                        const int64_t *__restrict__ gp, const int32_t *__restrict__ rl,
+                                        const typename VT<V>::A *__restrict__ x, int64_t tid, int64_t &first,
+                                        int &t0, typename VT<V>::A (&acc)[RPL]) {
     using A = typename VT<V>::A;
     constexpr int LPG = 32 / RPL;                                   // lanes per group
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t g = tid / LPG;
-    const int t0 = (int)(tid % LPG) * RPL;                          // first row within the group
-    const int64_t first = g * 32;
-    if (first >= n) return;
+    t0 = (int)(tid % LPG) * RPL;                                    // first row within the group
+    first = g * 32;
+    if (first >= n) return 0;
     const int R = (int)min((int64_t)32, n - first);
     const int64_t base = __ldg(gp + g);
     int len[RPL];
@@ -238,7 +239,6 @@ rgcsr_spmv_vec(int64_t n, const V *__restrict__ val, const int32_t *__restrict__
         len[r] = (t0 + r < R) ? __ldg(rl + first + t0 + r) : 0;
         lmax = max(lmax, len[r]);
     }
-    A acc[RPL];
 #pragma unroll
     for (int r = 0; r < RPL; ++r) acc[r] = 0;
     if (R == 32) {
@@ -263,6 +263,21 @@ rgcsr_spmv_vec(int64_t n, const V *__restrict__ val, const int32_t *__restrict__
                 acc[r] = fma(VT<V>::ld(val + p), __ldg(x + __ldcs(col + p)), acc[r]);
             }
     }
+    return R;
+}
+
+template <typename V, int RPL, int U, int MIN_BLOCKS>
+__global__ void __launch_bounds__(kDefaultThreads, MIN_BLOCKS)
+rgcsr_spmv_vec(int64_t n, const V *__restrict__ val, const int32_t *__restrict__ col,
+               const int64_t *__restrict__ gp, const int32_t *__restrict__ rl, const float *__restrict__ scale,
+               const typename VT<V>::A *__restrict__ x, typename VT<V>::A *__restrict__ y,
+               const int32_t *__restrict__ perm) {
+    using A = typename VT<V>::A;
+    int64_t first;
+    int t0;
+    A acc[RPL];
+    const int R = vec_rows<V, RPL, U>(n, val, col, gp, rl, x, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                      first, t0, acc);
 #pragma unroll
     for (int r = 0; r < RPL; ++r)
         if (t0 + r < R) y[out_row(perm, first + t0 + r)] = finish<V>(acc[r], scale, first + t0 + r);
@@ -460,7 +475,7 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
         return launch_status();
     }
     if (kernel == RGCSR_KERNEL_LEAN && L && (L->variant == 1 || L->variant == 2 || L->variant == 4 ||
-                                             L->variant == 8)) {
+                                             L->variant == 8 || L->variant == 9)) {
         auto aligned = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
         if (G != 32 || !aligned(val) || !aligned(M->columns)) return RGCSR_ERR_INVALID_ARG;
         // variant 1: 4 rows per lane (FP64: 2), 2 slot-rows in flight;
@@ -473,6 +488,13 @@ int launch_spmv(const rgcsr_matrix *M, const typename VT<V>::A *x, typename VT<V
         if (L->variant == 8)          // every slot-row of a short row in flight at once
             rgcsr_spmv_vec<V, rpl1, 8, 2><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
                 n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
+        else if (L->variant == 9) {   // BF16/FP16: as 1 at 6 blocks per SM (40 registers, no spills)
+            if constexpr (sizeof(V) == 2)
+                rgcsr_spmv_vec<V, rpl1, 2, 6><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
+                    n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
+            else
+                return RGCSR_ERR_INVALID_ARG;
+        }
         else if (L->variant == 1)
             rgcsr_spmv_vec<V, rpl1, 2, 5><<<(unsigned)blocks, kDefaultThreads, 0, s>>>(
                 n, val, M->columns, M->group_ptr, M->row_lengths, scale, x, y, M->row_perm);
@@ -665,6 +687,33 @@ int launch_long_rows(const rgcsr_matrix *M, const rgcsr_long_rows *S, const type
     return launch_status();
 }
 
+}  // namespace
+
+// The kernel RGCSR_KERNEL_AUTO runs, as timed on GB300.  Dense groups
+// (padding <= 25% of the stored slots, no row far longer than the average)
+// with short rows (<= 8 per row) at G = 32 take the vector-load kernel (4
+// rows per lane with 2 slot-rows per step; FP64: 2 rows with 4); longer
+// FP32 rows the TMA-staged kernel (16 slot-rows per stage); the rest the
+// full-occupancy thread-per-row kernel.  Uneven or long rows take the
+// warp-split kernel.
+int auto_kernel(const rgcsr_matrix *M, int *variant) {
+    const bool dense = M->n_stored * 4 <= M->nnz * 5 &&
+                       !(M->max_row_len > 64 && M->max_row_len * M->n_rows > 8 * M->nnz);
+    const bool short_rows = M->nnz <= 8 * M->n_rows;
+    auto aligned = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    *variant = 0;
+    if (dense && short_rows && M->group_size == 32 && aligned(M->values) && aligned(M->columns)) {
+        *variant = M->value_type == RGCSR_F64 ? 4 : 1;
+        return RGCSR_KERNEL_LEAN;
+    }
+    if (dense && M->value_type == RGCSR_F32 && tma_eligible(M)) {
+        *variant = 2;
+        return RGCSR_KERNEL_TMA;
+    }
+    return dense ? RGCSR_KERNEL_LEAN : RGCSR_KERNEL_SPLIT;
+}
+
+namespace {
 int check_matrix(const rgcsr_matrix *M) {
     if (!M || M->n_rows < 0 || M->n_cols < 0 || M->group_size < 1) return RGCSR_ERR_INVALID_ARG;
     if (M->n_rows == 0) return RGCSR_OK;
@@ -696,31 +745,7 @@ RGCSR_API int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
         !(kernel == RGCSR_KERNEL_PAPER || kernel == RGCSR_KERNEL_SPLIT ||
           (kernel == RGCSR_KERNEL_LEAN && variant == 0)))
         return RGCSR_ERR_INVALID_ARG;
-    if (kernel == RGCSR_KERNEL_AUTO) {
-        // Dense groups (padding <= 25% of the stored slots), as timed on
-        // GB300: short rows (<= 8 per row) at G = 32 take the vector-load
-        // kernel (4 rows per lane with 2 slot-rows per step; FP64: 2 rows
-        // with 4); longer FP32 rows the TMA-staged kernel (16 slot-rows per
-        // stage); the rest the full-occupancy thread-per-row kernel.  Uneven
-        // or long rows take the warp-split kernel.
-        // "dense": little padding and no row far longer than the average
-        const bool dense = M->n_stored * 4 <= M->nnz * 5 &&
-                           !(M->max_row_len > 64 && M->max_row_len * M->n_rows > 8 * M->nnz);
-        const bool short_rows = M->nnz <= 8 * M->n_rows;
-        auto aligned = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
-        variant = 0;
-        if (dense && short_rows && M->group_size == 32 && aligned(M->values) && aligned(M->columns)) {
-            kernel = RGCSR_KERNEL_LEAN;
-            variant = M->value_type == RGCSR_F64 ? 4 : 1;
-        } else if (dense && M->value_type == RGCSR_F32 && tma_eligible(M)) {
-            kernel = RGCSR_KERNEL_TMA;
-            variant = 2;
-        } else if (dense) {
-            kernel = RGCSR_KERNEL_LEAN;
-        } else {
-            kernel = RGCSR_KERNEL_SPLIT;
-        }
-    }
+    if (kernel == RGCSR_KERNEL_AUTO) kernel = auto_kernel(M, &variant);
     if (kernel == RGCSR_KERNEL_TMA) {
         if (!tma_eligible(M)) return RGCSR_ERR_INVALID_ARG;
         if (launch && launch->wait_limit < 0) return RGCSR_ERR_INVALID_ARG;
@@ -741,6 +766,16 @@ RGCSR_API int rgcsr_spmv_ex(const rgcsr_matrix *M, const void *x, void *y,
         default:
             return RGCSR_ERR_UNSUPPORTED_DTYPE;
     }
+}
+
+RGCSR_API int rgcsr_auto_kernel(const rgcsr_matrix *M, int32_t *kernel, int32_t *variant) {
+    if (!kernel || !variant) return RGCSR_ERR_INVALID_ARG;
+    const int st = check_matrix(M);
+    if (st != RGCSR_OK) return st;
+    int v = 0;
+    *kernel = auto_kernel(M, &v);
+    *variant = v;
+    return RGCSR_OK;
 }
 
 RGCSR_API int rgcsr_spmv(const rgcsr_matrix *M, const void *x, void *y, rgcsr_stream_t stream) {

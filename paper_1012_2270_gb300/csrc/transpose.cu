@@ -184,29 +184,44 @@ template <typename V>
 __global__ void gather_if_kernel(const V *__restrict__ src, const int64_t *__restrict__ index, int64_t n,
                                  V *__restrict__ dst, const unsigned long long *__restrict__ flags) {
     if (!(*flags & 2ull)) return;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = index[s];
-        dst[s] = i >= 0 ? src[i] : V(0);
+    constexpr int U = 4;                         // slots a thread has in flight
+    const int64_t S = (int64_t)gridDim.x * blockDim.x;
+#pragma unroll 1
+    for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s0 < n; s0 += U * S) {
+        int64_t i[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) i[u] = s0 + u * S < n ? __ldcs(index + s0 + u * S) : -1;
+        V w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) w[u] = i[u] >= 0 ? __ldg(src + i[u]) : V(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (s0 + u * S < n) dst[s0 + u * S] = w[u];
     }
 }
 
-// Hash of n values of ES bytes (2, 4 or 8), one 64-bit sum over the 64-bit
-// words of their bytes (little-endian; the last word zero-filled past the
-// end):
-//     h = sum_j mix(w_j ^ ((j + 1) K))   (mod 2^64),   K = 0x9E3779B97F4A7C15
+// Hash of n values of ES bytes (2, 4 or 8): one 64-bit sum over the
+// 32-byte blocks of their bytes (words w0..w3 little-endian; the last block
+// zero-filled past the end):
+//     h = sum_q mix((w0 ^ k_q) + w1 C1 + w2 C2 + w3 C3),   k_q = (q + 1) K   (mod 2^64)
 // with mix the SplitMix64 finalizer (Steele, Lea and Flood 2014; constants
-// as published), a bijection of 64-bit words, so changing any one value
-// always changes h; several values changed at once leave it unchanged only
-// by chance (about 2^-64), since mix destroys the structure a common change
-// of bits (e.g. every value scaled by one factor) would otherwise carry into
-// the sum.  One mix per 8 bytes keeps the kernel at the read rate.  The sum
-// is exact modular arithmetic, so it does not depend on the order of the
-// additions.  The last block to finish (a ticket after a fence) adds the
-// block sums and updates the state record: word 0 the hash, word 1 bit 0
-// "holds values", bit 1 "changed by this call".
-constexpr int kHashParts = 608;          // 4 blocks per SM
+// as published), a bijection of 64-bit words, and K, C1..C3 odd constants.
+// For a fixed block q the argument of mix changes whenever exactly one of
+// its words changes (w_i C_i changes because C_i is odd), so changing any
+// one value always changes h; changes of several values leave h unchanged
+// only by chance (about 2^-64), since mix destroys the structure a common
+// change of bits (e.g. every value scaled by one factor) would otherwise
+// carry into the sum.  One mix per 32 bytes keeps the integer work well
+// below the read time.  The sum is exact modular arithmetic, so it does not
+// depend on the order of the additions.  The last block to finish (a ticket
+// after a fence) adds the block sums and updates the state record: word 0
+// the hash, word 1 bit 0 "holds values", bit 1 "changed by this call".
+constexpr int kHashParts = 1216;         // 8 blocks per SM
 constexpr int kHashThreads = 256;
 constexpr unsigned long long kHashK = 0x9E3779B97F4A7C15ull;
+constexpr unsigned long long kHashC1 = 0xD1B54A32D192ED03ull;
+constexpr unsigned long long kHashC2 = 0x8CB92BA72F3D8DD7ull;
+constexpr unsigned long long kHashC3 = 0xAEF17502108EF2D9ull;
 
 __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int o) {
     const unsigned lo = __shfl_xor_sync(kFull, (unsigned)v, o), hi = __shfl_xor_sync(kFull, (unsigned)(v >> 32), o);
@@ -224,7 +239,8 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
     return t;
 }
 
-// Word j assembled from its values (each loaded at its own alignment).
+// Word j of the byte stream, assembled from its values (each loaded at its
+// own alignment); 0 past the end.
 template <int ES>
 __device__ __forceinline__ unsigned long long hash_word(const void *v, int64_t n, int64_t j) {
     constexpr int PER = 8 / ES;
@@ -243,37 +259,43 @@ __device__ __forceinline__ unsigned long long hash_word(const void *v, int64_t n
     return w;
 }
 
-// Each thread takes 16-byte packs (words 2p, 2p + 1) in a grid-stride loop
-// with kHashU packs loaded before they are used, then the words past the
-// last whole pack; with a base that is not 16-byte aligned every word is
-// assembled from its values.
-constexpr int kHashU = 4;
+__device__ __forceinline__ unsigned long long block_term(unsigned long long w0, unsigned long long w1,
+                                                         unsigned long long w2, unsigned long long w3,
+                                                         unsigned long long k) {
+    return mix64((w0 ^ k) + w1 * kHashC1 + w2 * kHashC2 + w3 * kHashC3);
+}
 
+__device__ __forceinline__ unsigned long long block_term(const uint4 &a, const uint4 &b, unsigned long long k) {
+    return block_term(((unsigned long long)a.y << 32) | a.x, ((unsigned long long)a.w << 32) | a.z,
+                      ((unsigned long long)b.y << 32) | b.x, ((unsigned long long)b.w << 32) | b.z, k);
+}
+
+// Each thread takes one 32-byte block (two 16-byte loads) per step of a
+// grid-stride loop, on a full-occupancy grid (8 CTAs per SM, at most 32
+// registers): the many warps of an SM, not deep unrolling, keep the reads
+// in flight while others mix.  Then the blocks past the last whole one;
+// with a base that is not 16-byte aligned every block is assembled from
+// its values.
 template <int ES>
-__global__ void __launch_bounds__(kHashThreads)
+__global__ void __launch_bounds__(kHashThreads, 8)
 values_hash_kernel(const void *__restrict__ v, int64_t n, unsigned long long *__restrict__ state) {
     __shared__ unsigned long long sh[kHashThreads / 32];
     __shared__ bool last;
     unsigned long long h = 0;
     const int64_t S = (int64_t)gridDim.x * blockDim.x, tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t bytes = n * ES, words = (bytes + 7) / 8;
-    const int64_t np = ((uintptr_t)v & 15) == 0 ? bytes / 16 : 0;
+    const int64_t bytes = n * ES, blocks = (bytes + 31) / 32;
+    const int64_t nq = ((uintptr_t)v & 15) == 0 ? bytes / 32 : 0;
+    const uint4 *pv = static_cast<const uint4 *>(v);
+    const unsigned long long kS = (unsigned long long)S * kHashK;
+    unsigned long long k = (unsigned long long)(tid + 1) * kHashK;
 #pragma unroll 1
-    for (int64_t p0 = tid; p0 < np; p0 += kHashU * S) {
-        uint4 pk[kHashU];
-#pragma unroll
-        for (int u = 0; u < kHashU; ++u)
-            if (p0 + u * S < np) pk[u] = __ldcs(static_cast<const uint4 *>(v) + p0 + u * S);
-#pragma unroll
-        for (int u = 0; u < kHashU; ++u)
-            if (p0 + u * S < np) {
-                const unsigned long long k0 = (unsigned long long)(2 * (p0 + u * S) + 1) * kHashK;
-                h += mix64((((unsigned long long)pk[u].y << 32) | pk[u].x) ^ k0);
-                h += mix64((((unsigned long long)pk[u].w << 32) | pk[u].z) ^ (k0 + kHashK));
-            }
+    for (int64_t q = tid; q < nq; q += S, k += kS) {
+        const uint4 a = __ldcs(pv + 2 * q), b = __ldcs(pv + 2 * q + 1);
+        h += block_term(a, b, k);
     }
-    for (int64_t j = 2 * np + tid; j < words; j += S)
-        h += mix64(hash_word<ES>(v, n, j) ^ ((unsigned long long)(j + 1) * kHashK));
+    for (int64_t q = nq + tid; q < blocks; q += S)
+        h += block_term(hash_word<ES>(v, n, 4 * q), hash_word<ES>(v, n, 4 * q + 1), hash_word<ES>(v, n, 4 * q + 2),
+                        hash_word<ES>(v, n, 4 * q + 3), (unsigned long long)(q + 1) * kHashK);
     h = block_sum_u64(h, sh);
     unsigned long long *part = state + 8;               // [kHashParts] block sums
     unsigned *ticket = reinterpret_cast<unsigned *>(state + 2);

@@ -251,6 +251,13 @@ class RgCSRMatrix:
             self.split_long_rows(other._long[0].threshold, other._long[0].segment)
         return self
 
+    def auto_kernel(self) -> tuple:
+        """(kernel, variant) that spmv() runs without a schedule or options
+        (rgcsr_auto_kernel: the library's RGCSR_KERNEL_AUTO rule)."""
+        k, v = ctypes.c_int32(0), ctypes.c_int32(0)
+        L.call("rgcsr_auto_kernel", ctypes.byref(self.s), ctypes.byref(k), ctypes.byref(v))
+        return k.value, v.value
+
     def check(self, stream=None) -> dict:
         """The library's structural checks of the stored layout
         (rgcsr_check_matrix): {"ok", "flags" (names of the failed checks),

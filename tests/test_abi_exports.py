@@ -121,6 +121,27 @@ def _argument_checks():
     assert lib.rgcsr_check_matrix(ctypes.byref(M4), ctypes.byref(rep), None) == L.RGCSR_ERR_UNSUPPORTED_DTYPE
     assert lib.rgcsr_check_matrix(ctypes.byref(M0), ctypes.byref(rep), None) == L.RGCSR_OK
     assert (rep.flags, rep.group, rep.row, rep.slot) == (0, -1, -1, -1)
+    # the AUTO rule, host only (the pointers are only tested for alignment)
+    def auto(**kw):
+        base = dict(n_rows=4096, n_cols=4096, nnz=28000, group_size=32, n_groups=128, n_stored=28672,
+                    max_row_len=7, value_type=L.F32, values=256, columns=512, group_ptr=8, row_lengths=1024)
+        base.update(kw)
+        k, v = ctypes.c_int32(-1), ctypes.c_int32(-1)
+        assert lib.rgcsr_auto_kernel(ctypes.byref(L.Matrix(**base)), ctypes.byref(k), ctypes.byref(v)) == 0
+        return k.value, v.value
+    assert auto() == (L.KERNEL_LEAN, 1)                                  # dense, short rows: vector loads
+    assert auto(value_type=L.F64) == (L.KERNEL_LEAN, 4)
+    assert auto(value_type=L.BF16) == (L.KERNEL_LEAN, 1)
+    assert auto(nnz=28000 * 3, n_stored=28672 * 3, max_row_len=21) == (L.KERNEL_TMA, 2)   # longer rows
+    assert auto(values=260) == (L.KERNEL_LEAN, 0)                        # misaligned: thread per row
+    assert auto(values=260, value_type=L.F64) == (L.KERNEL_LEAN, 0)
+    assert auto(n_stored=28000 * 2) == (L.KERNEL_SPLIT, 0)              # padding > 25%: uneven rows
+    assert auto(group_size=8, n_groups=512) == (L.KERNEL_LEAN, 0)
+    k = ctypes.c_int32(0)
+    assert lib.rgcsr_auto_kernel(ctypes.byref(M1), ctypes.byref(k), ctypes.byref(k)) == L.RGCSR_ERR_INVALID_ARG
+    assert lib.rgcsr_auto_kernel(ctypes.byref(M2), None, ctypes.byref(k)) == L.RGCSR_ERR_INVALID_ARG
+    assert lib.rgcsr_set_wait_limit(-1) == L.RGCSR_ERR_INVALID_ARG
+    assert lib.rgcsr_set_wait_limit(0) == L.RGCSR_OK
     # checks mode: the switch returns the previous setting
     prev = lib.rgcsr_set_checks(1)
     assert lib.rgcsr_set_checks(0) == 1

@@ -278,12 +278,13 @@ def test_value_hash_sees_every_change(dtype, offset):
         assert changed(), i
         v[i] = old
         assert changed(), i
-    i, j = 3, n - 4
-    assert v[i].item() != v[j].item()
-    vi, vj = v[i].item(), v[j].item()
-    v[i], v[j] = vj, vi
-    assert changed()
-    assert not changed()
+    for i, j in ((3, n - 4), (4, 5), (4, 4 + 8 // v.element_size())):
+        # far apart; neighbours; the two 8-byte words of one 16-byte pack
+        assert v[i].item() != v[j].item()
+        vi, vj = v[i].item(), v[j].item()
+        v[i], v[j] = vj, vi
+        assert changed(), (i, j)
+        assert not changed()
     v.mul_(2.0)                              # every element at once
     assert changed()
 

@@ -42,7 +42,7 @@ def check(A, src, fmt, x, G=32, kernels=({}, {"kernel": L.KERNEL_SPLIT}, {"kerne
     y_orig, a_orig = oracle.csr_spmv(A.rowptr, A.col, A.val, x)
     xd = torch.from_numpy(x32).cuda()
     if G == 32:
-        kernels = tuple(kernels) + tuple({"kernel": L.KERNEL_LEAN, "variant": v} for v in (1, 2, 4, 5, 6, 7, 8))   # vector loads
+        kernels = tuple(kernels) + tuple({"kernel": L.KERNEL_LEAN, "variant": v} for v in (1, 2, 4, 5, 6, 7, 8, 9))   # vector loads
         if A.n_rows >= 32:                                  # bulk-copy ring, several groups per copy
             kernels = kernels + tuple({"kernel": L.KERNEL_TMA, "variant": v} for v in (4, 5, 6))
     for kw in kernels:

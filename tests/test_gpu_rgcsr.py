@@ -535,7 +535,8 @@ def test_unknown_kernel_variants_rejected():
     A = ragged(300, 200, seed=2)
     M = to_gpu_matrix(A, "f32", 32)
     x = torch.zeros(A.n_cols, dtype=torch.float32, device="cuda")
-    for kw in (dict(kernel=L.KERNEL_LEAN, variant=3), dict(kernel=L.KERNEL_LEAN, variant=9),
+    for kw in (dict(kernel=L.KERNEL_LEAN, variant=3), dict(kernel=L.KERNEL_LEAN, variant=10),
+               dict(kernel=L.KERNEL_LEAN, variant=9),                   # BF16/FP16 storage only
                dict(kernel=L.KERNEL_TMA, variant=7),
                dict(kernel=L.KERNEL_LEAN, variant=-1)):
         with pytest.raises(L.RgCSRError) as e:

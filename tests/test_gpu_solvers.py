@@ -138,6 +138,41 @@ def test_cg_against_oracle(dtype):
     assert np.linalg.norm(xd - xr) <= 50 * tol * np.linalg.norm(xr)
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_cg_odd_size(dtype):
+    # n = 693, not a multiple of a 16-byte pack: the update's scalar tail
+    A = synth.laplacian_3d(7, 9, 11)
+    b = synth.uniform_vector(A.n_rows, seed=3)
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val, A.n_cols, dtype=dtype)
+    tol = 1e-10 if dtype == torch.float64 else 1e-5
+    x, its, rel = solvers.cg(M, torch.from_numpy(b).to("cuda", dtype), rel_tol=tol, max_iter=2000)
+    assert rel <= tol
+    r, _ = oracle.csr_spmv(A.rowptr, A.col, A.val, x.double().cpu().numpy())
+    assert np.linalg.norm(b - r) <= 5 * tol * np.linalg.norm(b)
+
+
+def test_cg_barrier_wait_runs_out():
+    # a one-poll limit on the update's grid barriers (64 blocks, so some
+    # block polls before the last one arrives): the call reports
+    # RGCSR_ERR_TIMEOUT instead of hanging, and the next solve with the
+    # default limit is right
+    A = synth.laplacian_2d(256)
+    b = torch.from_numpy(synth.uniform_vector(A.n_rows, seed=1)).to("cuda", torch.float32)
+    M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val, A.n_cols, dtype=torch.float32)
+    assert L.lib().rgcsr_set_wait_limit(1) == L.RGCSR_OK
+    try:
+        with pytest.raises(L.RgCSRError) as e:
+            solvers.cg(M, b, rel_tol=1e-5, max_iter=200)
+        assert e.value.status == L.RGCSR_ERR_TIMEOUT
+    finally:
+        assert L.lib().rgcsr_set_wait_limit(0) == L.RGCSR_OK
+    x, its, rel = solvers.cg(M, b, rel_tol=1e-5, max_iter=2000)
+    assert rel <= 1e-5
+    r, _ = oracle.csr_spmv(A.rowptr, A.col, A.val, x.double().cpu().numpy())
+    bn = b.double().cpu().numpy()
+    assert np.linalg.norm(bn - r) <= 5e-5 * np.linalg.norm(bn)
+
+
 def test_cg_zero_rhs():
     A = synth.laplacian_2d(8)
     M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val, A.n_cols, dtype=torch.float64)
