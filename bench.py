@@ -666,8 +666,8 @@ def roofline_of(cases, per_case_us, detail, fma_rate, clk, dev, gather_rate):
 def measure_e2e(cases, world, step_bytes, K, stream, barrier, dev):
     """The same six SpMVs end to end through rgcsr_spmv_host: per step and
     case x host->device, SpMV, y device->host (pinned buffers, matrix
-    resident, as in a Krylov solver); the six cases on three streams so that
-    one case's copies overlap another's SpMV."""
+    resident, as in a Krylov solver); one stream per case, so that one
+    case's copies overlap another's SpMV."""
     import torch
     host = []
     for c in cases:
@@ -677,9 +677,9 @@ def measure_e2e(cases, world, step_bytes, K, stream, barrier, dev):
     h2d = sum(h[0].numel() * h[0].element_size() for h in host)
     d2h = sum(h[1].numel() * h[1].element_size() for h in host)
     Ke = max(3, K // 4)
-    streams = [torch.cuda.Stream() for _ in range(3)]
-    # each case's SpMVs on one stream at a time: a schedule's scratch allows
-    # one product in flight, so case i always uses stream i mod 3
+    # one stream per case: a schedule's scratch allows one product in flight,
+    # and each case's chain (x in, SpMV, y out) then overlaps the other cases'
+    streams = [torch.cuda.Stream() for _ in range(len(cases))]
     def e2e_run(n_steps, overlap):
         e0, e1 = _ev()
         e0.record(stream)
@@ -687,7 +687,7 @@ def measure_e2e(cases, world, step_bytes, K, stream, barrier, dev):
             st.wait_event(e0)
         for _ in range(n_steps):
             for i, (c, h) in enumerate(zip(cases, host)):
-                c["M"].spmv_host(*h, stream=streams[i % 3] if overlap else stream, **c["kw"])
+                c["M"].spmv_host(*h, stream=streams[i] if overlap else stream, **c["kw"])
         for st in streams:
             ev = torch.cuda.Event()
             ev.record(st)
@@ -707,7 +707,7 @@ def measure_e2e(cases, world, step_bytes, K, stream, barrier, dev):
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "one_stream_value": whole_job_gbs(world, Ke, step_bytes, ms_e2e_serial),
             "note": "per step and case: x host->device, SpMV, y device->host through rgcsr_spmv_host (pinned "
-                    "buffers, matrix resident); the six cases on three streams so copies overlap SpMVs"}
+                    "buffers, matrix resident); one stream per case so copies overlap SpMVs"}
 
 
 # ---------------------------------------------------------------------------
@@ -962,9 +962,7 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None,
         torch.cuda.nvtx.range_push("autograd_forward")            # a profiler can pick it out
         t_f = per_call_us(fwd)
         torch.cuda.nvtx.range_pop()
-        torch.cuda.nvtx.range_push("autograd_forward_backward")
         t_fb = per_call_us(fwd_bwd)
-        torch.cuda.nvtx.range_pop()
         forms["backward_b_k8_f32"] = {"group_size": G, "schedule": "descending row order, group tiles C=64",
                                       "spmm_us": t_mm, "forward_us": t_f, "forward_backward_us": t_fb,
                                       "forward_over_spmm": t_f / t_mm, "backward_over_forward": (t_fb - t_f) / t_f}
