@@ -200,28 +200,25 @@ __global__ void gather_if_kernel(const V *__restrict__ src, const int64_t *__res
     }
 }
 
-// Hash of n values of ES bytes (2, 4 or 8): one 64-bit sum over the
-// 32-byte blocks of their bytes (words w0..w3 little-endian; the last block
-// zero-filled past the end):
-//     h = sum_q mix((w0 ^ k_q) + w1 C1 + w2 C2 + w3 C3),   k_q = (q + 1) K   (mod 2^64)
+// Hash of n values of ES bytes (2, 4 or 8): one 64-bit sum over the 8-byte
+// words w_j of their bytes (little-endian; the last word zero-filled past
+// the end):
+//     h = sum_j mix(w_j ^ ((j + 1) K))   (mod 2^64),   K = 0x9E3779B97F4A7C15
 // with mix the SplitMix64 finalizer (Steele, Lea and Flood 2014; constants
-// as published), a bijection of 64-bit words, and K, C1..C3 odd constants.
-// For a fixed block q the argument of mix changes whenever exactly one of
-// its words changes (w_i C_i changes because C_i is odd), so changing any
-// one value always changes h; changes of several values leave h unchanged
-// only by chance (about 2^-64), since mix destroys the structure a common
-// change of bits (e.g. every value scaled by one factor) would otherwise
-// carry into the sum.  One mix per 32 bytes keeps the integer work well
-// below the read time.  The sum is exact modular arithmetic, so it does not
-// depend on the order of the additions.  The last block to finish (a ticket
-// after a fence) adds the block sums and updates the state record: word 0
-// the hash, word 1 bit 0 "holds values", bit 1 "changed by this call".
+// as published), a bijection of 64-bit words, so changing any one value
+// always changes h; changes of several values leave h unchanged only by
+// chance (about 2^-64), since each word goes through its own mix: a common
+// change of bits (every value negated or scaled by one factor) reaches the
+// sum as unrelated 64-bit terms.  (Combining a block's words linearly
+// before one mix is cheaper but not safe: negating four FP64 values flips
+// bit 63 of four words, and four multiples of 2^63 cancel.)  The sum is
+// exact modular arithmetic, so it does not depend on the order of the
+// additions.  The last block to finish (a ticket after a fence) adds the
+// block sums and updates the state record: word 0 the hash, word 1 bit 0
+// "holds values", bit 1 "changed by this call".
 constexpr int kHashParts = 1216;         // 8 blocks per SM
 constexpr int kHashThreads = 256;
 constexpr unsigned long long kHashK = 0x9E3779B97F4A7C15ull;
-constexpr unsigned long long kHashC1 = 0xD1B54A32D192ED03ull;
-constexpr unsigned long long kHashC2 = 0x8CB92BA72F3D8DD7ull;
-constexpr unsigned long long kHashC3 = 0xAEF17502108EF2D9ull;
 
 __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int o) {
     const unsigned lo = __shfl_xor_sync(kFull, (unsigned)v, o), hi = __shfl_xor_sync(kFull, (unsigned)(v >> 32), o);
@@ -259,10 +256,12 @@ __device__ __forceinline__ unsigned long long hash_word(const void *v, int64_t n
     return w;
 }
 
+// The terms of the four words of 32-byte block q, k = (4q + 1) K the salt of
+// its first word.
 __device__ __forceinline__ unsigned long long block_term(unsigned long long w0, unsigned long long w1,
                                                          unsigned long long w2, unsigned long long w3,
                                                          unsigned long long k) {
-    return mix64((w0 ^ k) + w1 * kHashC1 + w2 * kHashC2 + w3 * kHashC3);
+    return mix64(w0 ^ k) + mix64(w1 ^ (k + kHashK)) + mix64(w2 ^ (k + 2 * kHashK)) + mix64(w3 ^ (k + 3 * kHashK));
 }
 
 __device__ __forceinline__ unsigned long long block_term(const uint4 &a, const uint4 &b, unsigned long long k) {
@@ -270,10 +269,10 @@ __device__ __forceinline__ unsigned long long block_term(const uint4 &a, const u
                       ((unsigned long long)b.y << 32) | b.x, ((unsigned long long)b.w << 32) | b.z, k);
 }
 
-// Each thread takes one 32-byte block (two 16-byte loads) per step of a
-// grid-stride loop, on a full-occupancy grid (8 CTAs per SM, at most 32
-// registers): the many warps of an SM, not deep unrolling, keep the reads
-// in flight while others mix.  Then the blocks past the last whole one;
+// Each thread takes one 32-byte block (two 16-byte loads, four words) per
+// step of a grid-stride loop, on a full-occupancy grid (8 CTAs per SM, at
+// most 32 registers): the many warps of an SM, not deep unrolling, keep the
+// reads in flight while others mix.  Then the blocks past the last whole one;
 // with a base that is not 16-byte aligned every block is assembled from
 // its values.
 template <int ES>
@@ -286,8 +285,8 @@ values_hash_kernel(const void *__restrict__ v, int64_t n, unsigned long long *__
     const int64_t bytes = n * ES, blocks = (bytes + 31) / 32;
     const int64_t nq = ((uintptr_t)v & 15) == 0 ? bytes / 32 : 0;
     const uint4 *pv = static_cast<const uint4 *>(v);
-    const unsigned long long kS = (unsigned long long)S * kHashK;
-    unsigned long long k = (unsigned long long)(tid + 1) * kHashK;
+    const unsigned long long kS = 4ull * (unsigned long long)S * kHashK;       // salt step of S blocks
+    unsigned long long k = (4ull * (unsigned long long)tid + 1) * kHashK;       // salt of block tid's word 0
 #pragma unroll 1
     for (int64_t q = tid; q < nq; q += S, k += kS) {
         const uint4 a = __ldcs(pv + 2 * q), b = __ldcs(pv + 2 * q + 1);
@@ -295,7 +294,7 @@ values_hash_kernel(const void *__restrict__ v, int64_t n, unsigned long long *__
     }
     for (int64_t q = nq + tid; q < blocks; q += S)
         h += block_term(hash_word<ES>(v, n, 4 * q), hash_word<ES>(v, n, 4 * q + 1), hash_word<ES>(v, n, 4 * q + 2),
-                        hash_word<ES>(v, n, 4 * q + 3), (unsigned long long)(q + 1) * kHashK);
+                        hash_word<ES>(v, n, 4 * q + 3), (4ull * (unsigned long long)q + 1) * kHashK);
     h = block_sum_u64(h, sh);
     unsigned long long *part = state + 8;               // [kHashParts] block sums
     unsigned *ticket = reinterpret_cast<unsigned *>(state + 2);

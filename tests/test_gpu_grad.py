@@ -287,6 +287,11 @@ def test_value_hash_sees_every_change(dtype, offset):
         assert not changed()
     v.mul_(2.0)                              # every element at once
     assert changed()
+    v.neg_()                                 # every sign bit at once
+    assert changed()
+    assert not changed()
+    ints.add_(1)                             # every lowest bit at once
+    assert changed()
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
