@@ -338,7 +338,9 @@ typedef struct {
     int32_t variant;            /* 0 = default; 1, 2: fewer / more slot-rows
                                    in flight per lane; 3, 4, 5: software-
                                    pipelined across a warp's tiles, 5 with
-                                   twice the slot-rows per step (tuning)      */
+                                   twice the slot-rows per step; 6, 7: each
+                                   step's columns loaded one step ahead
+                                   (tuning)                                   */
     int64_t n_groups;           /* (plan) the matrix's group count            */
     int64_t n_extra;            /* (plan) tasks beyond one per group          */
     int64_t n_split;            /* (plan) groups cut into more than one task  */

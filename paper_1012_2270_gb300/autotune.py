@@ -155,7 +155,7 @@ def candidates(rowptr, dtype: torch.dtype):
         cands += [dict(group_size=G, long_rows=[T, 256]) for G in (1, 2, 4) for T in (16, 32, 64)]
         desc = dict(group_size=32, row_order="descending")
         cands += [dict(desc, long_rows=[T, 256]) for T in (32, 64, 128, 256)]
-        cands += [dict(desc, tiles=[C, v]) for C in (32, 64, 128) for v in range(6)]
+        cands += [dict(desc, tiles=[C, v]) for C in (32, 64, 128) for v in range(8)]
     if not irregular:
         cands += [dict(group_size=32, tiles=[64, v]) for v in (0, 1, 2)]
     return cands

@@ -73,7 +73,11 @@ __device__ __forceinline__ A sum_partials(const A *p, int64_t nt) {
     return s[0];
 }
 
-template <typename V, int U, int MIN_BLOCKS>
+// CP: the columns of a tile's next step are loaded before the current
+// step's gathers (its values after them), so the DRAM latency of the
+// columns overlaps the gathers of the step before; the same sums in the
+// same order as without.
+template <typename V, int U, int MIN_BLOCKS, bool CP = false>
 __global__ void __launch_bounds__(kTileThreads, MIN_BLOCKS)
 rgcsr_spmv_tiles_kernel(int64_t n, int32_t G, int32_t C, int64_t n_groups, int64_t n_tasks,
                         const V *__restrict__ val, const int32_t *__restrict__ col,
@@ -109,21 +113,46 @@ rgcsr_spmv_tiles_kernel(int64_t n, int32_t G, int32_t C, int64_t n_groups, int64
         const V *vp = val + base + (int64_t)j0 * R + lane;
         const int32_t *cp = col + base + (int64_t)j0 * R + lane;
         A acc = 0;
-        for (int j = j0; j < jend; j += U) {
-            A v[U];
-            int c[U];
+        if constexpr (CP) {
+            int c[U], cn[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (j + u < jend) {
-                    v[u] = VT<V>::ld(vp + (int64_t)u * R);
-                    c[u] = ld_stream(cp + (int64_t)u * R);
-                }
+            for (int u = 0; u < U; ++u) c[u] = j0 + u < jend ? ld_stream(cp + (int64_t)u * R) : 0;
+            for (int j = j0; j < jend; j += U) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) cn[u] = j + U + u < jend ? ld_stream(cp + (int64_t)(U + u) * R) : 0;
+                A xv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (j + u < jend) xv[u] = __ldg(x + c[u]);
+                A v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (j + u < jend) v[u] = VT<V>::ld(vp + (int64_t)u * R);
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (j + u < jend) acc = fma(v[u], xv[u], acc);
+#pragma unroll
+                for (int u = 0; u < U; ++u) c[u] = cn[u];
+                vp += (int64_t)U * R;
+                cp += (int64_t)U * R;
             }
+        } else {
+            for (int j = j0; j < jend; j += U) {
+                A v[U];
+                int c[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (j + u < jend) acc = fma(v[u], __ldg(x + c[u]), acc);
-            vp += (int64_t)U * R;
-            cp += (int64_t)U * R;
+                for (int u = 0; u < U; ++u) {
+                    if (j + u < jend) {
+                        v[u] = VT<V>::ld(vp + (int64_t)u * R);
+                        c[u] = ld_stream(cp + (int64_t)u * R);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (j + u < jend) acc = fma(v[u], __ldg(x + c[u]), acc);
+                vp += (int64_t)U * R;
+                cp += (int64_t)U * R;
+            }
         }
         if (nt == 1) {
             if (active) y[orow] = VT<V>::scaled ? acc * sc : acc;
@@ -312,12 +341,13 @@ int launch_tiles(const rgcsr_matrix *M, const rgcsr_tiles *T, const typename VT<
     // slot-rows in flight per lane (U) and CTAs per SM by variant:
     // 0: U = 8 (FP64: 4), 5 CTAs;  1: U = 4 (FP64: 2), 6 CTAs;  2: U = 16 (FP64: 8), 4 CTAs;
     // 3, 4: software-pipelined, U = 4 (FP64: 2) with 4 CTAs, U = 8 (FP64: 4) with 3 CTAs;
-    // 5: software-pipelined, U = 16 (FP64: 8) with 2 CTAs
+    // 5: software-pipelined, U = 16 (FP64: 8) with 2 CTAs;
+    // 6, 7: each step's columns loaded one step ahead, U = 8 with 3 CTAs, U = 8 (FP64: 4) with 4
     constexpr int U0 = sizeof(A) == 8 ? 4 : 8;
     void (*kern)(int64_t, int32_t, int32_t, int64_t, int64_t, const V *, const int32_t *, const int64_t *,
                  const int32_t *, const float *, const int64_t *, const int64_t *, const int32_t *, int32_t *,
                  A *, const A *, A *, const int32_t *);
-    static int cache[6][64];
+    static int cache[8][64];
     int *cc;
     switch (T->variant) {
         case 0: kern = rgcsr_spmv_tiles_kernel<V, U0, 5>; cc = cache[0]; break;
@@ -326,6 +356,8 @@ int launch_tiles(const rgcsr_matrix *M, const rgcsr_tiles *T, const typename VT<
         case 3: kern = rgcsr_spmv_tiles_pipe_kernel<V, U0 / 2, 4>; cc = cache[3]; break;
         case 4: kern = rgcsr_spmv_tiles_pipe_kernel<V, U0, 3>; cc = cache[4]; break;
         case 5: kern = rgcsr_spmv_tiles_pipe_kernel<V, 2 * U0, 2>; cc = cache[5]; break;
+        case 6: kern = rgcsr_spmv_tiles_kernel<V, 8, 3, true>; cc = cache[6]; break;
+        case 7: kern = rgcsr_spmv_tiles_kernel<V, U0, 4, true>; cc = cache[7]; break;
         default: return RGCSR_ERR_INVALID_ARG;
     }
     int64_t grid = resident_ctas(kern, cc);                                 // persistent

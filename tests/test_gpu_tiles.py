@@ -137,7 +137,7 @@ def test_tiles_full_size_b_descending(dtype):
                              dtype=TT[dtype], row_order="descending")
     x = synth.uniform_vector(A.n_cols, seed=0)
     for C in (32, 64, 128):
-        for v in range(6):
+        for v in range(8):
             M._tiles = None
             M.tile_groups(C, variant=v)
             check(M, A, dtype, x)
@@ -154,7 +154,7 @@ def test_tiles_full_size_stencils(name):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("C", [3, 64])
 def test_tiles_variants(dtype, variant, C):
     A = ragged(3001, 4000, seed=variant * 10 + C)
@@ -162,6 +162,6 @@ def test_tiles_variants(dtype, variant, C):
                              dtype=TT[dtype], row_order="descending").tile_groups(C, variant=variant)
     check(M, A, dtype, synth.uniform_vector(A.n_cols, seed=6))
     bad = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dtype]), A.n_cols, group_size=32,
-                               dtype=TT[dtype]).tile_groups(C, variant=6)
+                               dtype=TT[dtype]).tile_groups(C, variant=8)
     with pytest.raises(L.RgCSRError):
         bad.spmv(torch.zeros(A.n_cols, dtype=TT[dtype], device="cuda"))
