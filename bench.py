@@ -222,8 +222,14 @@ def cpu_baseline(mats, seconds):
             nbytes += oracle_pass(pool, blocks)
             passes += 1
         t = time.perf_counter() - t0
+    # the same loop on one thread, one pass
+    with ThreadPoolExecutor(1) as pool1:
+        t1 = time.perf_counter()
+        nb1 = oracle_pass(pool1, blocks)
+        t1 = time.perf_counter() - t1
     return {"value": nbytes / t / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{passes} pass(es) of the six SpMVs (FP64 CSR loop), {t:.1f} s on {threads} threads"}
+            "sample": f"{passes} pass(es) of the six SpMVs (FP64 CSR loop), {t:.1f} s on {threads} threads",
+            "single_thread_gbs": nb1 / t1 / 1e9}
 
 
 def run_reference(args):
@@ -547,12 +553,15 @@ def run_ours(args):
 
     # ---- per case: a graph of its COPIES copies in turn, ROUNDS times ----
     per_case_us = [rotating_us([launcher(c, j) for j in range(COPIES)], stream) for c in cases]
+    # and hot: the same copy every time (what of the case L2 can keep, it keeps)
+    hot_us = [rotating_us([launcher(c, 0)] * COPIES, stream) for c in cases]
     clk = clocks.stop() if clocks else None
 
     detail = {}
-    for c, us in zip(cases, per_case_us):
+    for c, us, hot in zip(cases, per_case_us, hot_us):
         detail[c["key"]] = {"gbs": c["bytes"] / us / 1e3, "gflops": 2 * c["nnz"] / us / 1e3,
-                            "us": us, "pct_of_8tbs": 100 * c["bytes"] / us / 1e3 / roofline.NOMINAL_HBM_GBS,
+                            "us": us, "hot_us": hot,
+                            "pct_of_8tbs": 100 * c["bytes"] / us / 1e3 / roofline.NOMINAL_HBM_GBS,
                             "artificial_zero_pct": c["pad_pct"], "kernel": c["kernel"],
                             "launches": c["launches"],
                             "config": {k: v for k, v in c["config"].items() if k != "us"}}
@@ -638,7 +647,8 @@ def run_ours(args):
             launches=K * sum(c["launches"] for c in cases),
             clocks={k: v for k, v in clk.items() if k != "samples"} if clk else None,
             roof={k: v for k, v in roof.items() if k not in ("fp64_fma", "cases")},
-            e2e={k: v for k, v in e2e.items() if k not in ("note", "one_stream_value")}, cpu=cpu,
+            e2e={k: v for k, v in e2e.items() if k not in ("note", "one_stream_value")},
+            cpu={k: v for k, v in cpu.items() if k != "single_thread_gbs"} if cpu else None,
             cases={c["key"]: [d["us"], d["gbs"]]
                    for c, d in ((c, detail[c["key"]]) for c in cases)},
             forms_summary=forms_summary(forms), detail_file=args.detail_out)
