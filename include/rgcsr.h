@@ -595,7 +595,9 @@ int rgcsr_set_wait_limit(int32_t polls);
 /* Mixed-precision iterative refinement: outer loop in FP64 (r = b - A_hi x
  * with the F64 matrix A_hi, stop when ||r|| <= outer_tol ||b|| or after
  * max_outer corrections), inner CG in float on A_lo (F32, BF16 or F16
- * storage of the same matrix) to inner_tol, x += d in FP64.  b, x: double.
+ * storage of the same matrix) to a relative residual of max(inner_tol,
+ * outer_tol / (2 ||r|| / ||b||)) -- no further than the outer goal needs --,
+ * x += d in FP64.  b, x: double.
  * Writes the number of corrections, the total inner iterations and the
  * final true relative residual (host); synchronises `stream`. */
 size_t rgcsr_ir_cg_workspace_bytes(int64_t n);

@@ -588,11 +588,14 @@ RGCSR_API int rgcsr_ir_cg(const rgcsr_matrix *A_hi, const rgcsr_matrix *A_lo, co
         rel = std::sqrt(rr / bb);
         *outer_iters = k;
         if (rel <= outer_tol || k == max_outer || !(rel == rel)) break;
-        // inner: A_lo d = r in float
+        // inner: A_lo d = r in float, to the inner tolerance or, when the outer
+        // goal is nearer, only as far as it needs: a correction that cuts the
+        // residual by outer_tol / rel (halved for safety) ends the solve
         if ((st = convert_device(n, r64, RGCSR_F64, r32, RGCSR_F32, s)) != RGCSR_OK) return st;
         int its = 0;
         double irel = 0.0;
-        if ((st = cg_run<float>(A_lo, r32, d32, inner_tol, max_inner, 10, inner, &its, &irel, s)) != RGCSR_OK)
+        const double tol_k = std::max(inner_tol, 0.5 * outer_tol / rel);
+        if ((st = cg_run<float>(A_lo, r32, d32, tol_k, max_inner, 10, inner, &its, &irel, s)) != RGCSR_OK)
             return st;
         total_inner += its;
         if ((st = convert_device(n, d32, RGCSR_F32, d64, RGCSR_F64, s)) != RGCSR_OK) return st;
