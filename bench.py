@@ -933,12 +933,12 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None,
 
     if want("spmm"):
         # -- multi-RHS SpMM on (b) ------------------------------------------------
-        # natural row order, G = 1 with the long-row schedule (T = 32, 256-slot
+        # natural row order, G = 1 with the long-row schedule (T = 16, 64-slot
         # segments): the lanes-per-row kernels; the thread-per-row kernel at the
         # byte model's group size beside it
         b = [m for m in mats if m[0] == "b"][0][1]
         Mb = RgCSRMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32,
-                                  group_size=1).split_long_rows(32, 256)
+                                  group_size=1).split_long_rows(16, 64)
         Gm = model_group_size(b.rowptr, 4)
         Mt = RgCSRMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32,
                                   group_size=Gm)
@@ -946,7 +946,7 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None,
         Md = RgCSRMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32,
                                   group_size=32, row_order="descending").tile_groups(64)
         Hb = HybMatrix.from_csr(b.rowptr, b.col, b.val.astype(np.float32), b.n_cols, dtype=torch.float32)
-        forms["spmm_b_f32"] = {"configs": {"lanes_per_row": "G=1, long-row schedule T=32 S=256",
+        forms["spmm_b_f32"] = {"configs": {"lanes_per_row": "G=1, long-row schedule T=16 S=64",
                                            "tiles": "G=32, descending row order, group tiles C=64",
                                            "thread_per_row": f"G={Gm}"}}
         for k in (1, 4, 8, 16, 32):

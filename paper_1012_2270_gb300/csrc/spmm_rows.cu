@@ -19,6 +19,10 @@ namespace rgcsr {
 namespace {
 
 constexpr int kRowThreads = 256;
+// Blocks of the row kernel (rows up to the long-row threshold): two warps,
+// so that an SM slot is freed as soon as its few rows are done -- rows of
+// very different lengths end at very different times.
+constexpr int kShortThreads = 64;
 
 template <typename A, int W, bool VEC>
 __device__ __forceinline__ void load_w(const A *__restrict__ p, A (&o)[W]) {
@@ -153,11 +157,12 @@ int launch_chunk_rows(const rgcsr_matrix *M, const rgcsr_long_rows *L, const typ
                       typename VT<V>::A *Y, int64_t ldy, typename VT<V>::A *part, cudaStream_t s) {
     constexpr int kc = S * W;
     constexpr int rows_per_block = (kRowThreads / 32) * (32 / S);
+    constexpr int rows_per_short_block = (kShortThreads / 32) * (32 / S);
     const V *val = static_cast<const V *>(M->values);
     const int cap = L ? L->threshold : INT_MAX;
-    int64_t blocks = ceil_div(M->n_rows, rows_per_block);
+    int64_t blocks = ceil_div(M->n_rows, rows_per_short_block);
     if (blocks > INT32_MAX) return RGCSR_ERR_INDEX_OVERFLOW;
-    spmm_rows_kernel<V, S, W, U, VEC, false><<<(unsigned)blocks, kRowThreads, 0, s>>>(
+    spmm_rows_kernel<V, S, W, U, VEC, false><<<(unsigned)blocks, kShortThreads, 0, s>>>(
         M->n_rows, M->group_size, val, M->columns, M->group_ptr, M->row_lengths, M->row_scale, cap, M->n_rows,
         nullptr, nullptr, 0, X, ldx, Y, ldy, M->row_perm);
     int st = launch_status();
