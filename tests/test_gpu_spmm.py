@@ -148,11 +148,12 @@ def test_spmm_rows_partials_too_small():
     assert st == L.RGCSR_ERR_WORKSPACE
 
 
-@pytest.mark.parametrize("k", [4, 32])
-def test_spmm_rows_full_size_b(k):
+@pytest.mark.parametrize("k,sched", [(4, (32, 256)), (16, (16, 64)), (32, (16, 64))])
+def test_spmm_rows_full_size_b(k, sched):
+    # (16, 64): the schedule the benchmark's SpMM form times
     A = synth.workload_b()
     M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(np.float32), A.n_cols, group_size=1,
-                             dtype=torch.float32).split_long_rows(32, 256)
+                             dtype=torch.float32).split_long_rows(*sched)
     X = synth.uniform_matrix(A.n_cols, k, seed=k)
     check(A, M, "f32", X, TAU["f32"])
 
