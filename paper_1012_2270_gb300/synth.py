@@ -2,9 +2,10 @@
 
 This module only *generates inputs*; it contains none of the RgCSR method's
 arithmetic (no layout, no SpMV), so both the CUDA path and the CPU oracle can
-take their inputs from it.  All matrices come back as plain CSR in host
+take their inputs from it.  Matrices come back as plain CSR in host
 memory: ``rowptr`` int64 [n+1], ``col`` int32 [nnz] (ascending within a row),
-``val`` float64 [nnz].
+``val`` float64 [nnz] -- except ``uniform_rows_device``, a matrix past 2^31
+entries given by closed forms, which is generated on the device.
 
 The shapes stand in for the paper's test collection (University of Florida
 and Matrix Market matrices, Sec. 4.1, which are not redistributable here):
@@ -337,3 +338,46 @@ def batch_member(i: int, seed_base: int = 1000, n_min: int = 1000,
 def workload_batch(count: int = 512, seed_base: int = 1000, n_min: int = 1000,
                    n_max: int = 200_000) -> list[CSRMatrix]:
     return [batch_member(i, seed_base, n_min, n_max) for i in range(count)]
+
+
+# ---------------------------------------------------------------------------
+# A matrix with more than 2^31 stored slots (the 64-bit slot offsets of the
+# group pointers).  Every row holds exactly `length` entries given by closed
+# forms, so that the whole matrix can be generated on the device in bulk
+# (host arrays of that size would be unwieldy) and any sampled row again on
+# the host.
+# ---------------------------------------------------------------------------
+_UA, _UB = 7919, 104729
+
+
+def uniform_rows_entries(rows, length: int, n_cols: int) -> tuple[np.ndarray, np.ndarray]:
+    """Columns [len(rows), length] int32 and values float64 of the given rows:
+    entry j of row i has column (7919 i + 104729 j) mod n_cols and value
+    ((i + 3 j) mod 17 - 8) / 16 (exact in binary32 and below)."""
+    i = np.asarray(rows, dtype=np.int64)[:, None]
+    j = np.arange(length, dtype=np.int64)[None, :]
+    col = ((_UA * i + _UB * j) % n_cols).astype(np.int32)
+    val = (((i + 3 * j) % 17) - 8).astype(np.float64) / 16.0
+    return col, val
+
+
+def uniform_rows_device(n: int, length: int, n_cols: int, device="cuda", chunk: int = 1 << 22):
+    """The n-row matrix of uniform_rows_entries as torch tensors on `device`:
+    rowptr int64 [n+1], col int32 [n*length], val float32 [n*length]."""
+    import torch
+    rowptr = torch.arange(n + 1, dtype=torch.int64, device=device) * length
+    col = torch.empty(n * length, dtype=torch.int32, device=device)
+    val = torch.empty(n * length, dtype=torch.float32, device=device)
+    j = torch.arange(length, dtype=torch.int64, device=device)[None, :]
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        i = torch.arange(r0, r1, dtype=torch.int64, device=device)[:, None]
+        col[r0 * length:r1 * length] = ((_UA * i + _UB * j) % n_cols).to(torch.int32).reshape(-1)
+        val[r0 * length:r1 * length] = ((((i + 3 * j) % 17) - 8).to(torch.float32) / 16.0).reshape(-1)
+    return rowptr, col, val
+
+
+def uniform_x(n: int) -> np.ndarray:
+    """x_k = ((5 k) mod 23 - 11) / 32, float32 (exact)."""
+    k = np.arange(n, dtype=np.int64)
+    return ((((5 * k) % 23) - 11) / 32.0).astype(np.float32)

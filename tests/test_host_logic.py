@@ -189,3 +189,27 @@ def test_bench_headline_is_short_and_parses():
         assert key in back
     assert back["roofline"]["frac"] == pytest.approx(0.1235, rel=1e-3)
     assert "workload" in back["config"]
+
+
+def test_uniform_rows_generator_and_its_layout():
+    # the bulk device generator (here on the CPU) agrees with the per-row
+    # closed form, and the oracle's layout of such a matrix has the closed
+    # form that the GPU test past 2^31 slots expects: 32 rows x `length`
+    # slots per group, gp[g] = 32 length g, slot j of row i at
+    # gp[i // 32] + 32 j + i % 32
+    torch = pytest.importorskip("torch")
+    n, length, m = 128, 5, 37
+    rp, c, v = synth.uniform_rows_device(n, length, m, device="cpu", chunk=7)
+    cr, vr = synth.uniform_rows_entries(np.arange(n), length, m)
+    assert rp.dtype == torch.int64 and c.dtype == torch.int32 and v.dtype == torch.float32
+    assert np.array_equal(rp.numpy(), np.arange(n + 1) * length)
+    assert np.array_equal(c.numpy(), cr.reshape(-1))
+    assert np.array_equal(v.numpy().astype(np.float64), vr.reshape(-1))
+    lay = oracle.rgcsr_layout(rp.numpy(), c.numpy(), v.numpy(), 32)
+    assert np.array_equal(lay.group_ptr, 32 * length * np.arange(n // 32 + 1))
+    i = np.arange(n)[:, None]
+    slots = 32 * length * (i // 32) + 32 * np.arange(length)[None, :] + i % 32
+    assert np.array_equal(lay.columns[slots], cr)
+    assert np.array_equal(lay.values[slots], v.numpy().reshape(n, length))
+    x = synth.uniform_x(1000)
+    assert x.dtype == np.float32 and np.array_equal(x.astype(np.float64) * 32, ((5 * np.arange(1000)) % 23) - 11)
