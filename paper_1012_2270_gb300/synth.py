@@ -377,7 +377,7 @@ def uniform_rows_device(n: int, length: int, n_cols: int, device="cuda", chunk: 
     return rowptr, col, val
 
 
-def uniform_x(n: int) -> np.ndarray:
-    """x_k = ((5 k) mod 23 - 11) / 32, float32 (exact)."""
+def uniform_x(n: int, shift: int = 0) -> np.ndarray:
+    """x_k = ((5 k + shift) mod 23 - 11) / 32, float32 (exact)."""
     k = np.arange(n, dtype=np.int64)
-    return ((((5 * k) % 23) - 11) / 32.0).astype(np.float32)
+    return ((((5 * k + shift) % 23) - 11) / 32.0).astype(np.float32)

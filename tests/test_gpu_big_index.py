@@ -5,7 +5,8 @@ pointers and every slab offset of the last two million rows lie past the
 Sec. 3.4 layout on sampled groups and slots (the closed form itself is
 pinned against the oracle's layout on a small case in test_host_logic.py),
 and the SpMV kernels against the CPU oracle on sampled rows (the oracle
-computes each sampled row from its entries and the full x)."""
+computes each sampled row from its entries and the full x); likewise BF16
+storage and the three SpMM kernels with four right-hand sides."""
 import numpy as np
 import pytest
 import torch
@@ -74,7 +75,30 @@ def test_slots_past_2_pow_31():
     for kw in ({}, dict(kernel=L.KERNEL_LEAN), dict(kernel=L.KERNEL_SPLIT),
                dict(kernel=L.KERNEL_LEAN, variant=1), dict(kernel=L.KERNEL_TMA, variant=2)):
         check(M.spmv(xd, **kw), kw)
+    # BF16 storage: the values k/16, |k| <= 8, are exact in bfloat16 after the
+    # power-of-two row scale, so the dequantised matrix is the matrix itself
+    Q = M.quantized("bf16")
+    check(Q.spmv(xd), "bf16")
+    del Q
+
+    # SpMM, k = 4: thread per row, lanes per row, then (below) group tiles
+    k = 4
+    Xh = np.stack([synth.uniform_x(N, shift=3 * c) for c in range(k)], axis=1)
+    refs = [oracle.csr_spmv(sub_rowptr, cols_ref.reshape(-1), vals_ref.reshape(-1), Xh[:, c].astype(np.float64))
+            for c in range(k)]
+    Xd = torch.from_numpy(Xh).cuda()
+    del Xh
+
+    def check_mm(Y, what):
+        Yr = Y[r_t].cpu().numpy().astype(np.float64)
+        for c, (yc, ac) in enumerate(refs):
+            err = np.abs(Yr[:, c] - yc)
+            assert (err <= 2e-6 * ac).all(), (what, c, float(err.max()))
+
+    check_mm(M.spmm(Xd, rows=False), "spmm thread per row")
+    check_mm(M.spmm(Xd, rows=True), "spmm lanes per row")
     M.tile_groups(64)
     check(M.spmv(xd), "tiles")
-    del M
+    check_mm(M.spmm(Xd), "spmm tiles")
+    del M, Xd
     torch.cuda.empty_cache()
