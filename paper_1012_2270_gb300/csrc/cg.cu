@@ -344,6 +344,17 @@ unsigned cg_grid(int64_t units, int per_sm) {
     return (unsigned)(b > 0 ? b : 1);
 }
 
+// The recorded round of CG iterations, destroyed when the solve returns.
+struct GraphExec {
+    cudaGraphExec_t h = nullptr;
+    GraphExec() = default;
+    GraphExec(const GraphExec &) = delete;
+    GraphExec &operator=(const GraphExec &) = delete;
+    ~GraphExec() {
+        if (h) cudaGraphExecDestroy(h);
+    }
+};
+
 struct CgScratch {
     void *r, *d, *q;
     double *scal;       // [rr0, rr1, dq, alpha, beta]
@@ -459,15 +470,15 @@ int cg_run(const rgcsr_matrix *A, const void *b, void *x, double rel_tol, int ma
     // be the legacy default stream, which cannot be captured) and replayed on
     // the caller's stream.  check_every is even, so a round leaves `cur` as
     // it found it.  If recording fails the iterations are launched directly.
-    cudaGraphExec_t round = nullptr;
+    GraphExec round;                                 // destroyed on every return
     bool tried = false;
     while (it < max_iter) {
         const int chunk = check_every < max_iter - it ? check_every : max_iter - it;
-        if (round && chunk == check_every) {
-            RGCSR_CUDA_TRY(cudaGraphLaunch(round, s));
+        if (round.h && chunk == check_every) {
+            RGCSR_CUDA_TRY(cudaGraphLaunch(round.h, s));
         } else {
             for (int i = 0; i < chunk; ++i) {
-                if ((st = iteration(s, cur)) != RGCSR_OK) { if (round) cudaGraphExecDestroy(round); return st; }
+                if ((st = iteration(s, cur)) != RGCSR_OK) return st;
                 cur = 1 - cur;
             }
         }
@@ -476,7 +487,7 @@ int cg_run(const rgcsr_matrix *A, const void *b, void *x, double rel_tol, int ma
         RGCSR_CUDA_TRY(cudaMemcpyAsync(&rr, &c.scal[cur], sizeof(double), cudaMemcpyDeviceToHost, s));
         RGCSR_CUDA_TRY(cudaMemcpyAsync(&cw, words, sizeof(cw), cudaMemcpyDeviceToHost, s));
         RGCSR_CUDA_TRY(cudaStreamSynchronize(s));
-        if (cw.error) { if (round) cudaGraphExecDestroy(round); return RGCSR_ERR_TIMEOUT; }
+        if (cw.error) return RGCSR_ERR_TIMEOUT;
         if (!(rr == rr) || std::sqrt(rr) <= rel_tol * std::sqrt(bb)) break;   // converged (or NaN)
         if (!tried && check_every % 2 == 0 && max_iter - it >= 2 * check_every) {
             tried = true;
@@ -487,8 +498,8 @@ int cg_run(const rgcsr_matrix *A, const void *b, void *x, double rel_tol, int ma
                     int e = RGCSR_OK;
                     for (int i = 0; i < check_every && e == RGCSR_OK; ++i) e = iteration(cap, (cur + i) & 1);
                     if (cudaStreamEndCapture(cap, &g) == cudaSuccess && g && e == RGCSR_OK &&
-                        cudaGraphInstantiate(&round, g, 0) != cudaSuccess)
-                        round = nullptr;
+                        cudaGraphInstantiate(&round.h, g, 0) != cudaSuccess)
+                        round.h = nullptr;
                     if (g) cudaGraphDestroy(g);
                 }
                 cudaStreamDestroy(cap);
@@ -496,7 +507,6 @@ int cg_run(const rgcsr_matrix *A, const void *b, void *x, double rel_tol, int ma
             cudaGetLastError();                      // a failed recording leaves no sticky error
         }
     }
-    if (round) cudaGraphExecDestroy(round);
     *iterations = it;
     *rel_residual = std::sqrt(rr / bb);
     return (rr == rr) ? RGCSR_OK : RGCSR_ERR_INVALID_ARG;
