@@ -805,7 +805,7 @@ def max_scaled_error(y, y_ref, absy):
 
 def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None, ir_sweep=True):
     """The forms beside the plain SpMV; `only` (a set of names: hyb,
-    quantized, x_read_path, spmm, backward, ir_cg, jacobi, conversion,
+    quantized, x_read_path, spmm, backward, ir_cg, jacobi, small, conversion,
     group_size_sweep, table6, batched) limits them, None runs all."""
     import torch
     from paper_1012_2270_gb300 import solvers
@@ -1089,6 +1089,34 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None,
                 "peak_extra_mem_mb": (torch.cuda.max_memory_allocated() - base) / 2**20}
         forms["jacobi_grad_96_f32"] = res
         del opj
+
+    if want("small"):
+        # -- the small case (2D 5-point Laplacian 64 x 64, n = 4,096): it fits
+        # in L2, so no roofline claim -- the device time per SpMV (a graph of
+        # 20 back-to-back calls, median of 30 replays) and the latency of one
+        # call through the Python binding, launch to synchronised result ----
+        from paper_1012_2270_gb300 import synth
+        A = synth.workload_small_laplacian()
+        small = {"n": A.n_rows, "nnz": A.nnz}
+        for dt in DTYPES:
+            M = RgCSRMatrix.from_csr(A.rowptr, A.col, A.val.astype(NP[dt]), A.n_cols, group_size=32,
+                                     dtype=TT[dt])
+            x = torch.from_numpy(synth.uniform_vector(A.n_cols, seed=0).astype(NP[dt])).to(dev)
+            y = torch.empty(A.n_rows, dtype=TT[dt], device=dev)
+            g = capture_graph([lambda: M.spmv(x, out=y)] * 20)
+            dev_us = statistics.median(replay_us(g, 30, stream)) / 20
+            del g
+            ts = []
+            for rep in range(210):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                M.spmv(x, out=y)
+                torch.cuda.synchronize()
+                if rep >= 10:
+                    ts.append(1e6 * (time.perf_counter() - t0))
+            small[dt] = {"device_us": dev_us, "call_us": statistics.median(ts), "kernel": kernel_name({}, M, A, dt)}
+            del M, x, y
+        forms["small_laplacian_64"] = small
 
     if want("conversion"):
         # -- conversion CSR -> RgCSR on the device (plan + convert; FP32 values,
