@@ -1095,7 +1095,6 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None,
         # in L2, so no roofline claim -- the device time per SpMV (a graph of
         # 20 back-to-back calls, median of 30 replays) and the latency of one
         # call through the Python binding, launch to synchronised result ----
-        from paper_1012_2270_gb300 import synth
         A = synth.workload_small_laplacian()
         small = {"n": A.n_rows, "nnz": A.nnz}
         for dt in DTYPES:
