@@ -213,3 +213,27 @@ def test_uniform_rows_generator_and_its_layout():
     assert np.array_equal(lay.values[slots], v.numpy().reshape(n, length))
     x = synth.uniform_x(1000)
     assert x.dtype == np.float32 and np.array_equal(x.astype(np.float64) * 32, ((5 * np.arange(1000)) % 23) - 11)
+
+
+def test_bench_functions_do_not_shadow_module_imports():
+    # a function-local import of a name the module already imports makes
+    # the name local to the whole function, so any earlier use in it fails
+    # at run time (UnboundLocalError) -- only on the GPU machine, where the
+    # forms run; caught here by reading bench.py
+    import ast
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py")
+    tree = ast.parse(open(path).read())
+    module = {a.asname or a.name.split(".")[0] for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))
+              for a in n.names}
+    bad = []
+    for fn in ast.walk(tree):
+        if not isinstance(fn, ast.FunctionDef):
+            continue
+        for node in ast.walk(fn):
+            if isinstance(node, (ast.Import, ast.ImportFrom)):
+                for a in node.names:
+                    name = a.asname or a.name.split(".")[0]
+                    if name in module:
+                        bad.append((fn.name, name, node.lineno))
+    assert not bad, bad
