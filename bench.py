@@ -1007,17 +1007,39 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None,
         def spmm_only(op, vals, X):
             op.A.spmm(X.detach(), out=op._bench_y)
 
+        # a training step changes the values before every forward: each
+        # operator alternates between two value tensors (the second negated),
+        # so every call finds values that differ from the ones it last loaded
+        def changed(o):
+            op, vals, X = o
+            v = op._bench_vals[op._bench_flip]
+            op._bench_flip ^= 1
+            return op, v, X
+
+        def fwd_changed(op, vals, X):
+            return fwd(*changed((op, vals, X)))
+
+        def fwd_bwd_changed(op, vals, X):
+            return fwd_bwd(*changed((op, vals, X)))
+
         for o in ops:
             o[0]._bench_y = torch.empty(b.n_rows, 8, device=dev)
             o[0]._bench_dy = torch.rand(b.n_rows, 8, device=dev)
+            o[0]._bench_vals = [o[1], (-o[1].detach()).requires_grad_(True)]
+            o[0]._bench_flip = 0
         t_mm = per_call_us(spmm_only)
         torch.cuda.nvtx.range_push("autograd_forward")            # a profiler can pick it out
         t_f = per_call_us(fwd)
         torch.cuda.nvtx.range_pop()
         t_fb = per_call_us(fwd_bwd)
+        t_fc = per_call_us(fwd_changed)
+        t_fbc = per_call_us(fwd_bwd_changed)
         forms["backward_b_k8_f32"] = {"group_size": G, "schedule": "descending row order, group tiles C=64",
                                       "spmm_us": t_mm, "forward_us": t_f, "forward_backward_us": t_fb,
-                                      "forward_over_spmm": t_f / t_mm, "backward_over_forward": (t_fb - t_f) / t_f}
+                                      "forward_over_spmm": t_f / t_mm, "backward_over_forward": (t_fb - t_f) / t_f,
+                                      "values_changed": {"forward_us": t_fc, "forward_backward_us": t_fbc,
+                                                         "forward_over_spmm": t_fc / t_mm,
+                                                         "step_over_spmm": t_fbc / t_mm}}
         del ops
 
     if want("ir_cg") and "a_f64" in by:
