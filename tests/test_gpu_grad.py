@@ -188,14 +188,16 @@ def test_bwd_values_from_rgcsr(dtype, G, order, k):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-def test_values_reloaded_only_when_they_change(dtype):
+@pytest.mark.parametrize("schedule", [{}, {"row_order": "descending", "tiles": 16}])
+def test_values_reloaded_only_when_they_change(dtype, schedule):
     # the operator gathers values into A (forward) or A^T (backward) only
     # when the values tensor changed: products stay right when values are
     # updated in place, when another tensor is used, and when a backward
-    # runs after a forward with other values
+    # runs after a forward with other values; with and without a row order
+    # and group tiles on A and A^T
     rng = np.random.default_rng(9)
     A = synth.random_csr(700, 500, rng.integers(0, 30, 700), seed=9)
-    op = SparseOperator(A.rowptr, A.col, A.n_cols, dtype=TT[dtype])
+    op = SparseOperator(A.rowptr, A.col, A.n_cols, dtype=TT[dtype], **schedule)
     X = synth.uniform_matrix(A.n_cols, 3, seed=4).astype(NP[dtype])
     Xt = torch.tensor(X, device="cuda")
 
