@@ -1202,7 +1202,7 @@ def measure_forms(mats, cases, detail, dev, stream, tune_cache=False, only=None,
         # the same batch as one block-diagonal matrix, rows in descending length
         # order over the whole batch, group tiles
         bd = {}
-        for tile, var in ((64, 0), (64, 1), (32, 1), (64, 7)):
+        for tile, var in ((64, 1), (64, 7), (128, 7), (256, 7)):
             Bd = BlockDiagonalBatch.from_csr_list(members, dtype=torch.float32, tile=tile, variant=var)
             gd = Bd.capture(xb, yb, repeats=1)
             bd[f"tiles_{tile}_v{var}"] = time_flushed(lambda: gd.replay(), 10, flush, stream)

@@ -103,11 +103,12 @@ def test_block_diagonal_batch(dtype, order, tile):
     assert torch.equal(y2, y_cat)                                           # deterministic, replayable
 
 
-def test_block_diagonal_full_batch_sampled():
-    # the benchmark's 512-member batch in its block-diagonal configuration:
-    # every member's rows checked against the oracle
+@pytest.mark.parametrize("tile,variant", [(128, 7), (256, 7)])
+def test_block_diagonal_full_batch_sampled(tile, variant):
+    # the benchmark's 512-member batch in the block-diagonal configurations
+    # it times fastest: every member's rows checked against the oracle
     mats = synth.workload_batch(512)
-    Bd = BlockDiagonalBatch.from_csr_list(mats, dtype=torch.float32, tile=64, variant=1)
+    Bd = BlockDiagonalBatch.from_csr_list(mats, dtype=torch.float32, tile=tile, variant=variant)
     x_cat = torch.from_numpy(synth.uniform_vector(Bd.n_cols_total, seed=9).astype(np.float32)).cuda()
     y_cat = Bd.spmv(x_cat)
     check_batch(mats, Bd, "f32", x_cat, y_cat)
